@@ -1,0 +1,145 @@
+"""Level operators, transfers and the exact coarse solve of the space-time
+multigrid (paper Section 4.2, Eq. 4.1).  Oracle: test infrastructure only.
+
+A level l carries its own grid (shape, Nt_l, dt_l) and a per-slab, per-point
+reaction coefficient cbar_l (Nt_l, Ns_l).  Its linear operator is the slab
+Jacobian with the reaction derivative averaged over the nodes:
+
+    (A_l e)_n = e_n - dt_l (Q (x) (nu*Delta_{h_l} + diag cbar_{l,n})) e_n,
+    (C e)_n   = 1 (x) e_{n-1,M}    (e_{-1} = 0),
+
+and a correction e at level l solves  A_l e - C e = r.  On the finest level
+with cbar = mean_m R'(U_{n,m}) this is -dG/dU up to the node averaging; for a
+linear problem it is exactly -dG/dU.
+
+Transfers are Eq. (4.1) with the mass-coarsening factor fixed to the
+identity: either S (x) I_t (spatial full weighting / linear interpolation) or
+I_s (x) T (slab bisection, ``collocation.time_restriction``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import collocation as col
+from . import space
+
+
+@dataclass
+class Level:
+    shape: tuple     # numpy order
+    bc: int
+    Nt: int
+    M: int
+    dt: float
+    nu: float
+    X: float
+    cbar: np.ndarray  # (Nt, Ns)
+
+    @property
+    def Ns(self):
+        return int(np.prod(self.shape))
+
+    @property
+    def Q(self):
+        return col.collocation_matrix(col.radau_right_nodes(self.M))
+
+    @property
+    def L(self):
+        return (self.nu * space.laplacian(self.bc, self.shape, self.X)).tocsr()
+
+
+def _apply_L(L, E):
+    return (L @ E.reshape(-1, L.shape[0]).T).T.reshape(E.shape)
+
+
+def apply_A(lev: Level, e: np.ndarray) -> np.ndarray:
+    """A_l e (block diagonal part, no slab coupling)."""
+    e = e.reshape(lev.Nt, lev.M, lev.Ns)
+    Fe = _apply_L(lev.L, e) + lev.cbar[:, None, :] * e
+    return e - lev.dt * np.einsum("mj,njs->nms", lev.Q, Fe)
+
+
+def coupling(lev: Level, e: np.ndarray) -> np.ndarray:
+    """(C e)_n = 1 (x) e_{n-1,M}."""
+    e = e.reshape(lev.Nt, lev.M, lev.Ns)
+    out = np.zeros_like(e)
+    out[1:] = e[:-1, -1:, :]
+    return out
+
+
+def linear_residual(lev: Level, e: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """r - A_l e + C e."""
+    return r.reshape(lev.Nt, lev.M, lev.Ns) - apply_A(lev, e) + coupling(lev, e)
+
+
+def slab_matrix(lev: Level, n: int) -> sp.csc_matrix:
+    """A_{l,n} = I - dt_l Q (x) (L_l + diag cbar_{l,n}) as a sparse matrix."""
+    Ln = lev.L + sp.diags(lev.cbar[n])
+    return (sp.identity(lev.M * lev.Ns) - lev.dt * sp.kron(sp.csr_matrix(lev.Q), Ln)).tocsc()
+
+
+def coarse_solve_exact(lev: Level, r: np.ndarray) -> np.ndarray:
+    """Exact solution of A_l e - C e = r by forward substitution over slabs."""
+    r = r.reshape(lev.Nt, lev.M, lev.Ns)
+    e = np.zeros_like(r)
+    prev = np.zeros(lev.Ns)
+    for n in range(lev.Nt):
+        rhs = r[n] + prev[None, :]
+        e[n] = spla.spsolve(slab_matrix(lev, n), rhs.ravel()).reshape(lev.M, lev.Ns)
+        prev = e[n, -1]
+    return e
+
+
+def smoothing_step_exact(lev: Level, e: np.ndarray, r: np.ndarray, omega: float) -> np.ndarray:
+    """Damped block Jacobi in time with exact slab solves (one block per slab,
+    the Cores = Nt case of Section 4.2): e + omega * A_n^{-1}(r - A e + C e).
+    Parity unpinned: the weight omega is a solver parameter, not paper content."""
+    res = linear_residual(lev, e, r)
+    out = e.reshape(res.shape).copy()
+    for n in range(lev.Nt):
+        out[n] += omega * spla.spsolve(slab_matrix(lev, n), res[n].ravel()).reshape(lev.M, lev.Ns)
+    return out
+
+
+# -------------------------------------------------------------- transfers
+
+def restrict_space(bc: int, shape, v: np.ndarray) -> np.ndarray:
+    """Full weighting of every (slab, node) plane; v has shape (..., Ns)."""
+    R = space.restriction(bc, shape)
+    lead = v.shape[:-1]
+    return (R @ v.reshape(-1, v.shape[-1]).T).T.reshape(*lead, R.shape[0])
+
+
+def prolong_space(bc: int, shape, v: np.ndarray) -> np.ndarray:
+    """Linear interpolation of every plane to the fine grid ``shape``."""
+    P = space.prolongation(bc, shape)
+    lead = v.shape[:-1]
+    return (P @ v.reshape(-1, v.shape[-1]).T).T.reshape(*lead, P.shape[0])
+
+
+def restrict_time(M: int, v: np.ndarray) -> np.ndarray:
+    """Slab bisection restriction: (Nt, M, Ns) -> (Nt/2, M, Ns) with R_t."""
+    Nt, _, Ns = v.shape
+    Rt = col.time_restriction(col.radau_right_nodes(M))
+    pairs = v.reshape(Nt // 2, 2 * M, Ns)
+    return np.einsum("mk,nks->nms", Rt, pairs)
+
+
+def prolong_time(M: int, v: np.ndarray) -> np.ndarray:
+    """(Nt/2, M, Ns) -> (Nt, M, Ns) with P_t."""
+    Nc, _, Ns = v.shape
+    Pt = col.time_prolongation(col.radau_right_nodes(M))
+    return np.einsum("km,nms->nks", Pt, v).reshape(2 * Nc, M, Ns)
+
+
+def restrict_cbar_space(bc: int, shape, cb: np.ndarray) -> np.ndarray:
+    return restrict_space(bc, shape, cb)
+
+
+def restrict_cbar_time(cb: np.ndarray) -> np.ndarray:
+    """Average of the two fine slabs' coefficients."""
+    return 0.5 * (cb[0::2] + cb[1::2])

@@ -1,0 +1,162 @@
+"""Pins of oracle.collocation against closed forms (paper Section 2, textbook
+Radau IIA facts).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import collocation as col
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_radau3():
+    vals = {}
+    with open(os.path.join(GOLDEN, "radau_iia_m3.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, _, val = line.split()
+            vals[key] = float(val)
+    return vals
+
+
+def test_nodes_closed_forms():
+    assert np.allclose(col.radau_right_nodes(1), [1.0], atol=0)
+    assert np.allclose(col.radau_right_nodes(2), [1 / 3, 1.0], atol=1e-15)
+    s6 = math.sqrt(6.0)
+    assert np.allclose(col.radau_right_nodes(3), [(4 - s6) / 10, (4 + s6) / 10, 1.0], atol=1e-15)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_radau_quadrature_degree(M):
+    """Right Radau quadrature is exact for degree 2M-2 and not for 2M-1."""
+    tau = col.radau_right_nodes(M)
+    b = col.quadrature_weights(tau)
+    for k in range(2 * M - 1):
+        assert abs(b @ tau ** k - 1.0 / (k + 1)) < 1e-14
+    assert abs(b @ tau ** (2 * M - 1) - 1.0 / (2 * M)) > 1e-6
+    assert tau[-1] == 1.0 and np.all(np.diff(tau) > 0) and tau[0] > 0
+
+
+def test_q_m2_exact():
+    Q = col.collocation_matrix(col.radau_right_nodes(2))
+    assert np.allclose(Q, [[5 / 12, -1 / 12], [3 / 4, 1 / 4]], atol=1e-15)
+
+
+def test_q_m3_golden():
+    g = _golden_radau3()
+    Q = col.collocation_matrix(col.radau_right_nodes(3))
+    for i in range(3):
+        for j in range(3):
+            assert abs(Q[i, j] - g[f"a{i + 1}{j + 1}"]) < 2e-15
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_q_simplifying_assumption(M):
+    """Collocation integrates polynomials of degree < M exactly on every
+    sub-interval: Q tau^{k-1} = tau^k / k for k = 1..M; the last row is b."""
+    tau = col.radau_right_nodes(M)
+    Q = col.collocation_matrix(tau)
+    for k in range(1, M + 1):
+        assert np.abs(Q @ tau ** (k - 1) - tau ** k / k).max() < 1e-14
+    assert np.abs(Q[-1] - col.quadrature_weights(tau)).max() < 1e-15
+    assert np.abs(Q.sum(axis=1) - tau).max() < 1e-15
+
+
+# Pade (M-1, M) approximants of exp: the stability functions of Radau IIA
+PADE = {
+    1: (lambda z: 1.0, lambda z: 1 - z),
+    2: (lambda z: 1 + z / 3, lambda z: 1 - 2 * z / 3 + z * z / 6),
+    3: (lambda z: 1 + 2 * z / 5 + z * z / 20, lambda z: 1 - 3 * z / 5 + 3 * z * z / 20 - z ** 3 / 60),
+}
+PADE_DEN_COEFFS = {  # numpy.roots order, highest power first
+    1: [-1.0, 1.0],
+    2: [1 / 6, -2 / 3, 1.0],
+    3: [-1 / 60, 3 / 20, -3 / 5, 1.0],
+}
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_stability_function_is_pade(M):
+    Q = col.collocation_matrix(col.radau_right_nodes(M))
+    num, den = PADE[M]
+    for z in [-0.3, -2.0, -50.0, 0.7j - 1.0, -1e3 + 5j]:
+        assert abs(col.stability_function(z, Q) - num(z) / den(z)) < 1e-13 * max(1, abs(num(z) / den(z)))
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_q_eigenvalues_pade_roots(M):
+    Q = col.collocation_matrix(col.radau_right_nodes(M))
+    lam, V = col.q_eig(Q)
+    roots = np.roots(PADE_DEN_COEFFS[M])
+    expect = 1.0 / roots
+    for e in expect:  # every Pade-denominator root's reciprocal is an eigenvalue
+        assert np.abs(lam - e).min() < 1e-13
+    assert len(lam) == len(expect)
+    assert np.abs(Q @ V - V @ np.diag(lam)).max() < 1e-14
+    if M == 3:
+        real = lam[np.abs(lam.imag) < 1e-12].real
+        assert abs(real[0] - 1 / 3.6378342527444957) < 1e-12
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_dg_equals_collocation_matrices(M):
+    """DG in time (Eq. 2.8-2.10) and collocation (Eq. 2.3) define the same
+    step: Mq^{-1} K = Q^{-1} and K 1 = l(0) (the J column)."""
+    tau = col.radau_right_nodes(M)
+    K, Mq, J = col.dg_matrices(tau)
+    Q = col.collocation_matrix(tau)
+    rel = np.abs(np.linalg.solve(Mq, K) - np.linalg.inv(Q)).max() / np.abs(np.linalg.inv(Q)).max()
+    assert rel < 1e-12
+    assert np.abs(K @ np.ones(M) - J[:, M - 1]).max() < 1e-13
+    if M == 2:
+        assert np.allclose(J[:, 1], [1.5, -0.5], atol=1e-14)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_order_2m_minus_1(M):
+    """|R(dt*lam)^Nt - e^{lam T}| falls at order 2M-1 (Section 2.1; Fig. 5.1)."""
+    Q = col.collocation_matrix(col.radau_right_nodes(M))
+    lam, T = -1.0, 1.0
+    errs = []
+    Nts = [4, 8, 16, 32]
+    for Nt in Nts:
+        R = col.stability_function(lam * T / Nt, Q)
+        errs.append(abs(R ** Nt - math.exp(lam * T)))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(slopes[-1] - (2 * M - 1)) < 0.15
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_time_transfers(M):
+    tau = col.radau_right_nodes(M)
+    P = col.time_prolongation(tau)
+    R = col.time_restriction(tau)
+    # the coarse slab's polynomial of degree < M is reproduced at the fine nodes
+    for k in range(M):
+        coarse = tau ** k
+        fine_t = np.concatenate([tau / 2, (1 + tau) / 2])
+        assert np.abs(P @ coarse - fine_t ** k).max() < 1e-13
+    assert np.abs(R @ np.ones(2 * M) - 1).max() < 1e-14
+    assert np.abs(R * P.sum(axis=0)[:, None] - P.T).max() < 1e-14
+
+
+@pytest.mark.parametrize("kind", ["IE", "LU"])
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_sdc_qdelta(kind, M):
+    tau = col.radau_right_nodes(M)
+    QI, QE = col.sdc_qdelta(tau, kind)
+    assert np.allclose(np.triu(QI, 1), 0) and np.allclose(np.triu(QE), 0)
+    if kind == "IE":
+        # implicit Euler node to node integrates constants exactly: row sums = tau
+        assert np.abs(QI.sum(axis=1) - tau).max() < 1e-15
+    else:
+        # Q^T = L U with unit-lower L: Q^T - QI^T is strictly lower (U = QI^T)
+        Q = col.collocation_matrix(tau)
+        Lm = np.linalg.solve(QI, Q).T  # L = Q^T U^{-1} = (QI^{-1} Q)^T
+        assert np.allclose(np.diag(Lm), 1.0)
+        assert np.allclose(np.triu(Lm, 1), 0, atol=1e-13)
+    # explicit Euler from node j to node j+1 (strictly lower; row sums tau - tau_1)
+    assert np.abs(QE.sum(axis=1) - (tau - tau[0])).max() < 1e-15
