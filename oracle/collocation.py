@@ -149,10 +149,17 @@ def time_prolongation(tau: np.ndarray) -> np.ndarray:
 
 
 def time_restriction(tau: np.ndarray) -> np.ndarray:
-    """R_t (M x 2M) = P_t^T with each row scaled to sum to one, so that a
-    constant-in-time residual restricts to the same constant."""
-    Pt = time_prolongation(tau).T
-    return Pt / Pt.sum(axis=1, keepdims=True)
+    """R_t (M x 2M) for residuals of the collocation form.
+
+    The paper restricts the DG system (3.4) with the transpose of the time
+    prolongation (Eq. 4.1, time bisection of Section 5.2).  A DG residual is K
+    times the collocation residual of the same slab (K of Eq. 2.9 on the
+    unit interval), so the same restriction acting on collocation residuals
+    is  R_t = K^{-1} P_t^T blockdiag(K, K).  Constants in time are mapped to
+    constants on the last node (row M sums to 2, the other rows do not)."""
+    K, _, _ = dg_matrices(tau)
+    Pt = time_prolongation(tau)
+    return np.linalg.solve(K, Pt.T @ np.kron(np.eye(2), K))
 
 
 def sdc_qdelta(tau: np.ndarray, kind: str = "IE"):

@@ -139,8 +139,16 @@ def test_time_transfers(M):
         coarse = tau ** k
         fine_t = np.concatenate([tau / 2, (1 + tau) / 2])
         assert np.abs(P @ coarse - fine_t ** k).max() < 1e-13
-    assert np.abs(R @ np.ones(2 * M) - 1).max() < 1e-14
-    assert np.abs(R * P.sum(axis=0)[:, None] - P.T).max() < 1e-14
+    # R_t is P_t^T acting on DG residuals K r (Eq. 2.9): K R = P^T blockdiag(K, K)
+    K, _, _ = col.dg_matrices(tau)
+    assert np.abs(K @ R - P.T @ np.kron(np.eye(2), K)).max() < 1e-12
+    # a DG residual supported on one fine slab's node keeps its total weight
+    # against the coarse constant test function (Galerkin restriction property)
+    one = np.ones(M)
+    for k in range(2 * M):
+        v = np.zeros(2 * M)
+        v[k] = 1.0
+        assert abs(one @ (K @ (R @ v)) - np.ones(2 * M) @ (np.kron(np.eye(2), K) @ v)) < 1e-12
 
 
 @pytest.mark.parametrize("kind", ["IE", "LU"])
