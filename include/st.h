@@ -1,0 +1,312 @@
+/*
+ * st.h - C ABI of the GB300 space-time multigrid / SDC library (libst.so).
+ *
+ * Problem (Benedusi, Minion, Krause, "An experimental comparison of a
+ * space-time multigrid method with PFASST for a reaction-diffusion problem",
+ * Sections 2-4): the reaction-diffusion equation u_t = nu*Delta u + R(u)
+ * (Eq. 3.1 with nu and the reaction generalised) on a d-dimensional box,
+ * second-order finite differences in space (the lumped P1 FEM of Section 3
+ * for NEUMANN), right-Radau collocation in time on Nt slabs of M nodes
+ * (Eq. 2.3; equivalently DG in time, Eq. 2.8-2.11).  All slabs are solved at
+ * once: the unknown U is the space-time vector of Eq. (3.6),
+ *
+ *     U[n][m][z][y][x]   n < Nt (slab), m < M (Radau node), x fastest,
+ *
+ * stored as doubles, and the discrete system is, for every slab n,
+ *
+ *     G_n(U) = 1 (x) u_{n-1,M} + dt (Q (x) I) F(U_n) - U_n = 0,
+ *     F(u) = nu*Delta_h u + R(u),  u_{-1,M} := u0,                      (*)
+ *
+ * the collocation form (2.3) chained through the slab coupling of Eq. (3.4).
+ *
+ * Grids (per axis, domain [0, X)): DIRICHLET n interior points, h = X/(n+1);
+ * PERIODIC n points, h = X/n; NEUMANN n vertices, h = X/(n-1).
+ *
+ * Pointers.  Every double* argument named U, u0, u_target, gT, du0 or R may be
+ * a device pointer (on the handle's device) or a host pointer; host data is
+ * staged through library-owned device buffers inside the call.  The caller
+ * owns all these arrays; the library never keeps a pointer across calls.
+ * The st_level_* diagnostic calls take device pointers only.
+ *
+ * Streams.  All work is ordered on the stream given in st_runtime (0 = the
+ * legacy default stream).  Calls that return a host value (a norm, a
+ * gradient, an info struct) synchronise that stream once per iteration.
+ *
+ * Errors.  Every int-returning call returns an st_status.  No call aborts,
+ * exits or traps; on a CUDA error the handle should be destroyed.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_INVALID_ARG = 1,   /* bad size, pointer or option */
+  ST_ERR_OOM = 2,           /* the allocator returned NULL */
+  ST_ERR_CUDA = 3,          /* a CUDA runtime error (see st_last_error) */
+  ST_ERR_NOT_CONVERGED = 4, /* max_iters reached ("n.c." of Section 5.2) */
+  ST_ERR_DIVERGED = 5,      /* non-finite or growing residual ("n.c.") */
+  ST_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait expired */
+  ST_ERR_UNSUPPORTED = 7    /* valid input the library does not handle */
+} st_status;
+
+enum { ST_BC_DIRICHLET = 0, ST_BC_PERIODIC = 1, ST_BC_NEUMANN = 2 };
+/* R(u): NONE 0; LOGISTIC rho*u*(1-u); CUBIC rho*u*(1-u^2), which is the
+ * paper's -gamma*(u^3 - u) of Eq. (3.1)/(3.7) with gamma = rho. */
+enum { ST_REACTION_NONE = 0, ST_REACTION_LOGISTIC = 1, ST_REACTION_CUBIC = 2 };
+/* FP64: every level in double.  FP32_REFINE: the multigrid cycle, smoother,
+ * transfers and coarse solve in float inside an FP64 residual / update. */
+enum { ST_PREC_FP64 = 0, ST_PREC_FP32_REFINE = 1 };
+/* Level hierarchy of Eq. (4.1): SPACE = SMG (space bisection only, Section
+ * 5.2); AUTO_MU = per level, bisect space if mu_l = nu*dt_l/h_l^2 >= mu_crit,
+ * else bisect the slabs (the mu rule of Section 4.2). */
+enum { ST_COARSEN_SPACE = 0, ST_COARSEN_AUTO_MU = 1 };
+/* SDC lower-triangular preconditioner: implicit Euler node to node, or the
+ * LU trick (Q^T = L U, QI = U^T). */
+enum { ST_SDC_IE = 0, ST_SDC_LU = 1 };
+
+#define ST_MAX_M 5
+#define ST_MAX_LEVELS 32
+#define ST_MAX_HISTORY 64
+
+typedef struct {
+  int d;            /* 1, 2 or 3 */
+  int n[3];         /* points per axis, n[0] = x (fastest); unused axes 1 */
+  int bc;           /* ST_BC_* (same on every face) */
+  double X;         /* domain length per axis */
+  double nu;        /* diffusion coefficient (> 0) */
+  int reaction;     /* ST_REACTION_* */
+  double rho;       /* reaction rate */
+  double T;         /* final time */
+  int Nt;           /* slabs */
+  int M;            /* right-Radau nodes per slab, 1..5 */
+  const double* u0; /* initial value, n[0]*n[1]*n[2] doubles (host or device);
+                       copied at st_create */
+} st_problem;
+
+typedef struct {
+  int precision;        /* ST_PREC_*, default FP32_REFINE */
+  int coarsening;       /* ST_COARSEN_*, default AUTO_MU */
+  int max_levels;       /* default ST_MAX_LEVELS */
+  int nu1, nu2;         /* pre/post smoothing steps, default 1, 1 */
+  double omega;         /* block-Jacobi damping; <= 0: per level from mu_l
+                           (1.0 if mu_l >= 16, 0.8 if mu_l >= mu_crit, else 0.5) */
+  double mu_crit;       /* default 1.0 */
+  int inner_cycles;     /* spatial multigrid cycles per slab solve, default 1 */
+  int inner_smooth;     /* Jacobi sweeps per inner level and side, default 1 */
+  int inner_coarse_iters; /* Jacobi sweeps on the coarsest inner grid, default 8 */
+  int coarse_max_points;  /* stop space coarsening at <= this many points, default 16 */
+  int coarse_max_slabs;   /* AUTO_MU: stop time coarsening at <= this many slabs, default 4 */
+  int sdc_qdelta;       /* ST_SDC_*, default IE */
+  int sdc_inner_cycles; /* spatial multigrid cycles per SDC node solve, default 2 */
+  double tol;           /* relative residual ||G(U)|| / ||G(0)|| target, default 1e-8 */
+  int max_iters;        /* default 1000 (Section 5.2) */
+  int newton;           /* 1: relinearise (cbar from the current U) every
+                           iteration; 0: keep the first linearisation */
+  int use_graphs;       /* 1 (default): replay the cycle as a CUDA graph */
+} st_solver_opts;
+
+/* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
+ * return memory usable on `stream`, aligned to 256 bytes, or NULL.  With
+ * alloc == NULL the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef void* (*st_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*st_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+typedef struct {
+  void* stream;     /* cudaStream_t; NULL = legacy default stream */
+  st_alloc_fn alloc;
+  st_free_fn free;
+  void* ctx;
+} st_runtime;
+
+typedef struct {
+  int iterations;          /* outer iterations performed */
+  int status;              /* st_status of the call */
+  double rel_residual;     /* final ||G(U)|| / ||G(0)|| (adjoint: / ||g||) */
+  double abs_residual;     /* final ||G(U)||_2 */
+  double ref_norm;         /* ||G(0)||_2 = sqrt(M) ||u0||_2 (adjoint: ||g||) */
+  double seconds;          /* wall time of the call */
+  int history_len;
+  double history[ST_MAX_HISTORY]; /* relative residual per iteration */
+} st_solve_info;
+
+typedef struct {
+  int n[3];
+  long long Ns;       /* points per plane */
+  int Nt;             /* slabs */
+  double dt, h[3], mu;
+  int next_kind;      /* 0 coarsest, 1 space bisection, 2 slab bisection */
+  double omega;       /* damping used on this level */
+  int inner_levels;   /* spatial multigrid depth of the slab solves */
+} st_level_info;
+
+typedef struct {
+  int levels;
+  st_level_info level[ST_MAX_LEVELS];
+  size_t workspace_bytes;   /* device bytes st_create allocates */
+  int coarse_points;        /* points of the coarsest grid */
+} st_plan_info;
+
+typedef struct st_handle st_handle;
+
+/* Fill *o with the defaults listed above. */
+void st_default_opts(st_solver_opts* o);
+
+/* Level hierarchy and workspace size for (p, o) without touching a GPU.
+ * Errors: ST_ERR_INVALID_ARG for an invalid problem or options;
+ * ST_ERR_UNSUPPORTED if the grid does not coarsen to a small coarsest grid. */
+int st_plan(const st_problem* p, const st_solver_opts* o, st_plan_info* out);
+
+/* Create a handle: collocation setup (right-Radau nodes, Q, eigen-
+ * decomposition of Q; Section 2.1), level hierarchy, workspace allocation,
+ * copy of u0.  o may be NULL (defaults), rt may be NULL (default stream,
+ * cudaMallocAsync).  *out is NULL on failure. */
+int st_create(const st_problem* p, const st_solver_opts* o, const st_runtime* rt,
+              st_handle** out);
+
+/* Release the workspace (stream-ordered) and the handle.  NULL is allowed. */
+void st_destroy(st_handle* h);
+
+/* Replace nu and rho (e.g. for finite differences or a new parameter point);
+ * the next call relinearises. */
+int st_set_params(st_handle* h, double nu, double rho);
+
+/* Replace the initial value u0 (Ns doubles, host or device). */
+int st_set_u0(st_handle* h, const double* u0);
+
+/* Collocation residual (*) in FP64 at U (Eq. 2.3 on every slab, Eq. 3.4
+ * coupling).  R receives G(U) in the handle's cycle precision (float for
+ * FP32_REFINE, double for FP64) unless R_is_fp64 = 1 (always double); R may
+ * be NULL.  norm_out (may be NULL) receives ||G(U)||_2 computed in FP64 with
+ * a fixed reduction order. */
+int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* norm_out);
+
+/* One outer iteration: r = G(U) (FP64), linearise (cbar_n = mean_m R'(U_n,m)
+ * on every level), one space-time V-cycle on A e - C e = r (damped block
+ * Jacobi in time with Q-diagonalised spatial multigrid slab solves, space /
+ * slab bisection transfers, exact forward substitution on the coarsest
+ * level; Section 4.2), then U += e.  norm_out receives ||G(U)|| before the
+ * update. */
+int st_vcycle(st_handle* h, double* U, double* norm_out);
+
+/* nsweeps IMEX SDC sweeps on all slabs at once (Section 4.1; reaction
+ * explicit, diffusion implicit as in Section 5.4), in correction form on
+ * top of the FP64 residual: slab n starts from the previous iterate's last
+ * node of slab n-1.  norm_out receives ||G(U)|| before the last sweep. */
+int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out);
+
+/* Solve G(U) = 0 from the given U (zero initial guess in the paper, Section
+ * 5.2) by V-cycles inside FP64 defect correction (Newton with the averaged
+ * reaction derivative for R != 0) until ||G(U)||/||G(0)|| <= tol.
+ * Returns ST_ERR_NOT_CONVERGED / ST_ERR_DIVERGED with info filled. */
+int st_solve(st_handle* h, double* U, st_solve_info* info);
+
+/* Discrete adjoint at a converged U (not in the paper; derived from (*)).
+ * Objective Phi = 1/2 h^d sum_x (u_{Nt,M} - u_target)^2.  Solves
+ * J^T lambda = -dPhi/dU backward in time with the transposed V-cycle and
+ * FP64 refinement, then returns dPhi/dnu, dPhi/drho (host doubles, may be
+ * NULL) and dPhi/du0 (Ns doubles, host or device, may be NULL).
+ * ST_ERR_UNSUPPORTED for NEUMANN (non-symmetric Delta_h). */
+int st_adjoint_solve(st_handle* h, const double* U, const double* u_target,
+                     double* dnu, double* drho, double* du0, st_solve_info* info);
+
+/* Same with an arbitrary terminal gradient gT = dPhi/du_{Nt,M} (Ns doubles). */
+int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT,
+                              double* dnu, double* drho, double* du0,
+                              st_solve_info* info);
+
+const char* st_status_str(int status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* st_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Setup values and level-wise diagnostics (device pointers only).  They
+ * expose the individual hot-path steps for testing against a reference.
+ * Vectors at level l have Nt_l * M * Ns_l elements in the cycle precision
+ * (float for FP32_REFINE, double for FP64).
+ * ------------------------------------------------------------------- */
+
+/* Right-Radau nodes tau[M] and Q[M*M] (row major) on the unit interval
+ * (Section 2.1), eigenvalues lam[M] (re, im pairs: 2M doubles), eigenvector
+ * matrix V and its inverse (row major, complex as re/im pairs: 2M*M doubles
+ * each), ordered: real eigenvalues first, then each complex eigenvalue with
+ * Im > 0 followed by its conjugate.  Any output may be NULL. */
+int st_collocation(int M, double* tau, double* Q, double* lam, double* V, double* Vinv);
+
+/* Time transfer matrices used for slab bisection: P_t (2M x M) and R_t
+ * (M x 2M), row major (Eq. 4.1; the restriction acts through the DG form,
+ * R_t = K^{-1} P_t^T blockdiag(K, K)). */
+int st_time_transfer(int M, double* Pt, double* Rt);
+
+int st_num_levels(const st_handle* h);
+int st_level_info_get(const st_handle* h, int level, st_level_info* out);
+
+/* Linearise at U: cbar_0 = mean_m R'(U_{n,m}) and its restrictions to every
+ * level, plus the coarsest-level factorisation. */
+int st_linearize(st_handle* h, const double* U);
+
+/* cbar of level l into out (Nt_l * Ns_l floats/doubles per precision). */
+int st_level_cbar(st_handle* h, int level, void* out);
+
+/* out = r - A_l e + C e at level l (transpose = 1: r - A_l^T e + C^T e). */
+int st_level_residual(st_handle* h, int level, int transpose, const void* e,
+                      const void* r, void* out);
+
+/* One damped block-Jacobi-in-time smoothing step at level l, in place on e. */
+int st_level_smooth(st_handle* h, int level, int transpose, void* e, const void* r);
+
+/* coarse = restriction of fine (level l -> l+1). */
+int st_level_restrict(st_handle* h, int level, int transpose, const void* fine, void* coarse);
+
+/* fine += prolongation of coarse (level l+1 -> l). */
+int st_level_prolong(st_handle* h, int level, int transpose, const void* coarse, void* fine);
+
+/* Exact solve of A_L e - C e = r on the coarsest level (transpose = 1:
+ * A_L^T e - C^T e = r, backward in time). */
+int st_coarse_solve(st_handle* h, int transpose, const void* r, void* e);
+
+/* One V-cycle on the linear level-0 problem A e - C e = r with zero start
+ * (e overwritten). */
+int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e);
+
+/* ---------------------------------------------------------------------
+ * Measurement
+ * ------------------------------------------------------------------- */
+
+enum {
+  ST_KERNEL_FINE_RESIDUAL = 0, /* FP64 residual G(U) -> cycle precision + cbar */
+  ST_KERNEL_LEVEL_RESIDUAL = 1,/* level-0 residual r - A e + C e with the Q-eigenbasis transform */
+  ST_KERNEL_JACOBI = 2,        /* one Jacobi sweep of the level-0 shifted slab systems */
+  ST_KERNEL_BACKTRANSFORM = 3, /* level-0 back-transform + damped block-Jacobi update */
+  ST_KERNEL_VCYCLE = 4         /* one whole V-cycle (graph replay), not a single kernel */
+};
+
+/* Launch kernel `which` `iters` times back to back on the handle's stream
+ * between two CUDA events (after one untimed launch) and return the mean
+ * duration per launch in milliseconds, plus the algorithmic bytes one launch
+ * must move (each input read once, each output written once).  U (device,
+ * Nt*M*Ns doubles) is the input of ST_KERNEL_FINE_RESIDUAL; the other kernels
+ * run on the handle's level-0 work buffers (contents unspecified). */
+int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
+                   double* bytes_per_launch);
+
+typedef struct {
+  int levels;
+  int cycle_graph_nodes;        /* kernel + memset nodes of one V-cycle */
+  int linearize_graph_nodes;    /* nodes of one relinearisation */
+  int launches_per_vcycle;      /* all launches of one st_vcycle call */
+} st_stats_info;
+
+/* Launch counts of the captured graphs (0 before the first st_vcycle). */
+int st_stats(st_handle* h, st_stats_info* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H */

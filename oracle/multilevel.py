@@ -76,6 +76,40 @@ def linear_residual(lev: Level, e: np.ndarray, r: np.ndarray) -> np.ndarray:
     return r.reshape(lev.Nt, lev.M, lev.Ns) - apply_A(lev, e) + coupling(lev, e)
 
 
+def apply_AT(lev: Level, e: np.ndarray) -> np.ndarray:
+    """A_l^T e: (A^T e)_j = e_j - dt_l sum_m Q_mj (L_l + diag cbar_n) e_m
+    (L_l symmetric for DIRICHLET and PERIODIC)."""
+    e = e.reshape(lev.Nt, lev.M, lev.Ns)
+    Fe = _apply_L(lev.L.T.tocsr(), e) + lev.cbar[:, None, :] * e
+    return e - lev.dt * np.einsum("mj,nms->njs", lev.Q, Fe)
+
+
+def coupling_T(lev: Level, e: np.ndarray) -> np.ndarray:
+    """(C^T e)_n: the last node of slab n receives sum_m e_{n+1,m}."""
+    e = e.reshape(lev.Nt, lev.M, lev.Ns)
+    out = np.zeros_like(e)
+    out[:-1, -1, :] = e[1:].sum(axis=1)
+    return out
+
+
+def linear_residual_T(lev: Level, e: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """r - A_l^T e + C^T e (the transposed level system of the adjoint)."""
+    return r.reshape(lev.Nt, lev.M, lev.Ns) - apply_AT(lev, e) + coupling_T(lev, e)
+
+
+def coarse_solve_exact_T(lev: Level, r: np.ndarray) -> np.ndarray:
+    """Exact solution of A_l^T e - C^T e = r by backward substitution."""
+    r = r.reshape(lev.Nt, lev.M, lev.Ns)
+    e = np.zeros_like(r)
+    nxt = np.zeros(lev.Ns)
+    for n in range(lev.Nt - 1, -1, -1):
+        rhs = r[n].copy()
+        rhs[-1] += nxt
+        e[n] = spla.spsolve(slab_matrix(lev, n).T.tocsc(), rhs.ravel()).reshape(lev.M, lev.Ns)
+        nxt = e[n].sum(axis=0)
+    return e
+
+
 def slab_matrix(lev: Level, n: int) -> sp.csc_matrix:
     """A_{l,n} = I - dt_l Q (x) (L_l + diag cbar_{l,n}) as a sparse matrix."""
     Ln = lev.L + sp.diags(lev.cbar[n])

@@ -100,6 +100,44 @@ def residual(p: Problem, U: np.ndarray, u0: np.ndarray) -> np.ndarray:
     return previous_node(p, U, u0)[:, None, :] + p.dt * QF - U
 
 
+def residual_points(p: Problem, U: np.ndarray, u0: np.ndarray, slabs, points) -> np.ndarray:
+    """G_{n,m}(s) for the listed (slab n, point s) pairs and every node m,
+    evaluated one point at a time from the stencil definition (any problem
+    size; no global operator is formed).  Returns shape (len(slabs), M)."""
+    U = U.reshape(p.Nt, p.M, p.Ns)
+    shape = p.shape
+    d = len(shape)
+    hs = [space.spacing(p.bc, n, p.X) for n in shape]
+    strides = [int(np.prod(shape[a + 1:])) for a in range(d)]
+    out = np.zeros((len(slabs), p.M))
+    for t, (n, s) in enumerate(zip(slabs, points)):
+        idx = np.unravel_index(int(s), shape)
+        Fv = np.zeros(p.M)
+        for j in range(p.M):
+            plane = U[n, j]
+            c = plane[s]
+            lap = 0.0
+            for a in range(d):
+                vals = []
+                for di in (-1, 1):
+                    q = idx[a] + di
+                    if 0 <= q < shape[a]:
+                        vals.append(plane[s + di * strides[a]])
+                    elif p.bc == space.PERIODIC:
+                        q %= shape[a]
+                        vals.append(plane[s + (q - idx[a]) * strides[a]])
+                    elif p.bc == space.NEUMANN:
+                        q = 1 if q < 0 else shape[a] - 2
+                        vals.append(plane[s + (q - idx[a]) * strides[a]])
+                    else:
+                        vals.append(0.0)
+                lap += (vals[0] + vals[1] - 2 * c) / hs[a] ** 2
+            Fv[j] = p.nu * lap + float(p.R(np.array([c]))[0])
+        prev = u0.reshape(-1)[s] if n == 0 else U[n - 1, -1, s]
+        out[t] = prev + p.dt * (p.Q @ Fv) - U[n, :, s]
+    return out
+
+
 def residual_norm(p: Problem, U, u0) -> float:
     return float(np.linalg.norm(residual(p, U, u0).ravel()))
 
@@ -159,6 +197,27 @@ def full_jacobian_dense(p: Problem, U: np.ndarray) -> np.ndarray:
 
 # ------------------------------------------------------------------ solves
 
+_DIRECT_MAX = 20000  # slab systems up to this size use sparse LU, larger ones GMRES
+
+
+class _SlabSolver:
+    """Linear solves with one slab Jacobian: sparse LU for small systems;
+    restarted GMRES(50) to a 1e-14 relative residual for large ones (the slab
+    matrix I - dt Q (x) (L + D) is well conditioned for these step sizes)."""
+
+    def __init__(self, A):
+        self.A = A
+        self.lu = spla.splu(A) if A.shape[0] <= _DIRECT_MAX else None
+
+    def solve(self, b):
+        if self.lu is not None:
+            return self.lu.solve(b)
+        x, info = spla.gmres(self.A, b, rtol=1e-14, atol=0.0, restart=50, maxiter=200)
+        if info != 0:
+            x = spla.spsolve(self.A, b)
+        return x
+
+
 def _newton_slab(p: Problem, prev: np.ndarray, guess: np.ndarray, lu_cache: dict | None,
                  tol: float = 1e-14, maxit: int = 40) -> np.ndarray:
     """Newton's method on G_n(U_n) = 0 for one slab given u_{n-1,M} = prev
@@ -180,10 +239,10 @@ def _newton_slab(p: Problem, prev: np.ndarray, guess: np.ndarray, lu_cache: dict
             break
         if linear and lu_cache is not None:
             if "lu" not in lu_cache:
-                lu_cache["lu"] = spla.splu(slab_jacobian(p, Un))
+                lu_cache["lu"] = _SlabSolver(slab_jacobian(p, Un))
             lu = lu_cache["lu"]
         else:
-            lu = spla.splu(slab_jacobian(p, Un))
+            lu = _SlabSolver(slab_jacobian(p, Un))
         delta = lu.solve(-g.ravel()).reshape(M, Ns)
         if linear:
             Un = Un + delta

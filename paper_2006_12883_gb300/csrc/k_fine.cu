@@ -1,0 +1,325 @@
+// FP64 fine-level kernels: the collocation residual G(U) (Eq. 2.3 chained by
+// the slab coupling of Eq. 3.4), its adjoint, parameter gradients, FP64
+// reductions, the U update and the SDC right-hand side.
+//
+// Thread mapping: one thread owns one spatial point s for a run of `chunk`
+// consecutive slabs, so the coupling plane u_{n-1,M} is carried in a
+// register from one slab to the next; consecutive threads own consecutive
+// points (coalesced along x).  The per-block partial sums depend only on this
+// fixed mapping, so norms are bitwise reproducible.
+#include "st_kernels.cuh"
+
+namespace st {
+
+// ---------------------------------------------------------------------------
+// K1: r = G(U),  cbar_n = mean_m R'(U_{n,m}),  partial sums of G^2.
+// ---------------------------------------------------------------------------
+template <int D, typename TR, typename TC>
+__global__ void __launch_bounds__(256) k_residual(ResidParams p) {
+  const long long Ns = p.g.Ns;
+  const int M = p.M;
+  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (idx < Ns * nchunks) {
+    const long long s = idx % Ns;
+    const int c = (int)(idx / Ns);
+    const int n0 = c * p.chunk;
+    const int n1 = min(n0 + p.chunk, p.Nt);
+    int i, j, k;
+    decompose(s, p.g, i, j, k);
+    const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
+    double prev = (n0 == 0) ? p.u0[s] : p.U[((long long)(n0 - 1) * M + (M - 1)) * Ns + s];
+    TR* R = (TR*)p.R;
+    TC* cb = (TC*)p.cbar;
+    for (int n = n0; n < n1; ++n) {
+      double u[MAXM], F[MAXM];
+      double cbs = 0.0;
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          const double* pl = p.U + ((long long)n * M + m) * Ns;
+          const double um = pl[s];
+          u[m] = um;
+          F[m] = p.nu * lap_at<D, double, double>(pl, s, i, j, k, p.g, um, ihx, ihy, ihz) +
+                 react<double>(p.reaction, p.rho, um);
+          cbs += dreact<double>(p.reaction, p.rho, um);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          double acc = 0.0;
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < M) acc += p.dtq[m][q] * F[q];
+          const double g = (prev - u[m]) + acc;
+          sq += g * g;
+          if (R) R[((long long)n * M + m) * Ns + s] = (TR)g;
+        }
+      }
+      if (cb) cb[(long long)n * Ns + s] = (TC)(cbs / M);
+      prev = u[M - 1];
+    }
+  }
+  if (p.partial) {
+    const double t = block_sum(sq);
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint residual rho = g - A^T lambda + C^T lambda with the exact Jacobian:
+//   rho_{n,j} = g_{n,j} - lambda_{n,j}
+//             + sum_m dtq[j][m] (nu*Lap lambda_{n,m}) + R'(U_{n,j}) sum_m dtq[j][m] lambda_{n,m}
+//             + [j = M-1] sum_m lambda_{n+1,m}
+// (dtq holds dt*Q^T).  Marches backward through its chunk of slabs.
+// ---------------------------------------------------------------------------
+template <int D, typename TR>
+__global__ void __launch_bounds__(256) k_adj_residual(ResidParams p) {
+  const long long Ns = p.g.Ns;
+  const int M = p.M;
+  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (idx < Ns * nchunks) {
+    const long long s = idx % Ns;
+    const int c = (int)(idx / Ns);
+    const int n0 = c * p.chunk;
+    const int n1 = min(n0 + p.chunk, p.Nt);
+    int i, j, k;
+    decompose(s, p.g, i, j, k);
+    const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
+    double next = 0.0;  // sum_m lambda_{n+1,m}
+    if (n1 < p.Nt) {
+      for (int m = 0; m < M; ++m) next += p.lam[((long long)n1 * M + m) * Ns + s];
+    }
+    TR* R = (TR*)p.R;
+    for (int n = n1 - 1; n >= n0; --n) {
+      double l[MAXM], Ll[MAXM];
+      double sum = 0.0;
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          const double* pl = p.lam + ((long long)n * M + m) * Ns;
+          const double lm = pl[s];
+          l[m] = lm;
+          Ll[m] = p.nu * lap_at<D, double, double>(pl, s, i, j, k, p.g, lm, ihx, ihy, ihz);
+          sum += lm;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < MAXM; ++a) {
+        if (a < M) {
+          double accL = 0.0, accl = 0.0;
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m)
+            if (m < M) {
+              accL += p.dtq[a][m] * Ll[m];
+              accl += p.dtq[a][m] * l[m];
+            }
+          double rp = 0.0;
+          if (p.reaction != ST_REACTION_NONE)
+            rp = dreact<double>(p.reaction, p.rho, p.U[((long long)n * M + a) * Ns + s]);
+          double g = accL + rp * accl - l[a];
+          if (a == M - 1) {
+            g += next;
+            if (n == p.Nt - 1 && p.gT) g += p.gT[s];
+          }
+          sq += g * g;
+          if (R) R[((long long)n * M + a) * Ns + s] = (TR)g;
+        }
+      }
+      next = sum;
+    }
+  }
+  if (p.partial) {
+    const double t = block_sum(sq);
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradients lambda^T dG/dtheta: per block partial sums of
+//   dnu:  sum_j (dt Q^T lambda_n)_j * Lap U_{n,j}
+//   drho: sum_j (dt Q^T lambda_n)_j * r(U_{n,j})
+// and du0 = sum_m lambda_{0,m} (written by the threads of slab 0).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) k_gradients(ResidParams p, double* partial2, double* du0) {
+  const long long Ns = p.g.Ns;
+  const int M = p.M;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double gnu = 0.0, grho = 0.0;
+  if (idx < Ns * p.Nt) {
+    const long long s = idx % Ns;
+    const int n = (int)(idx / Ns);
+    int i, j, k;
+    decompose(s, p.g, i, j, k);
+    const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
+    double l[MAXM];
+    double sum = 0.0;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m)
+      if (m < M) {
+        l[m] = p.lam[((long long)n * M + m) * Ns + s];
+        sum += l[m];
+      }
+#pragma unroll
+    for (int a = 0; a < MAXM; ++a) {
+      if (a < M) {
+        double qt = 0.0;
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m)
+          if (m < M) qt += p.dtq[a][m] * l[m];
+        const double* pl = p.U + ((long long)n * M + a) * Ns;
+        const double ua = pl[s];
+        gnu += qt * lap_at<D, double, double>(pl, s, i, j, k, p.g, ua, ihx, ihy, ihz);
+        grho += qt * rshape<double>(p.reaction, ua);
+      }
+    }
+    if (n == 0 && du0) du0[s] = sum;
+  }
+  const double t1 = block_sum(gnu);
+  if (threadIdx.x == 0) p.partial[blockIdx.x] = t1;
+  const double t2 = block_sum(grho);
+  if (threadIdx.x == 0) partial2[blockIdx.x] = t2;
+}
+
+// Sum n partials in a fixed order into out[0] (single block of 1024).
+__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ part, long long n,
+                                                       double* out) {
+  double v = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[0] = v;
+}
+
+// U += e (e in the cycle precision), optionally scaled.
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ U, const T* __restrict__ e,
+                                                long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) U[i] += (double)e[i];
+}
+
+// ---------------------------------------------------------------------------
+// SDC right-hand side for node m (correction form):
+//   y = g_m + sum_{j<m} [ dt*QI_mj*nu*Lap delta_j + dt*QE_mj*(R(U_j + delta_j) - R(U_j)) ]
+// g is G(U^k) (cycle precision), delta holds the corrections of nodes < m.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, double nu, int reaction,
+                                                 double rho, SdcCoef cf,
+                                                 const T* __restrict__ G, const T* __restrict__ delta,
+                                                 const double* __restrict__ U, T* __restrict__ y) {
+  const long long Ns = g.Ns;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * Nt) return;
+  const long long s = idx % Ns;
+  const int n = (int)(idx / Ns);
+  int i, j, k;
+  decompose(s, g, i, j, k);
+  const double ihx = g.ih2[0], ihy = g.ih2[1], ihz = g.ih2[2];
+  double acc = (double)G[((long long)n * M + m) * Ns + s];
+  for (int q = 0; q < m; ++q) {
+    const T* pl = delta + ((long long)n * M + q) * Ns;
+    const double dq = (double)pl[s];
+    acc += cf.qi[q] * nu * lap_at<D, T, double>(pl, s, i, j, k, g, dq, ihx, ihy, ihz);
+    if (reaction != ST_REACTION_NONE) {
+      const double uq = U[((long long)n * M + q) * Ns + s];
+      acc += cf.qe[q] * (react<double>(reaction, rho, uq + dq) - react<double>(reaction, rho, uq));
+    }
+  }
+  y[(long long)n * Ns + s] = (T)acc;
+}
+
+// Copy a [Nt][Ns] field into plane m of a [Nt][M][Ns] field.
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_plane(const T* __restrict__ src, T* __restrict__ dst,
+                                                       long long Ns, int Nt, int M, int m) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * Nt) return;
+  const long long s = idx % Ns;
+  const long long n = idx / Ns;
+  dst[(n * M + m) * Ns + s] = src[idx];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+long long residual_blocks(const ResidParams& p) {
+  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
+  return (p.g.Ns * nchunks + 255) / 256;
+}
+
+template <typename TR, typename TC>
+static void launch_res_t(int D, const ResidParams& p, cudaStream_t st) {
+  const unsigned nb = (unsigned)residual_blocks(p);
+  if (D == 1) k_residual<1, TR, TC><<<nb, 256, 0, st>>>(p);
+  else if (D == 2) k_residual<2, TR, TC><<<nb, 256, 0, st>>>(p);
+  else k_residual<3, TR, TC><<<nb, 256, 0, st>>>(p);
+}
+
+void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st) {
+  if (r_fp64 && c_fp64) launch_res_t<double, double>(D, p, st);
+  else if (r_fp64) launch_res_t<double, float>(D, p, st);
+  else launch_res_t<float, float>(D, p, st);
+}
+
+void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st) {
+  const unsigned nb = (unsigned)residual_blocks(p);
+  if (r_fp64) {
+    if (D == 1) k_adj_residual<1, double><<<nb, 256, 0, st>>>(p);
+    else if (D == 2) k_adj_residual<2, double><<<nb, 256, 0, st>>>(p);
+    else k_adj_residual<3, double><<<nb, 256, 0, st>>>(p);
+  } else {
+    if (D == 1) k_adj_residual<1, float><<<nb, 256, 0, st>>>(p);
+    else if (D == 2) k_adj_residual<2, float><<<nb, 256, 0, st>>>(p);
+    else k_adj_residual<3, float><<<nb, 256, 0, st>>>(p);
+  }
+}
+
+long long gradient_blocks(const ResidParams& p) { return (p.g.Ns * p.Nt + 255) / 256; }
+
+void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st) {
+  const unsigned nb = (unsigned)gradient_blocks(p);
+  if (D == 1) k_gradients<1><<<nb, 256, 0, st>>>(p, partial2, du0);
+  else if (D == 2) k_gradients<2><<<nb, 256, 0, st>>>(p, partial2, du0);
+  else k_gradients<3><<<nb, 256, 0, st>>>(p, partial2, du0);
+}
+
+void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 1024, 0, st>>>(part, n, out);
+}
+
+void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st) {
+  if (fp64) k_update<double><<<blocks_for(n, 256), 256, 0, st>>>(U, (const double*)e, n);
+  else k_update<float><<<blocks_for(n, 256), 256, 0, st>>>(U, (const float*)e, n);
+}
+
+void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,
+                    double rho, const SdcCoef& cf, const void* G, const void* delta,
+                    const double* U, void* y, cudaStream_t st) {
+  const unsigned nb = blocks_for(g.Ns * Nt, 256);
+#define SDC_L(DD, TT)                                                                              \
+  k_sdc_rhs<DD, TT><<<nb, 256, 0, st>>>(g, Nt, M, m, nu, reaction, rho, cf, (const TT*)G,     \
+                                        (const TT*)delta, U, (TT*)y)
+  if (fp64) {
+    if (D == 1) SDC_L(1, double); else if (D == 2) SDC_L(2, double); else SDC_L(3, double);
+  } else {
+    if (D == 1) SDC_L(1, float); else if (D == 2) SDC_L(2, float); else SDC_L(3, float);
+  }
+#undef SDC_L
+}
+
+void launch_scatter_plane(int fp64, const void* src, void* dst, long long Ns, int Nt, int M, int m,
+                          cudaStream_t st) {
+  const unsigned nb = blocks_for(Ns * Nt, 256);
+  if (fp64) k_scatter_plane<double><<<nb, 256, 0, st>>>((const double*)src, (double*)dst, Ns, Nt, M, m);
+  else k_scatter_plane<float><<<nb, 256, 0, st>>>((const float*)src, (float*)dst, Ns, Nt, M, m);
+}
+
+}  // namespace st

@@ -1,0 +1,1464 @@
+// C ABI of the space-time multigrid / SDC library: handle, level hierarchy,
+// workspace, the V-cycle / SDC / adjoint drivers and CUDA-graph replay.
+// See include/st.h for the contract of every entry point.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "st_kernels.cuh"
+#include "st_setup.h"
+
+using namespace st;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(cudaError_t e, const char* what) {
+  snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      set_err(e_, #x);                          \
+      return ST_ERR_CUDA;                       \
+    }                                           \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+#define TRY(x)                \
+  do {                        \
+    int s_ = (x);             \
+    if (s_ != ST_OK) return s_; \
+  } while (0)
+
+struct InnerLev {
+  GridP g;
+  void* y = nullptr;
+  void* z = nullptr;
+  void* t = nullptr;
+  void* cbar = nullptr;
+};
+
+struct Level {
+  GridP g;
+  int Nt = 0;
+  double dt = 0, mu = 0, omega = 1;
+  int next = 0;  // 0 coarsest, 1 space, 2 slabs
+  void* e = nullptr;
+  void* r = nullptr;
+  void* cbar = nullptr;
+  std::vector<InnerLev> in;
+};
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+double spacing(int bc, int n, double X) {
+  if (bc == ST_BC_DIRICHLET) return X / (n + 1);
+  if (bc == ST_BC_PERIODIC) return X / n;
+  return X / (n - 1);
+}
+
+GridP make_grid(int d, const int n[3], int bc, double X) {
+  GridP g;
+  g.n0 = n[0];
+  g.n1 = d >= 2 ? n[1] : 1;
+  g.n2 = d >= 3 ? n[2] : 1;
+  g.bc = bc;
+  g.Ns = (long long)g.n0 * g.n1 * g.n2;
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  for (int a = 0; a < 3; ++a) {
+    if (a < d) {
+      const double h = spacing(bc, nn[a], X);
+      g.ih2[a] = 1.0 / (h * h);
+    } else {
+      g.ih2[a] = 0.0;
+    }
+  }
+  return g;
+}
+
+bool can_coarsen_axis(int bc, int n) {
+  if (bc == ST_BC_DIRICHLET) return n >= 3 && (n & 1);
+  if (bc == ST_BC_PERIODIC) return n >= 2 && !(n & 1);
+  return n >= 3 && !((n - 1) & 1);
+}
+
+int coarse_axis(int bc, int n) {
+  if (bc == ST_BC_DIRICHLET) return (n - 1) / 2;
+  if (bc == ST_BC_PERIODIC) return n / 2;
+  return (n - 1) / 2 + 1;
+}
+
+bool can_coarsen(int d, const GridP& g) {
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  for (int a = 0; a < d; ++a)
+    if (!can_coarsen_axis(g.bc, nn[a])) return false;
+  return true;
+}
+
+GridP coarsen(int d, const GridP& g, double X) {
+  int n[3] = {g.n0, g.n1, g.n2};
+  for (int a = 0; a < d; ++a) n[a] = coarse_axis(g.bc, n[a]);
+  return make_grid(d, n, g.bc, X);
+}
+
+const int kInnerCoarseMax = 8;     // stop inner coarsening at <= this many points
+const int kInnerCoarseLimit = 256; // largest grid the single-block kernel takes
+const int kCoarseKMax = 96;        // largest dense slab block M*Nc
+
+struct PlanLevel {
+  GridP g;
+  int Nt;
+  double dt, mu, omega;
+  int next;
+  std::vector<GridP> inner;
+};
+
+double default_omega(const st_solver_opts& o, double mu) {
+  if (o.omega > 0) return o.omega;
+  if (mu >= 16.0) return 1.0;
+  if (mu >= o.mu_crit) return 0.8;
+  return 0.5;
+}
+
+int validate(const st_problem* p, const st_solver_opts* o) {
+  if (!p) return ST_ERR_INVALID_ARG;
+  if (p->d < 1 || p->d > 3) return ST_ERR_INVALID_ARG;
+  for (int a = 0; a < p->d; ++a) {
+    if (p->n[a] < 1) return ST_ERR_INVALID_ARG;
+    if (p->bc == ST_BC_NEUMANN && p->n[a] < 2) return ST_ERR_INVALID_ARG;
+  }
+  if (p->bc < 0 || p->bc > 2) return ST_ERR_INVALID_ARG;
+  if (p->reaction < 0 || p->reaction > 2) return ST_ERR_INVALID_ARG;
+  if (!(p->X > 0) || !(p->T > 0) || !(p->nu > 0) || !std::isfinite(p->rho)) return ST_ERR_INVALID_ARG;
+  if (p->Nt < 1 || p->M < 1 || p->M > ST_MAX_M) return ST_ERR_INVALID_ARG;
+  if (o) {
+    if (o->precision != ST_PREC_FP64 && o->precision != ST_PREC_FP32_REFINE) return ST_ERR_INVALID_ARG;
+    if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU) return ST_ERR_INVALID_ARG;
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) return ST_ERR_INVALID_ARG;
+    if (o->inner_cycles < 1 || o->inner_smooth < 1 || o->inner_coarse_iters < 1) return ST_ERR_INVALID_ARG;
+    if (o->sdc_inner_cycles < 1 || o->max_iters < 0 || !(o->tol >= 0)) return ST_ERR_INVALID_ARG;
+    if (o->max_levels < 1 || o->coarse_max_points < 1 || o->coarse_max_slabs < 1) return ST_ERR_INVALID_ARG;
+    if (o->sdc_qdelta != ST_SDC_IE && o->sdc_qdelta != ST_SDC_LU) return ST_ERR_INVALID_ARG;
+  }
+  return ST_OK;
+}
+
+int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLevel>& out) {
+  out.clear();
+  const int d = p->d;
+  PlanLevel L0;
+  L0.g = make_grid(d, p->n, p->bc, p->X);
+  L0.Nt = p->Nt;
+  L0.dt = p->T / p->Nt;
+  out.push_back(L0);
+  const int maxl = std::min(o.max_levels, ST_MAX_LEVELS);
+  while ((int)out.size() < maxl) {
+    PlanLevel& cur = out.back();
+    const bool cs = can_coarsen(d, cur.g);
+    const bool ct = (cur.Nt % 2 == 0) && cur.Nt >= 2;
+    const double mu = p->nu * cur.dt * cur.g.ih2[0];
+    int kind = 0;
+    if (o.coarsening == ST_COARSEN_SPACE) {
+      if (cs && cur.g.Ns > o.coarse_max_points) kind = 1;
+    } else {
+      const bool small_s = cur.g.Ns <= o.coarse_max_points;
+      const bool small_t = cur.Nt <= o.coarse_max_slabs;
+      if (small_s && (small_t || !ct)) kind = 0;
+      else if (cs && !small_s && mu >= o.mu_crit) kind = 1;
+      else if (ct && !small_t) kind = 2;
+      else if (cs && !small_s) kind = 1;
+    }
+    if (kind == 0) break;
+    PlanLevel nx;
+    nx.Nt = cur.Nt;
+    nx.dt = cur.dt;
+    if (kind == 1) {
+      nx.g = coarsen(d, cur.g, p->X);
+    } else {
+      nx.g = cur.g;
+      nx.Nt = cur.Nt / 2;
+      nx.dt = cur.dt * 2;
+    }
+    cur.next = kind;
+    out.push_back(nx);
+  }
+  out.back().next = 0;
+  for (auto& L : out) {
+    L.mu = p->nu * L.dt * L.g.ih2[0];
+    L.omega = default_omega(o, L.mu);
+    L.inner.clear();
+    L.inner.push_back(L.g);
+    while (L.inner.back().Ns > kInnerCoarseMax && can_coarsen(d, L.inner.back()))
+      L.inner.push_back(coarsen(d, L.inner.back(), p->X));
+    if (L.inner.back().Ns > kInnerCoarseLimit) return ST_ERR_UNSUPPORTED;
+  }
+  if (out.back().g.Ns * p->M > kCoarseKMax) return ST_ERR_UNSUPPORTED;
+  return ST_OK;
+}
+
+size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct st_handle {
+  st_problem p;
+  st_solver_opts o;
+  st_runtime rt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  int D = 1, fp64 = 0;
+  size_t esz = 4;
+  Colloc col;
+  // shift groups of the Q-eigenbasis (real planes / complex pairs)
+  int ngroups = 0;
+  int gplane[MAXM], gcplx[MAXM];
+  std::complex<double> glam[MAXM];
+  double Ff[MAXM][MAXM], Bf[MAXM][MAXM], Fa[MAXM][MAXM], Ba[MAXM][MAXM];
+  double RtT[MAXM][2 * MAXM];  // P_t^T (adjoint restriction)
+  double PtT[2 * MAXM][MAXM];  // R_t^T (adjoint prolongation)
+  std::vector<Level> L;
+  // coarsest level
+  int Nc = 0, K = 0;
+  double* Lc = nullptr;
+  void *Ainv = nullptr, *Wf = nullptr, *Wt = nullptr, *Wfrow = nullptr, *Wtrow = nullptr, *cin = nullptr;
+  bool coarse_ready = false;
+  bool linearized = false;
+  // fine-level FP64 data
+  std::vector<double> u0_host;
+  double* u0 = nullptr;
+  double* partial = nullptr;
+  double* partial2 = nullptr;
+  long long npartial = 0;
+  double* scal = nullptr;   // device scalars
+  double* hscal = nullptr;  // pinned host scalars
+  double* Ustage = nullptr;
+  double* lam = nullptr;
+  double* plane = nullptr;  // staging for one plane (gT / target / du0)
+  double* plane2 = nullptr;
+  std::vector<Alloc> allocs;
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // 0 fwd cycle, 1 adjoint cycle, 2 linearise
+  size_t gnodes[3] = {0, 0, 0};
+  long long D_total = 0;
+  int chunk = 1;
+};
+
+namespace {
+
+void* dev_alloc(st_handle* h, size_t bytes) {
+  bytes = round_up(std::max<size_t>(bytes, 256));
+  void* p = nullptr;
+  if (h->rt.alloc) {
+    p = h->rt.alloc(bytes, (void*)h->stream, h->rt.ctx);
+  } else {
+    if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) p = nullptr;
+  }
+  if (p) h->allocs.push_back({p, bytes});
+  return p;
+}
+
+int alloc_into(st_handle* h, void** dst, size_t bytes) {
+  *dst = dev_alloc(h, bytes);
+  if (!*dst) {
+    cudaGetLastError();
+    return ST_ERR_OOM;
+  }
+  return ST_OK;
+}
+
+template <typename P>
+int alloc_typed(st_handle* h, P** dst, size_t bytes) {
+  void* v = nullptr;
+  int s = alloc_into(h, &v, bytes);
+  *dst = (P*)v;
+  return s;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void build_transforms(st_handle* h) {
+  const int M = h->p.M;
+  const Colloc& c = h->col;
+  // groups
+  h->ngroups = 0;
+  for (int q = 0; q < M;) {
+    h->gplane[h->ngroups] = q;
+    h->glam[h->ngroups] = c.lam[q];
+    if (c.lam[q].imag() == 0.0) {
+      h->gcplx[h->ngroups] = 0;
+      ++q;
+    } else {
+      h->gcplx[h->ngroups] = 1;
+      q += 2;
+    }
+    ++h->ngroups;
+  }
+  // forward (Q = V L V^-1): y = Vinv res, e += Re(V z);
+  // adjoint (Q^T = W L W^-1 with W = V^{-T}, W^{-1} = V^T)
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) h->Ff[a][b] = h->Bf[a][b] = h->Fa[a][b] = h->Ba[a][b] = 0;
+  for (int gq = 0; gq < h->ngroups; ++gq) {
+    const int p = h->gplane[gq];
+    for (int j = 0; j < M; ++j) {
+      const std::complex<double> fi = c.Vinv[p][j];   // forward row p of V^-1
+      const std::complex<double> ai = c.V[j][p];      // adjoint row p of V^T
+      const std::complex<double> fb = c.V[j][p];      // forward back-transform
+      const std::complex<double> ab = c.Vinv[p][j];   // adjoint back: (V^{-T})[j][p] = Vinv[p][j]
+      if (!h->gcplx[gq]) {
+        h->Ff[p][j] = fi.real();
+        h->Fa[p][j] = ai.real();
+        h->Bf[j][p] = fb.real();
+        h->Ba[j][p] = ab.real();
+      } else {
+        h->Ff[p][j] = fi.real();
+        h->Ff[p + 1][j] = fi.imag();
+        h->Fa[p][j] = ai.real();
+        h->Fa[p + 1][j] = ai.imag();
+        h->Bf[j][p] = 2 * fb.real();
+        h->Bf[j][p + 1] = -2 * fb.imag();
+        h->Ba[j][p] = 2 * ab.real();
+        h->Ba[j][p + 1] = -2 * ab.imag();
+      }
+    }
+  }
+  for (int m = 0; m < MAXM; ++m)
+    for (int kk = 0; kk < 2 * MAXM; ++kk) {
+      h->RtT[m][kk] = (m < M && kk < 2 * M) ? c.Pt[kk][m] : 0.0;
+      h->PtT[kk][m] = (m < M && kk < 2 * M) ? c.Rt[m][kk] : 0.0;
+    }
+}
+
+template <typename T>
+Shifts<T> level_shifts(const st_handle* h, double dt) {
+  Shifts<T> s;
+  s.ngroups = h->ngroups;
+  for (int q = 0; q < MAXM; ++q) {
+    s.plane[q] = q < h->ngroups ? h->gplane[q] : 0;
+    s.cplx[q] = q < h->ngroups ? h->gcplx[q] : 0;
+    s.sr[q] = q < h->ngroups ? (T)(dt * h->glam[q].real()) : (T)0;
+    s.si[q] = q < h->ngroups ? (T)(dt * h->glam[q].imag()) : (T)0;
+  }
+  return s;
+}
+
+double jacobi_weight(int d) { return d == 1 ? 2.0 / 3.0 : (d == 2 ? 0.8 : 6.0 / 7.0); }
+
+// ---------------------------------------------------------------------------
+// Inner spatial multigrid on the shifted slab systems of level l.
+// ---------------------------------------------------------------------------
+template <typename T>
+InnerParams<T> inner_params(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, bool use_cbar) {
+  InnerParams<T> ip;
+  InnerLev& I = Lv.in[k];
+  ip.g = I.g;
+  ip.gc = (k + 1 < (int)Lv.in.size()) ? Lv.in[k + 1].g : I.g;
+  ip.Nt = Lv.Nt;
+  ip.P = P;
+  ip.sh = sh;
+  ip.nu = (T)h->p.nu;
+  ip.omega = (T)jacobi_weight(h->D);
+  ip.cbar = use_cbar ? (const T*)I.cbar : nullptr;
+  ip.cbarc = (use_cbar && k + 1 < (int)Lv.in.size()) ? (const T*)Lv.in[k + 1].cbar : nullptr;
+  ip.y = (const T*)I.y;
+  ip.z = (const T*)I.z;
+  ip.zout = (T*)I.t;
+  ip.yc = (k + 1 < (int)Lv.in.size()) ? (T*)Lv.in[k + 1].y : nullptr;
+  ip.zc = (k + 1 < (int)Lv.in.size()) ? (T*)Lv.in[k + 1].z : nullptr;
+  ip.iters = h->o.inner_coarse_iters;
+  return ip;
+}
+
+template <typename T>
+int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, bool use_cbar, bool presmoothed,
+                 cudaStream_t st) {
+  InnerLev& I = Lv.in[k];
+  const int last = (int)Lv.in.size() - 1;
+  if (k == last) {
+    InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+    ip.zout = (T*)I.z;
+    launch_inner_coarse<T>(h->D, ip, st);
+    CKL();
+    return ST_OK;
+  }
+  const int ns = h->o.inner_smooth;
+  for (int it = 0; it < ns; ++it) {
+    if (it == 0 && presmoothed) continue;
+    InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+    launch_inner_jacobi<T>(h->D, 0, ip, st);
+    CKL();
+    std::swap(I.z, I.t);
+  }
+  {
+    InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+    launch_inner_restrict<T>(h->D, ip, st);
+    CKL();
+  }
+  TRY(inner_vcycle<T>(h, Lv, k + 1, P, sh, use_cbar, true, st));
+  launch_prolong_space_add<T>(h->D, I.g, Lv.in[k + 1].g, (long long)Lv.Nt * P, (const T*)Lv.in[k + 1].z,
+                              (T*)I.z, st);
+  CKL();
+  for (int it = 0; it < ns; ++it) {
+    InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+    launch_inner_jacobi<T>(h->D, 0, ip, st);
+    CKL();
+    std::swap(I.z, I.t);
+  }
+  return ST_OK;
+}
+
+// Solve the shifted systems with rhs in[0].y into in[0].z (zero start).
+template <typename T>
+int inner_solve(st_handle* h, Level& Lv, int P, const Shifts<T>& sh, bool use_cbar, int cycles, cudaStream_t st) {
+  for (int c = 0; c < cycles; ++c) {
+    if (c == 0 && Lv.in.size() > 1) {
+      InnerParams<T> ip = inner_params<T>(h, Lv, 0, P, sh, use_cbar);
+      ip.zout = (T*)Lv.in[0].z;
+      launch_inner_jacobi<T>(h->D, 1, ip, st);  // zero start
+      CKL();
+      TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, true, st));
+    } else {
+      TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, false, st));
+    }
+  }
+  return ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Level operations of the space-time cycle
+// ---------------------------------------------------------------------------
+template <typename T>
+LinParams<T> lin_params(st_handle* h, const Level& Lv, int adj) {
+  LinParams<T> lp;
+  lp.g = Lv.g;
+  lp.Nt = Lv.Nt;
+  lp.M = h->p.M;
+  lp.chunk = (Lv.g.Ns >= 4096 && Lv.Nt >= 8) ? 4 : 1;
+  lp.transpose = adj;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) {
+      const double q = (a < h->p.M && b < h->p.M) ? (adj ? h->col.Q[b][a] : h->col.Q[a][b]) : 0.0;
+      lp.W[a][b] = (T)(Lv.dt * q);
+      lp.F[a][b] = (T)(adj ? h->Fa[a][b] : h->Ff[a][b]);
+    }
+  lp.nu = (T)h->p.nu;
+  lp.e = nullptr;
+  lp.r = nullptr;
+  lp.cbar = (h->p.reaction != ST_REACTION_NONE) ? (const T*)Lv.cbar : nullptr;
+  lp.out = nullptr;
+  lp.transform = 0;
+  return lp;
+}
+
+template <typename T>
+int level_residual(st_handle* h, int l, int adj, const void* e, const void* r, void* out, int transform,
+                   cudaStream_t st) {
+  Level& Lv = h->L[l];
+  LinParams<T> lp = lin_params<T>(h, Lv, adj);
+  lp.e = (const T*)e;
+  lp.r = (const T*)r;
+  lp.out = (T*)out;
+  lp.transform = transform;
+  launch_lin_residual<T>(h->D, lp, st);
+  CKL();
+  return ST_OK;
+}
+
+template <typename T>
+int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
+  Level& Lv = h->L[l];
+  const int M = h->p.M;
+  TRY(level_residual<T>(h, l, adj, e_zero ? nullptr : Lv.e, Lv.r, Lv.in[0].y, 1, st));
+  const bool use_cbar = h->p.reaction != ST_REACTION_NONE;
+  TRY(inner_solve<T>(h, Lv, M, level_shifts<T>(h, Lv.dt), use_cbar, h->o.inner_cycles, st));
+  T B[MAXM][MAXM];
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) B[a][b] = (T)(adj ? h->Ba[a][b] : h->Bf[a][b]);
+  launch_backtransform<T>(Lv.g.Ns, Lv.Nt, M, B, (T)Lv.omega, e_zero ? 1 : 0, (const T*)Lv.in[0].z, (T*)Lv.e, st);
+  CKL();
+  return ST_OK;
+}
+
+template <typename T>
+int restrict_level(st_handle* h, int l, int adj, const void* fine, void* coarse, cudaStream_t st) {
+  Level& Lv = h->L[l];
+  Level& Lc = h->L[l + 1];
+  const int M = h->p.M;
+  if (Lv.next == 1) {
+    launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)coarse, st);
+  } else {
+    launch_restrict_time<T>(Lv.g.Ns, Lc.Nt, M, adj ? h->RtT : h->col.Rt, (const T*)fine, (T*)coarse, st);
+  }
+  CKL();
+  return ST_OK;
+}
+
+template <typename T>
+int prolong_level(st_handle* h, int l, int adj, const void* coarse, void* fine, cudaStream_t st) {
+  Level& Lv = h->L[l];
+  Level& Lc = h->L[l + 1];
+  const int M = h->p.M;
+  if (Lv.next == 1) {
+    launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)coarse, (T*)fine, st);
+  } else {
+    launch_prolong_time_add<T>(Lv.g.Ns, Lc.Nt, M, adj ? h->PtT : h->col.Pt, (const T*)coarse, (T*)fine, st);
+  }
+  CKL();
+  return ST_OK;
+}
+
+template <typename T>
+CoarseParams<T> coarse_params(st_handle* h) {
+  Level& Lv = h->L.back();
+  CoarseParams<T> cp;
+  cp.Nt = Lv.Nt;
+  cp.M = h->p.M;
+  cp.Nc = h->Nc;
+  cp.K = h->K;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b)
+      cp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? Lv.dt * h->col.Q[a][b] : 0.0;
+  cp.nu = h->p.nu;
+  cp.Lc = h->Lc;
+  cp.cbar = (h->p.reaction != ST_REACTION_NONE) ? (const T*)Lv.cbar : nullptr;
+  cp.Ainv = (T*)h->Ainv;
+  cp.Wf = (T*)h->Wf;
+  cp.Wt = (T*)h->Wt;
+  cp.Wfrow = (T*)h->Wfrow;
+  cp.Wtrow = (T*)h->Wtrow;
+  return cp;
+}
+
+template <typename T>
+int coarse_solve(st_handle* h, int adj, const void* r, void* e, cudaStream_t st) {
+  CoarseParams<T> cp = coarse_params<T>(h);
+  launch_coarse_solve<T>(cp, adj, (const T*)r, (T*)e, (T*)h->cin, st);
+  CKL();
+  return ST_OK;
+}
+
+template <typename T>
+int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
+  Level& Lv = h->L[l];
+  const int last = (int)h->L.size() - 1;
+  if (l == last) return coarse_solve<T>(h, adj, Lv.r, Lv.e, st);
+  const int nu1 = h->o.nu1, nu2 = h->o.nu2;
+  const long long n = Lv.g.Ns * Lv.Nt * h->p.M;
+  if (nu1 == 0) CK(cudaMemsetAsync(Lv.e, 0, n * h->esz, st));
+  for (int i = 0; i < nu1; ++i) TRY(smooth<T>(h, l, adj, i == 0, st));
+  TRY(level_residual<T>(h, l, adj, Lv.e, Lv.r, Lv.in[0].y, 0, st));
+  TRY(restrict_level<T>(h, l, adj, Lv.in[0].y, h->L[l + 1].r, st));
+  TRY(vcycle_level<T>(h, l + 1, adj, st));
+  TRY(prolong_level<T>(h, l, adj, h->L[l + 1].e, Lv.e, st));
+  for (int i = 0; i < nu2; ++i) TRY(smooth<T>(h, l, adj, false, st));
+  return ST_OK;
+}
+
+// cbar of every level and inner level from level 0's, then the coarsest
+// blocks' inverses.
+template <typename T>
+int enqueue_linearize(st_handle* h, cudaStream_t st) {
+  const bool rx = h->p.reaction != ST_REACTION_NONE;
+  if (rx) {
+    for (size_t l = 0; l < h->L.size(); ++l) {
+      Level& Lv = h->L[l];
+      for (size_t k = 1; k < Lv.in.size(); ++k) {
+        launch_restrict_space<T>(h->D, Lv.in[k - 1].g, Lv.in[k].g, Lv.Nt, (const T*)Lv.in[k - 1].cbar,
+                                 (T*)Lv.in[k].cbar, st);
+        CKL();
+      }
+      if (l + 1 < h->L.size()) {
+        Level& Lc = h->L[l + 1];
+        if (Lv.next == 1)
+          launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+        else
+          launch_cbar_time<T>(Lv.g.Ns, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+        CKL();
+      }
+    }
+  }
+  if (rx || !h->coarse_ready) {
+    CoarseParams<T> cp = coarse_params<T>(h);
+    launch_coarse_setup<T>(cp, st);
+    CKL();
+  }
+  return ST_OK;
+}
+
+int run_graph(st_handle* h, int which, int (*enq)(st_handle*, cudaStream_t)) {
+  if (!h->o.use_graphs) return enq(h, h->stream);
+  if (!h->gexec[which]) {
+    // make sure the capture stream sees all prior work of the user stream
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int s = enq(h, h->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (s != ST_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) {
+      set_err(e, "cudaStreamEndCapture");
+      return ST_ERR_CUDA;
+    }
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) h->gnodes[which] = nn;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_err(e, "cudaGraphInstantiate");
+      return ST_ERR_CUDA;
+    }
+    h->gexec[which] = ex;
+  }
+  CK(cudaGraphLaunch(h->gexec[which], h->stream));
+  return ST_OK;
+}
+
+template <typename T>
+int enq_cycle_fwd(st_handle* h, cudaStream_t st) { return vcycle_level<T>(h, 0, 0, st); }
+template <typename T>
+int enq_cycle_adj(st_handle* h, cudaStream_t st) { return vcycle_level<T>(h, 0, 1, st); }
+template <typename T>
+int enq_lin(st_handle* h, cudaStream_t st) { return enqueue_linearize<T>(h, st); }
+
+int cycle(st_handle* h, int adj) {
+  if (h->fp64) return run_graph(h, adj, adj ? enq_cycle_adj<double> : enq_cycle_fwd<double>);
+  return run_graph(h, adj, adj ? enq_cycle_adj<float> : enq_cycle_fwd<float>);
+}
+
+int linearize_levels(st_handle* h) {
+  int s = h->fp64 ? run_graph(h, 2, enq_lin<double>) : run_graph(h, 2, enq_lin<float>);
+  if (s == ST_OK) h->coarse_ready = true;
+  return s;
+}
+
+void invalidate_graphs(st_handle* h) {
+  for (int i = 0; i < 3; ++i)
+    if (h->gexec[i]) {
+      cudaGraphExecDestroy(h->gexec[i]);
+      h->gexec[i] = nullptr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fine FP64 steps
+// ---------------------------------------------------------------------------
+ResidParams fine_params(st_handle* h, const double* U, int adj) {
+  ResidParams rp;
+  const Level& L0 = h->L[0];
+  rp.g = L0.g;
+  rp.Nt = h->p.Nt;
+  rp.M = h->p.M;
+  rp.chunk = h->chunk;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b)
+      rp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? L0.dt * (adj ? h->col.Q[b][a] : h->col.Q[a][b]) : 0.0;
+  rp.nu = h->p.nu;
+  rp.rho = h->p.rho;
+  rp.reaction = h->p.reaction;
+  rp.U = U;
+  rp.u0 = h->u0;
+  rp.lam = nullptr;
+  rp.gT = nullptr;
+  rp.R = nullptr;
+  rp.cbar = nullptr;
+  rp.partial = h->partial;
+  return rp;
+}
+
+// r = G(U) into R (type per r_fp64), cbar optional, ||G||^2 into scal[slot].
+int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_cbar, int slot) {
+  ResidParams rp = fine_params(h, U, 0);
+  rp.R = R;
+  rp.cbar = (want_cbar && h->p.reaction != ST_REACTION_NONE) ? h->L[0].cbar : nullptr;
+  launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
+  CKL();
+  launch_sum_partials(h->partial, residual_blocks(rp), h->scal + slot, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+int read_scalars(st_handle* h, int n) {
+  CK(cudaMemcpyAsync(h->hscal, h->scal, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int stage_in(st_handle* h, const double* U, double** Ud, bool copy) {
+  if (!U) return ST_ERR_INVALID_ARG;
+  if (is_device_ptr(U)) {
+    *Ud = (double*)U;
+    return ST_OK;
+  }
+  if (!h->Ustage) TRY(alloc_typed(h, &h->Ustage, h->D_total * sizeof(double)));
+  if (copy)
+    CK(cudaMemcpyAsync(h->Ustage, U, h->D_total * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  *Ud = h->Ustage;
+  return ST_OK;
+}
+
+int stage_out(st_handle* h, double* U, const double* Ud) {
+  if (U != Ud) CK(cudaMemcpyAsync(U, Ud, h->D_total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return ST_OK;
+}
+
+int stage_plane(st_handle* h, const double* p, double* buf, const double** out) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    return ST_OK;
+  }
+  CK(cudaMemcpyAsync(buf, p, h->L[0].g.Ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  *out = buf;
+  return ST_OK;
+}
+
+double ref_norm(const st_handle* h) {
+  double s = 0;
+  for (double v : h->u0_host) s += v * v;
+  const double r = std::sqrt((double)h->p.M * s);
+  return r > 0 ? r : 1.0;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void fill_info(st_solve_info* info, int it, int status, double rel, double abs_, double ref, double secs,
+               const std::vector<double>& hist) {
+  if (!info) return;
+  info->iterations = it;
+  info->status = status;
+  info->rel_residual = rel;
+  info->abs_residual = abs_;
+  info->ref_norm = ref;
+  info->seconds = secs;
+  info->history_len = (int)std::min<size_t>(hist.size(), ST_MAX_HISTORY);
+  const size_t off = hist.size() > ST_MAX_HISTORY ? hist.size() - ST_MAX_HISTORY : 0;
+  for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[off + i];
+}
+
+// One outer iteration on device U: residual + cbar, linearise, cycle, update.
+// The squared norm of G(U) is left in scal[0].
+int outer_step(st_handle* h, double* Ud, bool do_cycle) {
+  const bool rx = h->p.reaction != ST_REACTION_NONE;
+  const bool relin = rx && (h->o.newton || !h->linearized);
+  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0));
+  if (!do_cycle) return ST_OK;
+  if (relin || !h->coarse_ready) {
+    TRY(linearize_levels(h));
+    h->linearized = true;
+  }
+  TRY(cycle(h, 0));
+  launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void st_default_opts(st_solver_opts* o) {
+  if (!o) return;
+  o->precision = ST_PREC_FP32_REFINE;
+  o->coarsening = ST_COARSEN_AUTO_MU;
+  o->max_levels = ST_MAX_LEVELS;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->omega = 0.0;
+  o->mu_crit = 1.0;
+  o->inner_cycles = 1;
+  o->inner_smooth = 1;
+  o->inner_coarse_iters = 8;
+  o->coarse_max_points = 16;
+  o->coarse_max_slabs = 4;
+  o->sdc_qdelta = ST_SDC_IE;
+  o->sdc_inner_cycles = 2;
+  o->tol = 1e-8;
+  o->max_iters = 1000;
+  o->newton = 1;
+  o->use_graphs = 1;
+}
+
+const char* st_status_str(int s) {
+  switch (s) {
+    case ST_OK: return "ok";
+    case ST_ERR_INVALID_ARG: return "invalid argument";
+    case ST_ERR_OOM: return "out of device memory";
+    case ST_ERR_CUDA: return "CUDA error";
+    case ST_ERR_NOT_CONVERGED: return "not converged";
+    case ST_ERR_DIVERGED: return "diverged";
+    case ST_ERR_TIMEOUT: return "timeout";
+    case ST_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* st_last_error(void) { return g_err; }
+
+int st_plan(const st_problem* p, const st_solver_opts* oin, st_plan_info* out) {
+  st_solver_opts o;
+  st_default_opts(&o);
+  if (oin) o = *oin;
+  TRY(validate(p, &o));
+  std::vector<PlanLevel> pl;
+  TRY(plan_levels(p, o, pl));
+  if (!out) return ST_OK;
+  memset(out, 0, sizeof(*out));
+  out->levels = (int)pl.size();
+  const size_t esz = o.precision == ST_PREC_FP64 ? 8 : 4;
+  const bool rx = p->reaction != ST_REACTION_NONE;
+  size_t bytes = 0;
+  for (size_t l = 0; l < pl.size(); ++l) {
+    const PlanLevel& L = pl[l];
+    st_level_info& li = out->level[l];
+    li.n[0] = L.g.n0; li.n[1] = L.g.n1; li.n[2] = L.g.n2;
+    li.Ns = L.g.Ns;
+    li.Nt = L.Nt;
+    li.dt = L.dt;
+    for (int a = 0; a < 3; ++a) li.h[a] = L.g.ih2[a] > 0 ? 1.0 / std::sqrt(L.g.ih2[a]) : 0.0;
+    li.mu = L.mu;
+    li.next_kind = L.next;
+    li.omega = L.omega;
+    li.inner_levels = (int)L.inner.size();
+    const size_t D = (size_t)L.g.Ns * L.Nt * p->M;
+    bytes += 5 * round_up(D * esz) + (rx ? round_up((size_t)L.g.Ns * L.Nt * esz) : 0);
+    for (size_t k = 1; k < L.inner.size(); ++k) {
+      const size_t Dk = (size_t)L.inner[k].Ns * L.Nt * p->M;
+      bytes += 3 * round_up(Dk * esz) + (rx ? round_up((size_t)L.inner[k].Ns * L.Nt * esz) : 0);
+    }
+  }
+  const PlanLevel& C = pl.back();
+  const size_t Kc = (size_t)C.g.Ns * p->M;
+  bytes += round_up(C.Nt * Kc * Kc * esz) + 2 * round_up(C.Nt * Kc * C.g.Ns * esz) +
+           2 * round_up(C.Nt * C.g.Ns * C.g.Ns * esz) + round_up(C.Nt * C.g.Ns * esz);
+  out->workspace_bytes = bytes;
+  out->coarse_points = (int)C.g.Ns;
+  return ST_OK;
+}
+
+int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime* rtin, st_handle** out) {
+  if (!out) return ST_ERR_INVALID_ARG;
+  *out = nullptr;
+  st_solver_opts o;
+  st_default_opts(&o);
+  if (oin) o = *oin;
+  TRY(validate(pin, &o));
+  if (!pin->u0) return ST_ERR_INVALID_ARG;
+  std::vector<PlanLevel> pl;
+  TRY(plan_levels(pin, o, pl));
+  st_handle* h = new st_handle();
+  h->p = *pin;
+  h->p.u0 = nullptr;
+  h->o = o;
+  if (rtin) h->rt = *rtin;
+  else memset(&h->rt, 0, sizeof(h->rt));
+  h->stream = (cudaStream_t)h->rt.stream;
+  h->D = pin->d;
+  h->fp64 = o.precision == ST_PREC_FP64;
+  h->esz = h->fp64 ? 8 : 4;
+  auto fail = [&](int s) {
+    st_destroy(h);
+    return s;
+  };
+  if (colloc_setup(pin->M, &h->col) != 0) return fail(ST_ERR_UNSUPPORTED);
+  build_transforms(h);
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err(cudaGetLastError(), "cudaStreamCreate");
+    return fail(ST_ERR_CUDA);
+  }
+  const int M = pin->M;
+  const bool rx = pin->reaction != ST_REACTION_NONE;
+  // levels and buffers
+  h->L.resize(pl.size());
+  for (size_t l = 0; l < pl.size(); ++l) {
+    Level& Lv = h->L[l];
+    Lv.g = pl[l].g;
+    Lv.Nt = pl[l].Nt;
+    Lv.dt = pl[l].dt;
+    Lv.mu = pl[l].mu;
+    Lv.omega = pl[l].omega;
+    Lv.next = pl[l].next;
+    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
+    int s = ST_OK;
+    s |= alloc_into(h, &Lv.e, D * h->esz);
+    s |= alloc_into(h, &Lv.r, D * h->esz);
+    if (rx) s |= alloc_into(h, &Lv.cbar, (size_t)Lv.g.Ns * Lv.Nt * h->esz);
+    Lv.in.resize(pl[l].inner.size());
+    for (size_t k = 0; k < Lv.in.size(); ++k) {
+      InnerLev& I = Lv.in[k];
+      I.g = pl[l].inner[k];
+      const size_t Dk = (size_t)I.g.Ns * Lv.Nt * M;
+      s |= alloc_into(h, &I.y, Dk * h->esz);
+      s |= alloc_into(h, &I.z, Dk * h->esz);
+      s |= alloc_into(h, &I.t, Dk * h->esz);
+      if (k == 0) I.cbar = Lv.cbar;
+      else if (rx) s |= alloc_into(h, &I.cbar, (size_t)I.g.Ns * Lv.Nt * h->esz);
+    }
+    if (s != ST_OK) return fail(ST_ERR_OOM);
+  }
+  h->D_total = (long long)h->L[0].g.Ns * pin->Nt * M;
+  h->chunk = (h->L[0].g.Ns >= 4096 && pin->Nt >= 8) ? 4 : 1;
+  // coarsest level
+  {
+    Level& C = h->L.back();
+    h->Nc = (int)C.g.Ns;
+    h->K = h->Nc * M;
+    // dense Laplacian of the coarsest grid by applying the stencil to unit vectors
+    std::vector<double> Lc((size_t)h->Nc * h->Nc, 0.0);
+    const int nn[3] = {C.g.n0, C.g.n1, C.g.n2};
+    const long long st3[3] = {1, C.g.n0, (long long)C.g.n0 * C.g.n1};
+    for (long long s = 0; s < C.g.Ns; ++s) {
+      long long r = s;
+      int ij[3];
+      ij[0] = (int)(r % nn[0]); r /= nn[0];
+      ij[1] = (int)(r % nn[1]);
+      ij[2] = (int)(r / nn[1]);
+      for (int a = 0; a < h->D; ++a) {
+        const double w = C.g.ih2[a];
+        Lc[s * h->Nc + s] += -2.0 * w;
+        for (int dir = -1; dir <= 1; dir += 2) {
+          int q = ij[a] + dir;
+          bool zero = false;
+          if (q < 0 || q >= nn[a]) {
+            if (C.g.bc == ST_BC_PERIODIC) q = (q + nn[a]) % nn[a];
+            else if (C.g.bc == ST_BC_NEUMANN) q = (q < 0) ? 1 : nn[a] - 2;
+            else zero = true;
+          }
+          if (!zero) Lc[s * h->Nc + (s + (long long)(q - ij[a]) * st3[a])] += w;
+        }
+      }
+    }
+    int s = ST_OK;
+    s |= alloc_typed(h, &h->Lc, Lc.size() * sizeof(double));
+    const size_t Kc = h->K;
+    s |= alloc_into(h, &h->Ainv, (size_t)C.Nt * Kc * Kc * h->esz);
+    s |= alloc_into(h, &h->Wf, (size_t)C.Nt * Kc * h->Nc * h->esz);
+    s |= alloc_into(h, &h->Wt, (size_t)C.Nt * Kc * h->Nc * h->esz);
+    s |= alloc_into(h, &h->Wfrow, (size_t)C.Nt * h->Nc * h->Nc * h->esz);
+    s |= alloc_into(h, &h->Wtrow, (size_t)C.Nt * h->Nc * h->Nc * h->esz);
+    s |= alloc_into(h, &h->cin, (size_t)C.Nt * h->Nc * h->esz);
+    if (s != ST_OK) return fail(ST_ERR_OOM);
+    if (cudaMemcpyAsync(h->Lc, Lc.data(), Lc.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+        cudaSuccess) {
+      set_err(cudaGetLastError(), "copy Lc");
+      return fail(ST_ERR_CUDA);
+    }
+    cudaError_t e = h->fp64 ? prepare_coarse_setup<double>(coarse_params<double>(h))
+                            : prepare_coarse_setup<float>(coarse_params<float>(h));
+    if (e != cudaSuccess) {
+      set_err(e, "cudaFuncSetAttribute");
+      return fail(ST_ERR_CUDA);
+    }
+  }
+  // fine-level buffers
+  {
+    const long long Ns = h->L[0].g.Ns;
+    ResidParams rp = fine_params(h, nullptr, 0);
+    h->npartial = std::max(residual_blocks(rp), gradient_blocks(rp));
+    int s = ST_OK;
+    s |= alloc_typed(h, &h->partial, h->npartial * sizeof(double));
+    s |= alloc_typed(h, &h->partial2, h->npartial * sizeof(double));
+    s |= alloc_typed(h, &h->scal, 8 * sizeof(double));
+    s |= alloc_typed(h, &h->u0, Ns * sizeof(double));
+    s |= alloc_typed(h, &h->plane, Ns * sizeof(double));
+    s |= alloc_typed(h, &h->plane2, Ns * sizeof(double));
+    if (s != ST_OK) return fail(ST_ERR_OOM);
+    if (cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess) {
+      set_err(cudaGetLastError(), "cudaMallocHost");
+      return fail(ST_ERR_CUDA);
+    }
+  }
+  int s = st_set_u0(h, pin->u0);
+  if (s != ST_OK) return fail(s);
+  // zero the cycle buffers once (cbar stays 0 for linear problems)
+  for (auto& Lv : h->L) {
+    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
+    if (cudaMemsetAsync(Lv.e, 0, D * h->esz, h->stream) != cudaSuccess) return fail(ST_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_err(cudaGetLastError(), "st_create sync");
+    return fail(ST_ERR_CUDA);
+  }
+  *out = h;
+  return ST_OK;
+}
+
+void st_destroy(st_handle* h) {
+  if (!h) return;
+  invalidate_graphs(h);
+  cudaStreamSynchronize(h->stream);
+  for (auto it = h->allocs.rbegin(); it != h->allocs.rend(); ++it) {
+    if (h->rt.alloc) {
+      if (h->rt.free) h->rt.free(it->p, it->bytes, (void*)h->stream, h->rt.ctx);
+    } else {
+      cudaFreeAsync(it->p, h->stream);
+    }
+  }
+  cudaStreamSynchronize(h->stream);
+  if (h->hscal) cudaFreeHost(h->hscal);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  cudaGetLastError();
+  delete h;
+}
+
+int st_set_params(st_handle* h, double nu, double rho) {
+  if (!h || !(nu > 0) || !std::isfinite(rho)) return ST_ERR_INVALID_ARG;
+  h->p.nu = nu;
+  h->p.rho = rho;
+  for (auto& Lv : h->L) {
+    Lv.mu = nu * Lv.dt * Lv.g.ih2[0];
+    Lv.omega = default_omega(h->o, Lv.mu);
+  }
+  invalidate_graphs(h);
+  h->coarse_ready = false;
+  h->linearized = false;
+  return ST_OK;
+}
+
+int st_set_u0(st_handle* h, const double* u0) {
+  if (!h || !u0) return ST_ERR_INVALID_ARG;
+  const long long Ns = h->L[0].g.Ns;
+  h->u0_host.assign(Ns, 0.0);
+  const cudaMemcpyKind k = is_device_ptr(u0) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  CK(cudaMemcpy(h->u0_host.data(), u0, Ns * sizeof(double), k));
+  CK(cudaMemcpyAsync(h->u0, h->u0_host.data(), Ns * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* norm_out) {
+  if (!h || !U) return ST_ERR_INVALID_ARG;
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  const int r64 = (R_is_fp64 || h->fp64) ? 1 : 0;
+  void* Rd = R;
+  const bool host_R = R && !is_device_ptr(R);
+  if (host_R) Rd = h->L[0].r;  // device staging (may need a double-size buffer)
+  if (host_R && r64 && !h->fp64) {
+    // FP64 output for an FP32 handle on the host: use the y/z pair of level 0
+    // only if large enough; otherwise stage through Ustage-sized buffer
+    if (!h->lam) TRY(alloc_typed(h, &h->lam, h->D_total * sizeof(double)));
+    Rd = h->lam;
+  }
+  TRY(fine_residual(h, Ud, Rd, r64, false, 0));
+  if (host_R)
+    CK(cudaMemcpyAsync(R, Rd, h->D_total * (r64 ? 8 : 4), cudaMemcpyDeviceToHost, h->stream));
+  TRY(read_scalars(h, 1));
+  if (norm_out) *norm_out = std::sqrt(h->hscal[0]);
+  return ST_OK;
+}
+
+int st_vcycle(st_handle* h, double* U, double* norm_out) {
+  if (!h || !U) return ST_ERR_INVALID_ARG;
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  TRY(outer_step(h, Ud, true));
+  TRY(stage_out(h, U, Ud));
+  TRY(read_scalars(h, 1));
+  if (norm_out) *norm_out = std::sqrt(h->hscal[0]);
+  return ST_OK;
+}
+
+int st_solve(st_handle* h, double* U, st_solve_info* info) {
+  if (!h || !U) return ST_ERR_INVALID_ARG;
+  const double t0 = now_s();
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  const double ref = ref_norm(h);
+  std::vector<double> hist;
+  int status = ST_ERR_NOT_CONVERGED;
+  double rel = 0, nrm = 0;
+  int it = 0;
+  for (;; ++it) {
+    TRY(fine_residual(h, Ud, h->L[0].r, h->fp64,
+                      h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized), 0));
+    TRY(read_scalars(h, 1));
+    nrm = std::sqrt(h->hscal[0]);
+    rel = nrm / ref;
+    hist.push_back(rel);
+    if (!std::isfinite(rel) || rel > 1e8) { status = ST_ERR_DIVERGED; break; }
+    if (rel <= h->o.tol) { status = ST_OK; break; }
+    if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
+    const bool relin = h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized);
+    if (relin || !h->coarse_ready) {
+      TRY(linearize_levels(h));
+      h->linearized = true;
+    }
+    TRY(cycle(h, 0));
+    launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
+    CKL();
+  }
+  TRY(stage_out(h, U, Ud));
+  CK(cudaStreamSynchronize(h->stream));
+  fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
+  return status;
+}
+
+int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
+  if (!h || !U || nsweeps < 1) return ST_ERR_INVALID_ARG;
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  Level& L0 = h->L[0];
+  const int M = h->p.M;
+  const double(*QI)[MAXM] = (h->o.sdc_qdelta == ST_SDC_LU) ? h->col.QI_lu : h->col.QI_ie;
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    TRY(fine_residual(h, Ud, L0.r, h->fp64, false, 0));
+    for (int m = 0; m < M; ++m) {
+      SdcCoef cf;
+      for (int q = 0; q < MAXM; ++q) {
+        cf.qi[q] = (q < m) ? L0.dt * QI[m][q] : 0.0;
+        cf.qe[q] = (q < m) ? L0.dt * h->col.QE[m][q] : 0.0;
+      }
+      launch_sdc_rhs(h->D, h->fp64, L0.g, L0.Nt, M, m, h->p.nu, h->p.reaction, h->p.rho, cf, L0.r, L0.e, Ud,
+                     L0.in[0].y, h->stream);
+      CKL();
+      if (h->fp64) {
+        Shifts<double> sh;
+        sh.ngroups = 1; sh.plane[0] = 0; sh.cplx[0] = 0; sh.sr[0] = L0.dt * QI[m][m]; sh.si[0] = 0;
+        TRY(inner_solve<double>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, h->stream));
+      } else {
+        Shifts<float> sh;
+        sh.ngroups = 1; sh.plane[0] = 0; sh.cplx[0] = 0; sh.sr[0] = (float)(L0.dt * QI[m][m]); sh.si[0] = 0;
+        TRY(inner_solve<float>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, h->stream));
+      }
+      launch_scatter_plane(h->fp64, L0.in[0].z, L0.e, L0.g.Ns, L0.Nt, M, m, h->stream);
+      CKL();
+    }
+    launch_update(h->fp64, Ud, L0.e, h->D_total, h->stream);
+    CKL();
+  }
+  TRY(stage_out(h, U, Ud));
+  TRY(read_scalars(h, 1));
+  if (norm_out) *norm_out = std::sqrt(h->hscal[0]);
+  return ST_OK;
+}
+
+int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, double* dnu, double* drho,
+                              double* du0, st_solve_info* info) {
+  if (!h || !U || !gT) return ST_ERR_INVALID_ARG;
+  if (h->p.bc == ST_BC_NEUMANN) return ST_ERR_UNSUPPORTED;
+  const double t0 = now_s();
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  const double* gd = nullptr;
+  TRY(stage_plane(h, gT, h->plane, &gd));
+  if (!h->lam) TRY(alloc_typed(h, &h->lam, h->D_total * sizeof(double)));
+  CK(cudaMemsetAsync(h->lam, 0, h->D_total * sizeof(double), h->stream));
+  // linearise at U (cbar of every level, coarsest blocks)
+  TRY(fine_residual(h, Ud, nullptr, h->fp64, true, 0));
+  TRY(linearize_levels(h));
+  h->linearized = true;
+  std::vector<double> hist;
+  int status = ST_ERR_NOT_CONVERGED;
+  double rel = 0, nrm = 0, ref = 1;
+  int it = 0;
+  for (;; ++it) {
+    ResidParams rp = fine_params(h, Ud, 1);
+    rp.lam = h->lam;
+    rp.gT = gd;
+    rp.R = h->L[0].r;
+    launch_adj_residual(h->D, h->fp64, rp, h->stream);
+    CKL();
+    launch_sum_partials(h->partial, residual_blocks(rp), h->scal, h->stream);
+    CKL();
+    TRY(read_scalars(h, 1));
+    nrm = std::sqrt(h->hscal[0]);
+    if (it == 0) ref = nrm > 0 ? nrm : 1.0;
+    rel = nrm / ref;
+    hist.push_back(rel);
+    if (!std::isfinite(rel) || rel > 1e8) { status = ST_ERR_DIVERGED; break; }
+    if (rel <= h->o.tol || nrm == 0) { status = ST_OK; break; }
+    if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
+    TRY(cycle(h, 1));
+    launch_update(h->fp64, h->lam, h->L[0].e, h->D_total, h->stream);
+    CKL();
+  }
+  // gradients
+  {
+    ResidParams rp = fine_params(h, Ud, 1);
+    rp.lam = h->lam;
+    const bool host_du0 = du0 && !is_device_ptr(du0);
+    double* du0d = du0 ? (host_du0 ? h->plane2 : du0) : nullptr;
+    // dnu partials go to rp.partial (= h->partial), drho partials to partial2
+    launch_gradients(h->D, rp, h->partial2, du0d, h->stream);
+    CKL();
+    const long long nb = gradient_blocks(rp);
+    launch_sum_partials(h->partial, nb, h->scal + 1, h->stream);
+    launch_sum_partials(h->partial2, nb, h->scal + 2, h->stream);
+    CKL();
+    if (host_du0)
+      CK(cudaMemcpyAsync(du0, h->plane2, h->L[0].g.Ns * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TRY(read_scalars(h, 3));
+    if (dnu) *dnu = h->hscal[1];
+    if (drho) *drho = h->hscal[2];
+  }
+  fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
+  return status;
+}
+
+int st_adjoint_solve(st_handle* h, const double* U, const double* u_target, double* dnu, double* drho,
+                     double* du0, st_solve_info* info) {
+  if (!h || !U || !u_target) return ST_ERR_INVALID_ARG;
+  // gT = h^d (u_{Nt,M} - target), formed on the host from the last plane
+  const long long Ns = h->L[0].g.Ns;
+  std::vector<double> last(Ns), tgt(Ns);
+  const double* lastp = U + (h->D_total - Ns);
+  CK(cudaMemcpy(last.data(), lastp, Ns * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(tgt.data(), u_target, Ns * sizeof(double), cudaMemcpyDefault));
+  double hd = 1.0;
+  for (int a = 0; a < h->D; ++a) hd /= std::sqrt(h->L[0].g.ih2[a]);
+  for (long long s = 0; s < Ns; ++s) last[s] = hd * (last[s] - tgt[s]);
+  return st_adjoint_solve_terminal(h, U, last.data(), dnu, drho, du0, info);
+}
+
+int st_collocation(int M, double* tau, double* Q, double* lam, double* V, double* Vinv) {
+  Colloc c;
+  if (colloc_setup(M, &c) != 0) return ST_ERR_INVALID_ARG;
+  for (int m = 0; m < M; ++m) {
+    if (tau) tau[m] = c.tau[m];
+    if (lam) { lam[2 * m] = c.lam[m].real(); lam[2 * m + 1] = c.lam[m].imag(); }
+    for (int j = 0; j < M; ++j) {
+      if (Q) Q[m * M + j] = c.Q[m][j];
+      if (V) { V[2 * (m * M + j)] = c.V[m][j].real(); V[2 * (m * M + j) + 1] = c.V[m][j].imag(); }
+      if (Vinv) {
+        Vinv[2 * (m * M + j)] = c.Vinv[m][j].real();
+        Vinv[2 * (m * M + j) + 1] = c.Vinv[m][j].imag();
+      }
+    }
+  }
+  return ST_OK;
+}
+
+int st_time_transfer(int M, double* Pt, double* Rt) {
+  Colloc c;
+  if (colloc_setup(M, &c) != 0) return ST_ERR_INVALID_ARG;
+  for (int kk = 0; kk < 2 * M; ++kk)
+    for (int m = 0; m < M; ++m) {
+      if (Pt) Pt[kk * M + m] = c.Pt[kk][m];
+      if (Rt) Rt[m * 2 * M + kk] = c.Rt[m][kk];
+    }
+  return ST_OK;
+}
+
+int st_num_levels(const st_handle* h) { return h ? (int)h->L.size() : 0; }
+
+int st_level_info_get(const st_handle* h, int level, st_level_info* out) {
+  if (!h || !out || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  const Level& Lv = h->L[level];
+  memset(out, 0, sizeof(*out));
+  out->n[0] = Lv.g.n0; out->n[1] = Lv.g.n1; out->n[2] = Lv.g.n2;
+  out->Ns = Lv.g.Ns;
+  out->Nt = Lv.Nt;
+  out->dt = Lv.dt;
+  for (int a = 0; a < 3; ++a) out->h[a] = Lv.g.ih2[a] > 0 ? 1.0 / std::sqrt(Lv.g.ih2[a]) : 0.0;
+  out->mu = Lv.mu;
+  out->next_kind = Lv.next;
+  out->omega = Lv.omega;
+  out->inner_levels = (int)Lv.in.size();
+  return ST_OK;
+}
+
+int st_linearize(st_handle* h, const double* U) {
+  if (!h || !U) return ST_ERR_INVALID_ARG;
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  TRY(fine_residual(h, Ud, nullptr, h->fp64, true, 0));
+  TRY(linearize_levels(h));
+  h->linearized = true;
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+static size_t level_elems(const st_handle* h, int l) {
+  return (size_t)h->L[l].g.Ns * h->L[l].Nt * h->p.M;
+}
+
+int st_level_cbar(st_handle* h, int level, void* out) {
+  if (!h || !out || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  const Level& Lv = h->L[level];
+  const size_t n = (size_t)Lv.g.Ns * Lv.Nt * h->esz;
+  if (Lv.cbar) CK(cudaMemcpyAsync(out, Lv.cbar, n, cudaMemcpyDeviceToDevice, h->stream));
+  else CK(cudaMemsetAsync(out, 0, n, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_level_residual(st_handle* h, int level, int transpose, const void* e, const void* r, void* out) {
+  if (!h || !r || !out || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  if (h->fp64) TRY(level_residual<double>(h, level, transpose, e, r, out, 0, h->stream));
+  else TRY(level_residual<float>(h, level, transpose, e, r, out, 0, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_level_smooth(st_handle* h, int level, int transpose, void* e, const void* r) {
+  if (!h || !e || !r || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  Level& Lv = h->L[level];
+  const size_t n = level_elems(h, level) * h->esz;
+  CK(cudaMemcpyAsync(Lv.e, e, n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(Lv.r, r, n, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->fp64) TRY(smooth<double>(h, level, transpose, false, h->stream));
+  else TRY(smooth<float>(h, level, transpose, false, h->stream));
+  CK(cudaMemcpyAsync(e, Lv.e, n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_level_restrict(st_handle* h, int level, int transpose, const void* fine, void* coarse) {
+  if (!h || !fine || !coarse || level < 0 || level + 1 >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  if (h->fp64) TRY(restrict_level<double>(h, level, transpose, fine, coarse, h->stream));
+  else TRY(restrict_level<float>(h, level, transpose, fine, coarse, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_level_prolong(st_handle* h, int level, int transpose, const void* coarse, void* fine) {
+  if (!h || !fine || !coarse || level < 0 || level + 1 >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
+  if (h->fp64) TRY(prolong_level<double>(h, level, transpose, coarse, fine, h->stream));
+  else TRY(prolong_level<float>(h, level, transpose, coarse, fine, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_coarse_solve(st_handle* h, int transpose, const void* r, void* e) {
+  if (!h || !r || !e) return ST_ERR_INVALID_ARG;
+  if (!h->coarse_ready) TRY(linearize_levels(h));
+  if (h->fp64) TRY(coarse_solve<double>(h, transpose, r, e, h->stream));
+  else TRY(coarse_solve<float>(h, transpose, r, e, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
+  if (!h || !r || !e) return ST_ERR_INVALID_ARG;
+  if (!h->coarse_ready) TRY(linearize_levels(h));
+  const size_t n = level_elems(h, 0) * h->esz;
+  CK(cudaMemcpyAsync(h->L[0].r, r, n, cudaMemcpyDeviceToDevice, h->stream));
+  TRY(cycle(h, transpose ? 1 : 0));
+  CK(cudaMemcpyAsync(e, h->L[0].e, n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
+                   double* bytes_per_launch) {
+  if (!h || iters < 1 || which < 0 || which > 4) return ST_ERR_INVALID_ARG;
+  if (which == ST_KERNEL_FINE_RESIDUAL && (!U || !is_device_ptr(U))) return ST_ERR_INVALID_ARG;
+  Level& L0 = h->L[0];
+  const bool rx = h->p.reaction != ST_REACTION_NONE;
+  const double D = (double)h->D_total;
+  const double planes = (double)L0.g.Ns * L0.Nt;
+  const double es = (double)h->esz;
+  double bytes = 0;
+  if (!h->coarse_ready) TRY(linearize_levels(h));
+  auto one = [&](cudaStream_t st) -> int {
+    switch (which) {
+      case ST_KERNEL_FINE_RESIDUAL: {
+        ResidParams rp = fine_params(h, U, 0);
+        rp.R = L0.r;
+        rp.cbar = rx ? L0.cbar : nullptr;
+        launch_residual(h->D, h->fp64, h->fp64, rp, st);
+        CKL();
+        return ST_OK;
+      }
+      case ST_KERNEL_LEVEL_RESIDUAL:
+        return h->fp64 ? level_residual<double>(h, 0, 0, L0.e, L0.r, L0.in[0].y, 1, st)
+                       : level_residual<float>(h, 0, 0, L0.e, L0.r, L0.in[0].y, 1, st);
+      case ST_KERNEL_JACOBI:
+        if (h->fp64) {
+          InnerParams<double> ip = inner_params<double>(h, L0, 0, h->p.M, level_shifts<double>(h, L0.dt), rx);
+          launch_inner_jacobi<double>(h->D, 0, ip, st);
+        } else {
+          InnerParams<float> ip = inner_params<float>(h, L0, 0, h->p.M, level_shifts<float>(h, L0.dt), rx);
+          launch_inner_jacobi<float>(h->D, 0, ip, st);
+        }
+        CKL();
+        return ST_OK;
+      case ST_KERNEL_BACKTRANSFORM: {
+        if (h->fp64) {
+          double B[MAXM][MAXM];
+          for (int a2 = 0; a2 < MAXM; ++a2)
+            for (int b = 0; b < MAXM; ++b) B[a2][b] = h->Bf[a2][b];
+          launch_backtransform<double>(L0.g.Ns, L0.Nt, h->p.M, B, L0.omega, 0, (const double*)L0.in[0].z,
+                                       (double*)L0.e, st);
+        } else {
+          float B[MAXM][MAXM];
+          for (int a2 = 0; a2 < MAXM; ++a2)
+            for (int b = 0; b < MAXM; ++b) B[a2][b] = (float)h->Bf[a2][b];
+          launch_backtransform<float>(L0.g.Ns, L0.Nt, h->p.M, B, (float)L0.omega, 0, (const float*)L0.in[0].z,
+                                      (float*)L0.e, st);
+        }
+        CKL();
+        return ST_OK;
+      }
+      default:
+        return cycle(h, 0);
+    }
+  };
+  switch (which) {
+    case ST_KERNEL_FINE_RESIDUAL: bytes = D * (8 + es) + (rx ? planes * es : 0); break;
+    case ST_KERNEL_LEVEL_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_JACOBI: bytes = D * 3 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
+    default: bytes = 0;
+  }
+  TRY(one(h->stream));  // warm (and capture, for the cycle)
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->stream));
+  for (int i = 0; i < iters; ++i) {
+    int s = one(h->stream);
+    if (s != ST_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return s;
+    }
+  }
+  CK(cudaEventRecord(e1, h->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_per_launch) *ms_per_launch = ms / iters;
+  if (bytes_per_launch) *bytes_per_launch = bytes;
+  return ST_OK;
+}
+
+int st_stats(st_handle* h, st_stats_info* out) {
+  if (!h || !out) return ST_ERR_INVALID_ARG;
+  out->levels = (int)h->L.size();
+  out->cycle_graph_nodes = (int)h->gnodes[0];
+  out->linearize_graph_nodes = (int)h->gnodes[2];
+  const bool rx = h->p.reaction != ST_REACTION_NONE;
+  // fine residual + partial sum + update, plus the graphs
+  out->launches_per_vcycle = 3 + (int)h->gnodes[0] + ((rx && h->o.newton) ? (int)h->gnodes[2] : 0);
+  return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Launcher declarations of the CUDA kernels (one translation unit per group).
+#pragma once
+
+#include "st_internal.cuh"
+
+namespace st {
+
+// SDC node coefficients: qi[q] = dt*QI[m][q], qe[q] = dt*QE[m][q] for q < m.
+struct SdcCoef {
+  double qi[MAXM];
+  double qe[MAXM];
+};
+
+// Coarsest-level data (one dense block per slab, K = M*Nc).
+template <typename T>
+struct CoarseParams {
+  int Nt, M, Nc, K;
+  double dtq[MAXM][MAXM];  // dt * Q of the coarsest level
+  double nu;
+  const double* Lc;        // dense Laplacian of the coarsest grid [Nc][Nc] (no nu)
+  const T* cbar;           // [Nt][Nc] or null
+  T* Ainv;                 // [Nt][K][K]
+  T* Wf;                   // [Nt][K][Nc]   A^{-1} (1 (x) I)
+  T* Wt;                   // [Nt][K][Nc]   A^{-T} (e_M (x) I)
+  T* Wfrow;                // [Nt][Nc][Nc]  rows of Wf at node M
+  T* Wtrow;                // [Nt][Nc][Nc]  sum over nodes of Wt
+};
+
+// k_fine.cu
+long long residual_blocks(const ResidParams& p);
+long long gradient_blocks(const ResidParams& p);
+void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st);
+void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st);
+void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st);
+void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st);
+void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st);
+void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,
+                    double rho, const SdcCoef& cf, const void* G, const void* delta, const double* U,
+                    void* y, cudaStream_t st);
+void launch_scatter_plane(int fp64, const void* src, void* dst, long long Ns, int Nt, int M, int m,
+                          cudaStream_t st);
+
+// k_level.cu
+template <typename T> void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st);
+template <typename T>
+void launch_backtransform(long long Ns, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero,
+                          const T* z, T* e, cudaStream_t st);
+template <typename T> void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st);
+template <typename T> void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st);
+template <typename T> size_t inner_coarse_smem(const InnerParams<T>& p);
+template <typename T> void launch_inner_coarse(int D, const InnerParams<T>& p, cudaStream_t st);
+template <typename T>
+void launch_restrict_space(int D, const GridP& gf, const GridP& gc, long long planes, const T* f, T* c,
+                           cudaStream_t st);
+template <typename T>
+void launch_prolong_space_add(int D, const GridP& gf, const GridP& gc, long long planes, const T* c, T* f,
+                              cudaStream_t st);
+template <typename T>
+void launch_restrict_time(long long Ns, int Ntc, int M, const double R[MAXM][2 * MAXM], const T* f, T* c,
+                          cudaStream_t st);
+template <typename T>
+void launch_prolong_time_add(long long Ns, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
+                             cudaStream_t st);
+template <typename T> void launch_cbar_time(long long Ns, int Ntc, const T* f, T* c, cudaStream_t st);
+
+// k_coarse.cu
+template <typename T> size_t coarse_setup_smem(const CoarseParams<T>& p);
+template <typename T> cudaError_t prepare_coarse_setup(const CoarseParams<T>& p);
+template <typename T> void launch_coarse_setup(const CoarseParams<T>& p, cudaStream_t st);
+template <typename T>
+void launch_coarse_solve(const CoarseParams<T>& p, int transpose, const T* r, T* e, T* in, cudaStream_t st);
+
+}  // namespace st

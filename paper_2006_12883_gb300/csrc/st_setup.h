@@ -1,0 +1,30 @@
+// Collocation setup data (host, double precision results of long double work).
+#pragma once
+
+#include <complex>
+
+#include "../../include/st.h"
+
+#ifndef MAXM
+#define MAXM ST_MAX_M
+#endif
+
+namespace st {
+
+struct Colloc {
+  int M;
+  double tau[MAXM];
+  double Q[MAXM][MAXM];
+  double K[MAXM][MAXM];               // DG matrix of Eq. (2.9), unit interval
+  std::complex<double> lam[MAXM];     // eigenvalues of Q (ordered, see st.h)
+  std::complex<double> V[MAXM][MAXM];
+  std::complex<double> Vinv[MAXM][MAXM];
+  double Pt[2 * MAXM][MAXM];          // slab-bisection prolongation
+  double Rt[MAXM][2 * MAXM];          // slab-bisection restriction
+  double QI_ie[MAXM][MAXM], QI_lu[MAXM][MAXM], QE[MAXM][MAXM];
+};
+
+// 0 on success, negative on failure.
+int colloc_setup(int M, Colloc* out);
+
+}  // namespace st

@@ -1,0 +1,104 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every entry
+point include/st.h declares, and its host-side setup (collocation nodes, Q,
+eigen-decomposition, time transfers, level planning) matches the oracle.  No
+GPU work is launched."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import collocation as col
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def stlib():
+    from paper_2006_12883_gb300 import build, stlib as s
+    build()
+    return s
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "st.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(st_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(stlib):
+    L = stlib.lib()
+    names = _declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(stlib._SIGS), set(names) - set(stlib._SIGS)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_host_collocation_setup_matches_oracle(stlib, M):
+    tau, Q, lam, V, Vi = stlib.st_collocation(M)
+    t0 = col.radau_right_nodes(M)
+    Q0 = col.collocation_matrix(t0)
+    l0, _ = col.q_eig(Q0)
+    assert np.abs(tau - t0).max() < 1e-15
+    assert np.abs(Q - Q0).max() < 1e-15
+    assert np.abs(lam - l0).max() < 1e-14
+    assert np.abs(Q @ V - V @ np.diag(lam)).max() < 1e-14
+    assert np.abs(V @ Vi - np.eye(M)).max() < 1e-13
+    # conjugate pairs are exact conjugates (the real transform relies on it)
+    for p in range(M):
+        if lam[p].imag > 0:
+            assert lam[p + 1] == np.conj(lam[p])
+            assert np.array_equal(V[:, p + 1], np.conj(V[:, p]))
+    Pt, Rt = stlib.st_time_transfer(M)
+    assert np.abs(Pt - col.time_prolongation(t0)).max() < 1e-13
+    assert np.abs(Rt - col.time_restriction(t0)).max() < 1e-12
+
+
+def test_plan_auto_mu_rule(stlib):
+    """AUTO_MU bisects space while mu_l = nu dt/h^2 >= mu_crit, else the slabs
+    (the mu rule of Section 4.2); SPACE bisects space only (SMG)."""
+    p = stlib.make_problem((256, 256), stlib.PERIODIC, 1e-2, 256, 3, reaction=stlib.LOGISTIC, rho=1.0)
+    info = stlib.st_plan(p)
+    lv = [info.level[l] for l in range(info.levels)]
+    assert lv[0].n[0] == 256 and lv[0].Nt == 256 and abs(lv[0].mu - 2.56) < 1e-12
+    for a, b in zip(lv, lv[1:]):
+        if a.next_kind == 1:
+            assert a.mu >= 1.0 or a.Nt <= 4
+            assert b.n[0] * 2 == a.n[0] and b.Nt == a.Nt and abs(b.dt - a.dt) < 1e-15
+        else:
+            assert a.next_kind == 2 and a.mu < 1.0
+            assert b.n[0] == a.n[0] and 2 * b.Nt == a.Nt and abs(b.dt - 2 * a.dt) < 1e-15
+    assert lv[-1].next_kind == 0 and lv[-1].Ns * 3 <= 96
+    o = stlib.make_opts(coarsening=stlib.COARSEN_SPACE)
+    info = stlib.st_plan(p, o)
+    assert all(info.level[l].Nt == 256 for l in range(info.levels))
+    assert info.level[info.levels - 1].Ns <= 16
+
+
+def test_plan_dirichlet_and_neumann_sizes(stlib):
+    p = stlib.make_problem((63,), stlib.DIRICHLET, 1.0, 16, 2)
+    info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE))
+    ns = [info.level[l].n[0] for l in range(info.levels)]
+    assert ns == [63, 31, 15]  # stops at <= coarse_max_points (16)
+    info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE, coarse_max_points=1))
+    ns = [info.level[l].n[0] for l in range(info.levels)]
+    assert ns == [63, 31, 15, 7, 3, 1]
+    p = stlib.make_problem((65,), stlib.NEUMANN, 1.0, 8, 3)
+    info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE, coarse_max_points=2))
+    ns = [info.level[l].n[0] for l in range(info.levels)]
+    assert ns == [65, 33, 17, 9, 5, 3, 2]
+    h = [info.level[l].h[0] for l in range(info.levels)]
+    assert all(abs(h[i + 1] - 2 * h[i]) < 1e-14 for i in range(len(h) - 1))
+
+
+def test_invalid_arguments_rejected(stlib):
+    for kw in [dict(nu=0.0), dict(M=6), dict(Nt=0)]:
+        args = dict(shape=(16,), bc=stlib.PERIODIC, nu=1.0, Nt=4, M=2)
+        args.update(kw)
+        p = stlib.make_problem(args["shape"], args["bc"], args["nu"], args["Nt"], args["M"])
+        with pytest.raises(stlib.StError) as ei:
+            stlib.st_plan(p)
+        assert ei.value.status == stlib.ST_ERR_INVALID_ARG

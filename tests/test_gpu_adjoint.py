@@ -1,0 +1,95 @@
+"""Discrete adjoint through the C ABI (transposed V-cycle, FP64 refinement):
+gradients against the oracle's adjoint, central finite differences of the
+GPU forward solve and the linear closed form."""
+import numpy as np
+import pytest
+
+import stgen
+from oracle import adjoint as oadj
+from oracle import space, system
+from tests.gpu_cases import Case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ADJ = Case("adjoint2d", (32, 32), space.PERIODIC, 1e-2, 8, 3, T=0.5, reaction=space.LOGISTIC, rho=1.0,
+           u0_kind="noise", seed=12887)
+
+
+def _target(case):
+    q = case.problem().with_params(nu=1.3e-2, rho=0.8)
+    return system.solve_sequential(q, case.u0())[-1, -1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_matches_oracle(prec):
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    target = _target(case)
+    S = case.solver(precision=stlib.FP64 if prec == "fp64" else stlib.FP32_REFINE, tol=1e-12)
+    U = S.zeros()
+    S.solve(U)
+    du0 = torch.empty(p.Ns, dtype=torch.float64, device="cuda")
+    dnu, drho, info = S.adjoint(U, target=torch.tensor(target, device="cuda"), du0=du0)
+    assert info["status"] == 0
+    _, _, (rnu, rrho, rdu0) = oadj.solve_and_gradients(p, case.u0(), target)
+    assert abs(dnu - rnu) <= 1e-6 * abs(rnu)
+    assert abs(drho - rrho) <= 1e-6 * abs(rrho)
+    assert np.linalg.norm(du0.cpu().numpy() - rdu0) <= 1e-6 * np.linalg.norm(rdu0)
+    S.close()
+
+
+def test_adjoint_central_fd_on_gpu():
+    """dPhi/dnu, dPhi/drho against central differences of GPU forward solves."""
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    target = _target(case)
+    S = case.solver(precision=stlib.FP64, tol=1e-13)
+    U = S.zeros()
+    S.solve(U)
+    dnu, drho, _ = S.adjoint(U, target=torch.tensor(target, device="cuda"))
+
+    def phi(nu, rho):
+        S.set_params(nu, rho)
+        V = S.zeros()
+        S.solve(V)
+        return oadj.objective(p, V.cpu().numpy().reshape(p.Nt, p.M, -1), target)
+
+    for name, th, g in (("nu", case.nu, dnu), ("rho", case.rho, drho)):
+        d = 1e-6 * th
+        args = [case.nu, case.rho]
+        i = 0 if name == "nu" else 1
+        a1 = list(args); a1[i] += d
+        a2 = list(args); a2[i] -= d
+        fd = (phi(*a1) - phi(*a2)) / (2 * d)
+        assert abs(g - fd) <= 1e-6 * abs(fd), (name, g, fd)
+    S.close()
+
+
+def test_adjoint_terminal_gradient_and_host_pointers():
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    S = case.solver(precision=stlib.FP64, tol=1e-12)
+    U = S.zeros()
+    S.solve(U)
+    gT = stgen.random_field((p.Ns,), 77)
+    du0 = torch.empty(p.Ns, dtype=torch.float64)  # host
+    dnu, drho, info = S.adjoint(U.cpu(), gT=torch.tensor(gT), du0=du0)
+    lam = oadj.adjoint_solve(p, U.cpu().numpy().reshape(p.Nt, p.M, -1), gT)
+    rnu, rrho, rdu0 = oadj.gradients(p, U.cpu().numpy().reshape(p.Nt, p.M, -1), lam)
+    assert abs(dnu - rnu) <= 1e-8 * abs(rnu)
+    assert np.linalg.norm(du0.numpy() - rdu0) <= 1e-8 * np.linalg.norm(rdu0)
+    S.close()
+
+
+def test_adjoint_neumann_unsupported():
+    from paper_2006_12883_gb300 import stlib
+    case = Case("neu", (17,), space.NEUMANN, 1.0, 4, 2)
+    S = case.solver()
+    U = S.zeros()
+    _, _, info = S.adjoint(U, target=torch.zeros(17, dtype=torch.float64, device="cuda"), raise_on_error=False)
+    assert info["status"] == stlib.ST_ERR_UNSUPPORTED
+    S.close()

@@ -1,0 +1,167 @@
+"""Level-wise steps of the space-time V-cycle (Eq. 4.1 hierarchy): level
+operator residuals (forward and transposed), cbar restriction, space / slab
+transfers, the exact coarsest solve and the smoothing step, through the C ABI
+against the oracle."""
+import numpy as np
+import pytest
+
+import stgen
+from oracle import multilevel as ml
+from oracle import space, system
+from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, Case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+P_ = space.PERIODIC
+# a case whose hierarchy mixes space and slab bisection (AUTO_MU) and one
+# with space bisection only (SPACE)
+MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise", seed=5)
+LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5]
+
+
+def _oracle_level(S, case, l, cbar):
+    li = S.level_info(l)
+    d = len(case.shape)
+    shape = tuple(li["n"][:d][::-1])
+    return ml.Level(shape=shape, bc=case.bc, Nt=li["Nt"], M=case.M, dt=li["dt"], nu=case.nu, X=case.X,
+                    cbar=cbar)
+
+
+def _setup(case, prec, **opts):
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    S = case.solver(precision=stlib.FP64 if prec == "fp64" else stlib.FP32_REFINE, **opts)
+    U = stgen.random_field((p.Nt, p.M, p.Ns), 11, 0.3) + 0.4
+    Ut = torch.tensor(U, device="cuda").reshape(S.field_shape)
+    S.linearize(Ut)
+    return p, S, U
+
+
+def _tol(prec):
+    return 1e-12 if prec == "fp64" else 3e-6
+
+
+@pytest.mark.parametrize("case", LEVEL_CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cbar_hierarchy(case, prec):
+    p, S, U = _setup(case, prec)
+    cb = system.cbar(p, U)
+    for l in range(S.num_levels()):
+        got = S.level_cbar(l).double().cpu().numpy()
+        got = got.reshape(got.shape[0], -1)
+        assert np.abs(got - cb).max() <= _tol(prec) * max(1, np.abs(cb).max()), l
+        if l + 1 < S.num_levels():
+            li = S.level_info(l)
+            lev = _oracle_level(S, case, l, cb)
+            if li["next_kind"] == 1:
+                cb = ml.restrict_space(case.bc, lev.shape, cb)
+            else:
+                cb = ml.restrict_cbar_time(cb)
+    S.close()
+
+
+@pytest.mark.parametrize("case", LEVEL_CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_level_residual_and_transfers(case, prec):
+    p, S, U = _setup(case, prec)
+    dt = S.cycle_dtype
+    for l in range(S.num_levels()):
+        cb = S.level_cbar(l).double().cpu().numpy()
+        cb = cb.reshape(cb.shape[0], -1)
+        lev = _oracle_level(S, case, l, cb)
+        shp = S.level_shape(l)
+        e = stgen.random_field(shp, 100 + l)
+        r = stgen.random_field(shp, 200 + l)
+        et = torch.tensor(e, dtype=dt, device="cuda")
+        rt = torch.tensor(r, dtype=dt, device="cuda")
+        e_, r_ = et.double().cpu().numpy(), rt.double().cpu().numpy()
+        for tr in (False, True):
+            if tr and case.bc == space.NEUMANN:
+                continue
+            got = S.level_residual(l, et, rt, transpose=tr).double().cpu().numpy().reshape(lev.Nt, p.M, -1)
+            ref = (ml.linear_residual_T if tr else ml.linear_residual)(lev, e_, r_)
+            scale = np.abs(e_).max() * (1 + lev.dt * case.nu * 4 * len(case.shape) / min(S.level_info(l)["h"][:len(case.shape)]) ** 2) + np.abs(r_).max()
+            assert np.abs(got - ref).max() <= _tol(prec) * scale, (l, tr)
+        if l + 1 < S.num_levels():
+            li = S.level_info(l)
+            for tr in (False, True):
+                c = S.level_restrict(l, rt, transpose=tr).double().cpu().numpy()
+                if li["next_kind"] == 1:
+                    ref = ml.restrict_space(case.bc, lev.shape, r_.reshape(lev.Nt, p.M, -1))
+                else:
+                    if tr:
+                        from oracle import collocation as col
+                        Pt = col.time_prolongation(col.radau_right_nodes(p.M))
+                        ref = np.einsum("km,nks->nms", Pt, r_.reshape(lev.Nt // 2, 2 * p.M, -1))
+                    else:
+                        ref = ml.restrict_time(p.M, r_.reshape(lev.Nt, p.M, -1))
+                assert np.abs(c.reshape(ref.shape) - ref).max() <= _tol(prec) * 4 * np.abs(r_).max(), (l, tr)
+                cshape = S.level_shape(l + 1)
+                cv = stgen.random_field(cshape, 300 + l)
+                ct = torch.tensor(cv, dtype=dt, device="cuda")
+                cv_ = ct.double().cpu().numpy().reshape(cshape[0], p.M, -1)
+                fine = et.clone()
+                S.level_prolong(l, ct, fine, transpose=tr)
+                if li["next_kind"] == 1:
+                    add = ml.prolong_space(case.bc, lev.shape, cv_)
+                else:
+                    if tr:
+                        from oracle import collocation as col
+                        Rt = col.time_restriction(col.radau_right_nodes(p.M))
+                        add = np.einsum("mk,nms->nks", Rt, cv_).reshape(lev.Nt, p.M, -1)
+                    else:
+                        add = ml.prolong_time(p.M, cv_)
+                ref = e_.reshape(add.shape) + add
+                assert np.abs(fine.double().cpu().numpy().reshape(ref.shape) - ref).max() <= \
+                    _tol(prec) * 4 * (np.abs(e_).max() + np.abs(cv_).max()), (l, tr)
+    S.close()
+
+
+@pytest.mark.parametrize("case", LEVEL_CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_coarse_solve_exact(case, transpose):
+    p, S, U = _setup(case, "fp64")
+    L = S.num_levels() - 1
+    cb = S.level_cbar(L).double().cpu().numpy()
+    lev = _oracle_level(S, case, L, cb.reshape(cb.shape[0], -1))
+    shp = S.level_shape(L)
+    r = stgen.random_field(shp, 400)
+    e = S.coarse_solve(torch.tensor(r, device="cuda"), transpose=transpose).cpu().numpy().reshape(lev.Nt, p.M, -1)
+    ref = (ml.coarse_solve_exact_T if transpose else ml.coarse_solve_exact)(lev, r.reshape(lev.Nt, p.M, -1))
+    assert np.abs(e - ref).max() <= 1e-10 * max(1, np.abs(ref).max())
+    S.close()
+
+
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, CUB3D], ids=lambda c: c.name)
+def test_smoothing_step_converged_inner(case):
+    """With many inner cycles the Q-diagonalised slab solve is exact, so one
+    smoothing step equals damped block Jacobi with exact slab solves."""
+    p, S, U = _setup(case, "fp64", inner_cycles=40, inner_coarse_iters=60)
+    l = 0
+    cb = S.level_cbar(l).cpu().numpy()
+    lev = _oracle_level(S, case, l, cb.reshape(cb.shape[0], -1))
+    shp = S.level_shape(l)
+    e = stgen.random_field(shp, 500)
+    r = stgen.random_field(shp, 501)
+    et = torch.tensor(e, device="cuda")
+    S.level_smooth(l, et, torch.tensor(r, device="cuda"))
+    ref = ml.smoothing_step_exact(lev, e.reshape(lev.Nt, p.M, -1), r.reshape(lev.Nt, p.M, -1),
+                                  S.level_info(l)["omega"])
+    err = np.abs(et.cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max()
+    assert err < 1e-9, err
+    S.close()
+
+
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5], ids=lambda c: c.name)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_level_vcycle_contracts(case, transpose):
+    """One V-cycle on A e - C e = r (zero start) reduces the residual."""
+    p, S, U = _setup(case, "fp64")
+    shp = S.level_shape(0)
+    r = torch.tensor(stgen.random_field(shp, 600), device="cuda")
+    e = S.level_vcycle(r, transpose=transpose)
+    res = S.level_residual(0, e, r, transpose=transpose)
+    ratio = float(res.norm() / r.norm())
+    assert ratio < 0.5, ratio
+    S.close()

@@ -1,0 +1,198 @@
+"""End-to-end solves through the C ABI (V-cycles inside FP64 defect
+correction / Newton) and SDC sweeps, against the oracle's direct solution of
+the collocation system; closed forms; error handling."""
+import math
+
+import numpy as np
+import pytest
+
+import stgen
+from oracle import sdc as osdc
+from oracle import space, system
+from tests.gpu_cases import HEAT1D, LOG2D, MONO, SOLVE_CASES, Case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+_REF = {}
+
+
+def _oracle_solution(case):
+    if case.name not in _REF:
+        _REF[case.name] = system.solve_sequential(case.problem(), case.u0())
+    return _REF[case.name]
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_matches_oracle(case, prec):
+    from paper_2006_12883_gb300 import stlib
+    tol = 1e-12
+    S = case.solver(precision=stlib.FP64 if prec == "fp64" else stlib.FP32_REFINE, tol=tol, max_iters=200)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0 and info["rel_residual"] <= tol
+    ref = _oracle_solution(case)
+    err = _rel(U.cpu().numpy().reshape(ref.shape), ref)
+    # all-FP64 path within 1e-10, FP32 cycle + FP64 refinement within 1e-8
+    assert err <= (1e-10 if prec == "fp64" else 1e-8), err
+    h = info["history"]
+    assert all(b < a for a, b in zip(h[1:], h[2:])), h  # monotone after the first cycle
+    S.close()
+
+
+def test_heat_closed_form_and_vcycle_api():
+    from paper_2006_12883_gb300 import stlib
+    case = HEAT1D
+    S = case.solver(precision=stlib.FP64, tol=1e-13)
+    U = S.zeros()
+    norms = [S.vcycle(U) for _ in range(12)]
+    assert norms[-1] < 1e-11 * norms[0]
+    x = stgen.coords1d(space.DIRICHLET, 63)
+    p = case.problem()
+
+    def R(z):
+        return (1 + z / 3) / (1 - 2 * z / 3 + z * z / 6)
+
+    exact = sum(a * R(p.dt * system.sine_mode_eigenvalue(k, 63, 1.0)) ** 16 * np.sin(k * np.pi * x)
+                for k, a in ((1, 1.0), (3, 0.5)))
+    assert np.abs(U.cpu().numpy()[-1, -1] - exact).max() < 1e-11
+    S.close()
+
+
+@pytest.mark.parametrize("coarsening", [0, 1])
+def test_space_only_and_auto_mu(coarsening):
+    from paper_2006_12883_gb300 import stlib
+    S = LOG2D.solver(coarsening=coarsening, tol=1e-10, max_iters=100)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0
+    ref = _oracle_solution(LOG2D)
+    assert _rel(U.cpu().numpy().reshape(ref.shape), ref) < 1e-8
+    S.close()
+
+
+def test_host_pointer_solve():
+    case = LOG2D
+    S = case.solver(tol=1e-10)
+    U = torch.zeros(S.field_shape, dtype=torch.float64)  # host memory
+    info = S.solve(U)
+    assert info["status"] == 0
+    ref = _oracle_solution(case)
+    assert _rel(U.numpy().reshape(ref.shape), ref) < 1e-8
+    S.close()
+
+
+def test_full_size_sampled_residual_and_truncation():
+    """2D logistic at 256^2 x 256 slabs x M=3 (50M space-time dofs): the GPU
+    solution's collocation residual, evaluated point by point by the oracle at
+    sampled points, is at the solver tolerance; slab 1 equals the oracle's
+    one-slab solve (causality of Eq. 3.4)."""
+    from paper_2006_12883_gb300 import stlib
+    case = Case("logistic2d_256", (256, 256), space.PERIODIC, 1e-2, 256, 3, reaction=space.LOGISTIC, rho=1.0,
+                u0_kind="noise", seed=12884)
+    S = case.solver(tol=1e-10, max_iters=60)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0, info
+    Uh = U.cpu().numpy().reshape(case.Nt, case.M, -1)
+    p = case.problem()
+    u0 = case.u0()
+    rng = np.random.default_rng(0)
+    slabs = list(rng.integers(0, case.Nt, 64))
+    pts = list(rng.integers(0, p.Ns, 64))
+    Gs = system.residual_points(p, Uh, u0, slabs, pts)
+    from tests.gpu_cases import residual_scale
+    bound = 1e-10 * system.reference_norm(p, u0) + 1e-13 * residual_scale(p, Uh[:2])
+    assert np.abs(Gs).max() <= bound, (np.abs(Gs).max(), bound)
+    first = system.solve_sequential(p, u0, nslabs=1)
+    assert _rel(Uh[:1], first) < 1e-8
+    S.close()
+
+
+# ------------------------------------------------------------------ SDC
+
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, MONO], ids=lambda c: c.name)
+@pytest.mark.parametrize("kind", [0, 1])
+def test_sdc_one_sweep_matches_oracle(case, kind):
+    """One IMEX sweep (correction form, converged inner solves) equals the
+    oracle's standard-form sweep with exact spatial solves."""
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    S = case.solver(precision=stlib.FP64, sdc_qdelta=kind, sdc_inner_cycles=40, inner_coarse_iters=60)
+    U0 = stgen.random_field((p.Nt, p.M, p.Ns), 21, 0.2) + np.tile(case.u0(), (p.Nt, p.M, 1))
+    U = torch.tensor(U0, device="cuda").reshape(S.field_shape)
+    S.sdc_sweep(U, 1)
+    ref = osdc.sdc_sweep(p, U0, case.u0(), "IE" if kind == 0 else "LU")
+    assert _rel(U.cpu().numpy().reshape(ref.shape), ref) < 1e-9
+    S.close()
+
+
+def test_sdc_converges_to_collocation():
+    """Config-1 heat problem: SDC sweeps from the spread initial value reach a
+    1e-10 residual and the collocation solution."""
+    from paper_2006_12883_gb300 import stlib
+    case = HEAT1D
+    p = case.problem()
+    S = case.solver(precision=stlib.FP32_REFINE, sdc_inner_cycles=3)
+    U = torch.tensor(np.tile(case.u0(), (p.Nt, p.M, 1)), device="cuda").reshape(S.field_shape)
+    r0 = system.reference_norm(p, case.u0())
+    rel = 1.0
+    for _ in range(200):
+        S.sdc_sweep(U, 1)
+        rel = S.residual(U) / r0
+        if rel < 1e-10:
+            break
+    assert rel < 1e-10
+    ref = _oracle_solution(case)
+    assert _rel(U.cpu().numpy().reshape(ref.shape), ref) < 1e-8
+    S.close()
+
+
+# ------------------------------------------------------------- failures
+
+def test_error_statuses():
+    from paper_2006_12883_gb300 import stlib
+    p = stlib.make_problem((8,), stlib.PERIODIC, -1.0, 4, 2)  # nu <= 0
+    with pytest.raises(stlib.StError) as ei:
+        stlib.st_plan(p)
+    assert ei.value.status == stlib.ST_ERR_INVALID_ARG
+    p = stlib.make_problem((100, 100), stlib.PERIODIC, 1.0, 4, 2)  # 100 -> 50 -> 25: coarsest too big
+    with pytest.raises(stlib.StError) as ei:
+        stlib.st_plan(p)
+    assert ei.value.status == stlib.ST_ERR_UNSUPPORTED
+    # max_iters = 1: not converged, info filled
+    S = LOG2D.solver(max_iters=1, tol=1e-14)
+    U = S.zeros()
+    info = S.solve(U, raise_on_error=False)
+    assert info["status"] == stlib.ST_ERR_NOT_CONVERGED and info["iterations"] == 1
+    S.close()
+    # NaN in u0: diverged, no abort
+    bad = Case("nan", (16, 16), space.PERIODIC, 0.01, 4, 2, reaction=space.LOGISTIC, rho=1.0)
+    u0 = bad.u0()
+    u0[5] = np.nan
+    S = stlib.Solver(bad.shape, bad.bc, bad.nu, bad.Nt, bad.M, u0, reaction=bad.reaction, rho=1.0)
+    info = S.solve(S.zeros(), raise_on_error=False)
+    assert info["status"] == stlib.ST_ERR_DIVERGED
+    S.close()
+
+
+def test_allocator_failure_is_oom():
+    from paper_2006_12883_gb300 import stlib
+    import ctypes
+    case = LOG2D
+    u0 = torch.tensor(case.u0())
+    prob = stlib.make_problem(case.shape[::-1], case.bc, case.nu, case.Nt, case.M, reaction=case.reaction,
+                              rho=case.rho, u0_ptr=u0.data_ptr())
+    rt = stlib.StRuntime()
+    rt.stream = None
+    rt.alloc = stlib.ALLOC_FN(lambda n, s, c: None)
+    rt.free = stlib.FREE_FN(lambda p, n, s, c: None)
+    h = ctypes.c_void_p()
+    s = stlib.lib().st_create(ctypes.byref(prob), None, ctypes.byref(rt), ctypes.byref(h))
+    assert s == stlib.ST_ERR_OOM and not h.value

@@ -252,3 +252,32 @@ def test_sdc_fixed_point_and_convergence(kind):
     for _ in range(30):
         U = sdc.sdc_sweep(p, U, u0, kind)
     assert np.abs(U - Ustar).max() < 1e-12
+
+
+def test_transposed_level_operator_dot_product():
+    """<(A - C) e, v> = <e, (A^T - C^T) v> for the level operators."""
+    lev = ml.Level(shape=(6,), bc=P, Nt=4, M=3, dt=0.1, nu=0.3, X=1.0,
+                   cbar=stgen.random_field((4, 6), 28, 0.3))
+    e = stgen.random_field((4, 3, 6), 29)
+    v = stgen.random_field((4, 3, 6), 30)
+    z = np.zeros_like(e)
+    lhs = float(np.sum(-ml.linear_residual(lev, e, z) * v))
+    rhs = float(np.sum(e * -ml.linear_residual_T(lev, v, z)))
+    assert abs(lhs - rhs) < 1e-12 * max(1, abs(lhs))
+    r = stgen.random_field((4, 3, 6), 31)
+    x = ml.coarse_solve_exact_T(lev, r)
+    assert np.abs(ml.linear_residual_T(lev, x, r)).max() < 1e-13
+
+
+def test_residual_points_matches_full_residual():
+    for bc, shape in [(P, (6, 8)), (D, (5, 3, 7)), (N, (9,))]:
+        p = system.Problem(shape=shape, bc=bc, nu=0.2, Nt=3, M=3, reaction=space.CUBIC, rho=1.5)
+        Ns = int(np.prod(shape))
+        U = stgen.random_field((3, 3, Ns), 50)
+        u0 = stgen.random_field((Ns,), 51)
+        G = system.residual(p, U, u0)
+        slabs = [0, 1, 2, 2, 0]
+        pts = [0, Ns - 1, Ns // 2, 1, Ns // 3]
+        Gp = system.residual_points(p, U, u0, slabs, pts)
+        for t, (n, s) in enumerate(zip(slabs, pts)):
+            assert np.abs(Gp[t] - G[n, :, s]).max() < 1e-11
