@@ -37,6 +37,9 @@ WORKLOAD = dict(workload="logistic2d_256x256_Nt256_M3", grid=[256, 256], bc="per
                 nu=1e-2, rho=1.0, T=1.0, reaction="logistic rho*u*(1-u)", seed=12884,
                 u0="uniform[0,1) noise smoothed by 10 neighbour-averaging passes")
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor) per the pool's hardware notes
+KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
+                 ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
+                 ("prolong_add", 7), ("vcycle_graph", 4))
 
 
 def env_int(name, default):
@@ -183,6 +186,17 @@ def run_ours(args):
     D = w["Nt"] * w["M"] * shape[0] * shape[1]
     U = S.zeros()
     stream = torch.cuda.current_stream()
+    if args.probe:
+        # each hot kernel in isolation at full size (for profiler captures)
+        S.linearize(U)
+        out = {}
+        for name, which in KERNEL_PROBES[:-1]:
+            kms, kb = S.time_kernel(which, U, iters=2)
+            out[name] = {"ms": kms, "GBps": kb / (kms / 1e3) / 1e9}
+        if rank == 0:
+            print(json.dumps({"mode": "probe", "kernels": out}), flush=True)
+        S.close()
+        return
     for _ in range(args.warmup):
         S.vcycle(U)
     torch.cuda.synchronize()
@@ -210,6 +224,12 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * D / (ms / 1e3)
+    if args.only_steps:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
+                              "mode": "only-steps (profiling run)"}), flush=True)
+        S.close()
+        return
 
     # e2e through the C ABI with host buffers (H2D + D2H of U inside every step)
     Uh = torch.zeros(S.field_shape, dtype=torch.float64).pin_memory()
@@ -232,11 +252,7 @@ def run_ours(args):
     stats = S.stats()
     # per-kernel live timings (CUDA events on the library's launching stream)
     kernels = {}
-    for name, which in (("fine_residual_fp64", stlib.KERNEL_FINE_RESIDUAL),
-                        ("level_residual_transform", stlib.KERNEL_LEVEL_RESIDUAL),
-                        ("slab_jacobi", stlib.KERNEL_JACOBI),
-                        ("backtransform_update", stlib.KERNEL_BACKTRANSFORM),
-                        ("vcycle_graph", stlib.KERNEL_VCYCLE)):
+    for name, which in KERNEL_PROBES:
         kms, kb = S.time_kernel(which, U, iters=max(5, args.steps // 2))
         kernels[name] = {"ms": kms, "bytes": kb, "GBps": (kb / (kms / 1e3) / 1e9) if kb else None}
     hbm, src = measured_peaks()
@@ -334,6 +350,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true", help="warm-up and timed steps only (profiling)")
+    ap.add_argument("--probe", action="store_true", help="launch each hot kernel alone (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

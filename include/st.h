@@ -283,7 +283,10 @@ enum {
   ST_KERNEL_LEVEL_RESIDUAL = 1,/* level-0 residual r - A e + C e with the Q-eigenbasis transform */
   ST_KERNEL_JACOBI = 2,        /* one Jacobi sweep of the level-0 shifted slab systems */
   ST_KERNEL_BACKTRANSFORM = 3, /* level-0 back-transform + damped block-Jacobi update */
-  ST_KERNEL_VCYCLE = 4         /* one whole V-cycle (graph replay), not a single kernel */
+  ST_KERNEL_VCYCLE = 4,        /* one whole V-cycle (graph replay), not a single kernel */
+  ST_KERNEL_SHIFTED_RESIDUAL = 5, /* residual of the level-0 shifted slab systems */
+  ST_KERNEL_INNER_RESTRICT = 6,   /* full weighting of that residual to the next inner grid */
+  ST_KERNEL_PROLONG = 7           /* linear interpolation + correction, inner grid 1 -> 0 */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream

@@ -14,15 +14,15 @@
 namespace st {
 
 // One block per slab: Gauss-Jordan with partial pivoting on [A | I] in
-// shared memory (double), then the inverse and the coupling matrices.
+// shared memory (cycle precision T; the pivot search is a warp argmax), then
+// the inverse and the coupling matrices.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_setup(CoarseParams<T> p) {
-  extern __shared__ double sm[];
+  extern __shared__ unsigned char smraw[];
+  T* A = reinterpret_cast<T*>(smraw);  // [K][2K]
   const int K = p.K, Nc = p.Nc, M = p.M;
   const int W2 = 2 * K;
-  double* A = sm;                 // [K][2K]
   __shared__ int piv;
-  __shared__ double pval;
   const int n = blockIdx.x;
   for (int t = threadIdx.x; t < K * W2; t += blockDim.x) {
     const int r = t / W2, c = t % W2;
@@ -35,74 +35,75 @@ __global__ void __launch_bounds__(256) k_coarse_setup(CoarseParams<T> p) {
     } else {
       v = (c - K == r) ? 1.0 : 0.0;
     }
-    A[t] = v;
+    A[t] = (T)v;
   }
   __syncthreads();
   for (int col = 0; col < K; ++col) {
-    if (threadIdx.x == 0) {
-      int best = col;
-      double bv = fabs(A[col * W2 + col]);
-      for (int r = col + 1; r < K; ++r) {
-        const double v = fabs(A[r * W2 + col]);
+    if (threadIdx.x < 32) {
+      int best = -1;
+      T bv = (T)-1;
+      for (int r = col + (int)threadIdx.x; r < K; r += 32) {
+        const T v = fabs(A[r * W2 + col]);
         if (v > bv) { bv = v; best = r; }
       }
-      piv = best;
-    }
-    __syncthreads();
-    if (piv != col) {
-      for (int c = threadIdx.x; c < W2; c += blockDim.x) {
-        const double t0 = A[col * W2 + c];
-        A[col * W2 + c] = A[piv * W2 + c];
-        A[piv * W2 + c] = t0;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int ob = __shfl_down_sync(0xffffffffu, best, o);
+        if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
       }
+      if (threadIdx.x == 0) piv = best < 0 ? col : best;
     }
     __syncthreads();
-    if (threadIdx.x == 0) pval = A[col * W2 + col];
+    const int pr = piv;
+    if (pr != col) {
+      for (int c = threadIdx.x; c < W2; c += blockDim.x) {
+        const T t0 = A[col * W2 + c];
+        A[col * W2 + c] = A[pr * W2 + c];
+        A[pr * W2 + c] = t0;
+      }
+      __syncthreads();
+    }
+    const T inv = (T)1 / A[col * W2 + col];
     __syncthreads();
-    const double inv = 1.0 / pval;
     for (int c = threadIdx.x; c < W2; c += blockDim.x) A[col * W2 + c] *= inv;
     __syncthreads();
     for (int t = threadIdx.x; t < K * W2; t += blockDim.x) {
       const int r = t / W2, c = t % W2;
-      if (r != col) {
-        const double f = A[r * W2 + col];
-        if (c != col) A[t] -= f * A[col * W2 + c];
-      }
+      if (r != col && c != col) A[t] -= A[r * W2 + col] * A[col * W2 + c];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < K; r += blockDim.x)
-      if (r != col) A[r * W2 + col] = 0.0;
+      if (r != col) A[r * W2 + col] = (T)0;
     __syncthreads();
   }
   // inverse is A[:, K:2K]
   T* Ai = p.Ainv + (long long)n * K * K;
   for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
     const int r = t / K, c = t % K;
-    Ai[t] = (T)A[r * W2 + K + c];
+    Ai[t] = A[r * W2 + K + c];
   }
   // forward coupling W = Ainv (1 (x) I): W[r][q] = sum_m Ainv[r][m Nc + q]
   T* W = p.Wf + (long long)n * K * Nc;
   T* Wt = p.Wt + (long long)n * K * Nc;
   for (int t = threadIdx.x; t < K * Nc; t += blockDim.x) {
     const int r = t / Nc, q = t % Nc;
-    double acc = 0.0;
+    T acc = (T)0;
     for (int m = 0; m < M; ++m) acc += A[r * W2 + K + m * Nc + q];
-    W[t] = (T)acc;
+    W[t] = acc;
     // transposed coupling Wt = Ainv^T (e_M (x) I): Wt[r][q] = Ainv[(M-1)Nc+q][r]
-    Wt[t] = (T)A[((M - 1) * Nc + q) * W2 + K + r];
+    Wt[t] = A[((M - 1) * Nc + q) * W2 + K + r];
   }
-  __syncthreads();
   T* Wr = p.Wfrow + (long long)n * Nc * Nc;
   T* Wtr = p.Wtrow + (long long)n * Nc * Nc;
   for (int t = threadIdx.x; t < Nc * Nc; t += blockDim.x) {
     const int pp = t / Nc, q = t % Nc;
-    double accf = 0.0, acct = 0.0;
+    T accf = (T)0, acct = (T)0;
     for (int m = 0; m < M; ++m) {
-      accf += A[((M - 1) * Nc + pp) * W2 + K + m * Nc + q];           // W[(M-1)Nc+pp][q]
-      acct += A[((M - 1) * Nc + q) * W2 + K + m * Nc + pp];           // sum_m Wt[m Nc+pp][q]
+      accf += A[((M - 1) * Nc + pp) * W2 + K + m * Nc + q];  // W[(M-1)Nc+pp][q]
+      acct += A[((M - 1) * Nc + q) * W2 + K + m * Nc + pp];  // sum_m Wt[m Nc+pp][q]
     }
-    Wr[t] = (T)accf;
-    Wtr[t] = (T)acct;
+    Wr[t] = accf;
+    Wtr[t] = acct;
   }
 }
 
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(128) k_coarse_finish(CoarseParams<T> p, int tr
 
 template <typename T>
 size_t coarse_setup_smem(const CoarseParams<T>& p) {
-  return (size_t)p.K * 2 * p.K * sizeof(double);
+  return (size_t)p.K * 2 * p.K * sizeof(T);
 }
 
 template <typename T>

@@ -16,50 +16,49 @@ namespace st {
 // ---------------------------------------------------------------------------
 template <int D, typename TR, typename TC>
 __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
-  const long long Ns = p.g.Ns;
-  const int M = p.M;
-  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   double sq = 0.0;
-  if (idx < Ns * nchunks) {
-    const long long s = idx % Ns;
-    const int c = (int)(idx / Ns);
+  if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
+    int c, s, i, j, k;
+    split_index(idx, p.g, c, s, i, j, k);
+    const Nbr nb = make_nbr<D>(i, j, k, p.g);
+    const long long Ns = p.g.Ns;
+    const int M = p.M;
     const int n0 = c * p.chunk;
     const int n1 = min(n0 + p.chunk, p.Nt);
-    int i, j, k;
-    decompose(s, p.g, i, j, k);
-    const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
     double prev = (n0 == 0) ? p.u0[s] : p.U[((long long)(n0 - 1) * M + (M - 1)) * Ns + s];
     TR* R = (TR*)p.R;
     TC* cb = (TC*)p.cbar;
+    const double invM = 1.0 / M;
     for (int n = n0; n < n1; ++n) {
+      const long long base = (long long)n * M * Ns + s;
       double u[MAXM], F[MAXM];
-      double cbs = 0.0;
+      double cbs = 0.0, ulast = 0.0;
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
         if (m < M) {
-          const double* pl = p.U + ((long long)n * M + m) * Ns;
+          const double* pl = p.U + (long long)n * M * Ns + (long long)m * Ns;
           const double um = pl[s];
           u[m] = um;
-          F[m] = p.nu * lap_at<D, double, double>(pl, s, i, j, k, p.g, um, ihx, ihy, ihz) +
-                 react<double>(p.reaction, p.rho, um);
-          cbs += dreact<double>(p.reaction, p.rho, um);
+          if (m == M - 1) ulast = um;
+          F[m] = lap_nb<D, double, double>(pl, s, nb, um, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2,
+                                            react<double>(p.reaction, p.rho, um));
+          if (cb) cbs += dreact<double>(p.reaction, p.rho, um);
         }
       }
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
         if (m < M) {
-          double acc = 0.0;
+          double g = prev - u[m];
 #pragma unroll
           for (int q = 0; q < MAXM; ++q)
-            if (q < M) acc += p.dtq[m][q] * F[q];
-          const double g = (prev - u[m]) + acc;
-          sq += g * g;
-          if (R) R[((long long)n * M + m) * Ns + s] = (TR)g;
+            if (q < M) g = fma(p.dtq[m][q], F[q], g);
+          sq = fma(g, g, sq);
+          if (R) R[base + (long long)m * Ns] = (TR)g;
         }
       }
-      if (cb) cb[(long long)n * Ns + s] = (TC)(cbs / M);
-      prev = u[M - 1];
+      if (cb) cb[(long long)n * Ns + s] = (TC)(cbs * invM);
+      prev = ulast;
     }
   }
   if (p.partial) {
@@ -77,34 +76,32 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
 // ---------------------------------------------------------------------------
 template <int D, typename TR>
 __global__ void __launch_bounds__(256) k_adj_residual(ResidParams p) {
-  const long long Ns = p.g.Ns;
-  const int M = p.M;
-  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   double sq = 0.0;
-  if (idx < Ns * nchunks) {
-    const long long s = idx % Ns;
-    const int c = (int)(idx / Ns);
+  if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
+    int c, s, i, j, k;
+    split_index(idx, p.g, c, s, i, j, k);
+    const Nbr nb = make_nbr<D>(i, j, k, p.g);
+    const long long Ns = p.g.Ns;
+    const int M = p.M;
     const int n0 = c * p.chunk;
     const int n1 = min(n0 + p.chunk, p.Nt);
-    int i, j, k;
-    decompose(s, p.g, i, j, k);
-    const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
     double next = 0.0;  // sum_m lambda_{n+1,m}
     if (n1 < p.Nt) {
       for (int m = 0; m < M; ++m) next += p.lam[((long long)n1 * M + m) * Ns + s];
     }
     TR* R = (TR*)p.R;
     for (int n = n1 - 1; n >= n0; --n) {
+      const long long base = (long long)n * M * Ns + s;
       double l[MAXM], Ll[MAXM];
       double sum = 0.0;
 #pragma unroll
       for (int m = 0; m < MAXM; ++m) {
         if (m < M) {
-          const double* pl = p.lam + ((long long)n * M + m) * Ns;
+          const double* pl = p.lam + (long long)n * M * Ns + (long long)m * Ns;
           const double lm = pl[s];
           l[m] = lm;
-          Ll[m] = p.nu * lap_at<D, double, double>(pl, s, i, j, k, p.g, lm, ihx, ihy, ihz);
+          Ll[m] = lap_nb<D, double, double>(pl, s, nb, lm, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, 0.0);
           sum += lm;
         }
       }
@@ -115,19 +112,18 @@ __global__ void __launch_bounds__(256) k_adj_residual(ResidParams p) {
 #pragma unroll
           for (int m = 0; m < MAXM; ++m)
             if (m < M) {
-              accL += p.dtq[a][m] * Ll[m];
-              accl += p.dtq[a][m] * l[m];
+              accL = fma(p.dtq[a][m], Ll[m], accL);
+              accl = fma(p.dtq[a][m], l[m], accl);
             }
           double rp = 0.0;
-          if (p.reaction != ST_REACTION_NONE)
-            rp = dreact<double>(p.reaction, p.rho, p.U[((long long)n * M + a) * Ns + s]);
-          double g = accL + rp * accl - l[a];
+          if (p.reaction != ST_REACTION_NONE) rp = dreact<double>(p.reaction, p.rho, p.U[base + (long long)a * Ns]);
+          double g = fma(rp, accl, accL) - l[a];
           if (a == M - 1) {
             g += next;
             if (n == p.Nt - 1 && p.gT) g += p.gT[s];
           }
-          sq += g * g;
-          if (R) R[((long long)n * M + a) * Ns + s] = (TR)g;
+          sq = fma(g, g, sq);
+          if (R) R[base + (long long)a * Ns] = (TR)g;
         }
       }
       next = sum;
@@ -149,13 +145,11 @@ template <int D>
 __global__ void __launch_bounds__(256) k_gradients(ResidParams p, double* partial2, double* du0) {
   const long long Ns = p.g.Ns;
   const int M = p.M;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   double gnu = 0.0, grho = 0.0;
-  if (idx < Ns * p.Nt) {
-    const long long s = idx % Ns;
-    const int n = (int)(idx / Ns);
-    int i, j, k;
-    decompose(s, p.g, i, j, k);
+  if (idx < (unsigned)p.Nt * (unsigned)p.g.Ns) {
+    int n, s, i, j, k;
+    split_index(idx, p.g, n, s, i, j, k);
     const double ihx = p.g.ih2[0], ihy = p.g.ih2[1], ihz = p.g.ih2[2];
     double l[MAXM];
     double sum = 0.0;
@@ -214,12 +208,10 @@ __global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, 
                                                  const T* __restrict__ G, const T* __restrict__ delta,
                                                  const double* __restrict__ U, T* __restrict__ y) {
   const long long Ns = g.Ns;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Ns * Nt) return;
-  const long long s = idx % Ns;
-  const int n = (int)(idx / Ns);
-  int i, j, k;
-  decompose(s, g, i, j, k);
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)Nt * (unsigned)g.Ns) return;
+  int n, s, i, j, k;
+  split_index(idx, g, n, s, i, j, k);
   const double ihx = g.ih2[0], ihy = g.ih2[1], ihz = g.ih2[2];
   double acc = (double)G[((long long)n * M + m) * Ns + s];
   for (int q = 0; q < m; ++q) {
@@ -250,10 +242,7 @@ __global__ void __launch_bounds__(256) k_scatter_plane(const T* __restrict__ src
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-long long residual_blocks(const ResidParams& p) {
-  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
-  return (p.g.Ns * nchunks + 255) / 256;
-}
+long long residual_blocks(const ResidParams& p) { return (p.g.Ns * p.nchunks + 255) / 256; }
 
 template <typename TR, typename TC>
 static void launch_res_t(int D, const ResidParams& p, cudaStream_t st) {

@@ -1,34 +1,51 @@
 // Cycle-precision kernels of the space-time V-cycle (templated on T = float
 // or double): the level operator residual with the Q-eigenbasis transform,
-// the back-transform with damped block-Jacobi update, the spatial multigrid
-// of the shifted slab systems, and the space / slab transfers (Eq. 4.1).
+// the spatial multigrid of the shifted slab systems (with the back-transform
+// and damped block-Jacobi update fused into its last sweep), and the space /
+// slab transfers (Eq. 4.1).
+//
+// Indexing: one thread per (slab or slab chunk, point), flattened into a
+// 32-bit index (the host guarantees Ns * slabs < 2^31); divisions by the grid
+// sizes use precomputed multiply-shift constants.
 #include "st_kernels.cuh"
 
 namespace st {
 
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// One group's zero-start Jacobi value  omega D^{-1} y  (D = 1 - s d').
+template <typename T>
+__device__ __forceinline__ void zero_jacobi(T yr, T yi, int cplx, T sr, T si, T dprime, T omega, T& zr, T& zi) {
+  if (!cplx) {
+    zr = omega * yr / ((T)1 - sr * dprime);
+    zi = (T)0;
+  } else {
+    const T dr = (T)1 - sr * dprime, di = -si * dprime;
+    const T inv = omega / (dr * dr + di * di);
+    zr = (yr * dr + yi * di) * inv;
+    zi = (yi * dr - yr * di) * inv;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Level residual  res = r - A_l e + C e   (transpose: r - A_l^T e + C^T e)
 //   forward:   res_a = r_a - e_a + sum_b W[a][b] (nu Lap e_b + cbar e_b) + e_{n-1,M}
 //   transpose: res_a = r_a - e_a + sum_b W[a][b] (nu Lap e_b + cbar e_b)
 //                      + [a = M-1] sum_b e_{n+1,b}
-// (W = dt_l Q or dt_l Q^T).  With transform = 1 the output is F * res.
+// (W = dt_l Q or dt_l Q^T).  With transform = 1 the output is F * res, and
+// with zout set also the zero-start Jacobi iterate of the shifted systems.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.nchunks * (unsigned)p.g.Ns) return;
+  int c, s, i, j, k;
+  split_index(idx, p.g, c, s, i, j, k);
+  const Nbr nb = make_nbr<D>(i, j, k, p.g);
   const long long Ns = p.g.Ns;
   const int M = p.M;
-  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Ns * nchunks) return;
-  const long long s = idx % Ns;
-  const int c = (int)(idx / Ns);
   const int n0 = c * p.chunk;
   const int n1 = min(n0 + p.chunk, p.Nt);
-  int i, j, k;
-  decompose(s, p.g, i, j, k);
-  const T ihx = (T)p.g.ih2[0], ihy = (T)p.g.ih2[1], ihz = (T)p.g.ih2[2];
   const bool hase = (p.e != nullptr);
   T carry = (T)0;
   if (hase) {
@@ -38,56 +55,74 @@ __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
       for (int b = 0; b < M; ++b) carry += p.e[((long long)n1 * M + b) * Ns + s];
     }
   }
+  const T dlap = p.sc.k2;
   for (int t = 0; t < n1 - n0; ++t) {
     const int n = p.transpose ? (n1 - 1 - t) : (n0 + t);
+    const long long base = (long long)n * M * Ns + s;
     T res[MAXM];
     const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
     if (hase) {
       T ev[MAXM], Fe[MAXM];
-      T sum = (T)0;
+      T sum = (T)0, last = (T)0;
 #pragma unroll
       for (int b = 0; b < MAXM; ++b) {
         if (b < M) {
-          const T* pl = p.e + ((long long)n * M + b) * Ns;
+          const T* pl = p.e + (long long)n * M * Ns + (long long)b * Ns;
           const T eb = pl[s];
           ev[b] = eb;
-          Fe[b] = p.nu * lap_at<D, T, T>(pl, s, i, j, k, p.g, eb, ihx, ihy, ihz) + cb * eb;
+          Fe[b] = lap_nb<D, T, T>(pl, s, nb, eb, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * eb);
           sum += eb;
+          if (b == M - 1) last = eb;
         }
       }
 #pragma unroll
       for (int a = 0; a < MAXM; ++a) {
         if (a < M) {
-          T acc = p.r[((long long)n * M + a) * Ns + s] - ev[a];
+          T acc = p.r[base + (long long)a * Ns] - ev[a];
 #pragma unroll
           for (int b = 0; b < MAXM; ++b)
-            if (b < M) acc += p.W[a][b] * Fe[b];
-          if (!p.transpose) acc += carry;
-          else if (a == M - 1) acc += carry;
+            if (b < M) acc = fma(p.W[a][b], Fe[b], acc);
+          if (!p.transpose || a == M - 1) acc += carry;
           res[a] = acc;
         }
       }
-      carry = p.transpose ? sum : ev[M - 1];
+      carry = p.transpose ? sum : last;
     } else {
 #pragma unroll
       for (int a = 0; a < MAXM; ++a)
-        if (a < M) res[a] = p.r[((long long)n * M + a) * Ns + s];
+        if (a < M) res[a] = p.r[base + (long long)a * Ns];
     }
     if (p.transform) {
+      T y[MAXM];
 #pragma unroll
       for (int a = 0; a < MAXM; ++a) {
         if (a < M) {
           T acc = (T)0;
 #pragma unroll
           for (int b = 0; b < MAXM; ++b)
-            if (b < M) acc += p.F[a][b] * res[b];
-          p.out[((long long)n * M + a) * Ns + s] = acc;
+            if (b < M) acc = fma(p.F[a][b], res[b], acc);
+          y[a] = acc;
+          p.out[base + (long long)a * Ns] = acc;
+        }
+      }
+      if (p.zout) {
+        const T dprime = dlap + cb;
+#pragma unroll
+        for (int pl = 0; pl < MAXM; ++pl) {
+          const int kd = p.sh.kind[pl];
+          if (kd == SH_REAL || kd == SH_RE) {
+            T zr, zi;
+            const T yi = (pl + 1 < MAXM && kd == SH_RE) ? y[pl + 1 < MAXM ? pl + 1 : pl] : (T)0;
+            zero_jacobi<T>(y[pl], yi, kd == SH_RE, p.sh.sr[pl], p.sh.si[pl], dprime, p.omega_j, zr, zi);
+            p.zout[base + (long long)pl * Ns] = zr;
+            if (kd == SH_RE) p.zout[base + (long long)(pl + 1) * Ns] = zi;
+          }
         }
       }
     } else {
 #pragma unroll
       for (int a = 0; a < MAXM; ++a)
-        if (a < M) p.out[((long long)n * M + a) * Ns + s] = res[a];
+        if (a < M) p.out[base + (long long)a * Ns] = res[a];
     }
   }
 }
@@ -95,7 +130,7 @@ __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
 // e = (e_zero ? 0 : e) + omega * B z   (pointwise over the M planes)
 template <typename T>
 struct BackParams {
-  long long Ns;
+  GridP g;
   int Nt, M, e_zero;
   T B[MAXM][MAXM];
   T omega;
@@ -105,272 +140,310 @@ struct BackParams {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_backtransform(BackParams<T> p) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p.Ns * p.Nt) return;
-  const long long s = idx % p.Ns;
-  const long long n = idx / p.Ns;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
+  const int n = (int)p.g.fNs.div(idx);
+  const int s = (int)(idx - (unsigned)n * (unsigned)p.g.Ns);
+  const long long Ns = p.g.Ns;
   const int M = p.M;
+  const long long base = (long long)n * M * Ns + s;
   T z[MAXM];
 #pragma unroll
   for (int b = 0; b < MAXM; ++b)
-    if (b < M) z[b] = p.z[(n * M + b) * p.Ns + s];
+    if (b < M) z[b] = p.z[base + (long long)b * Ns];
 #pragma unroll
   for (int a = 0; a < MAXM; ++a) {
     if (a < M) {
       T acc = (T)0;
 #pragma unroll
       for (int b = 0; b < MAXM; ++b)
-        if (b < M) acc += p.B[a][b] * z[b];
-      const long long o = (n * M + a) * p.Ns + s;
+        if (b < M) acc = fma(p.B[a][b], z[b], acc);
+      const long long o = base + (long long)a * Ns;
       p.e[o] = (p.e_zero ? (T)0 : p.e[o]) + p.omega * acc;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Shifted slab operator (I - s (nu Lap + cbar)) on one group, and its
-// diagonal.  For a complex group (zr, zi) with s = sr + i si:
-//   out_r = zr - sr L'zr + si L'zi,  out_i = zi - sr L'zi - si L'zr,
-// L' = nu Lap + cbar.
+// Shifted slab operators (I - s (nu Lap + cbar)) on every group.  For a
+// complex group (zr, zi) with s = sr + i si and L' = nu Lap + cbar:
+//   out_r = zr - sr L'zr + si L'zi,   out_i = zi - sr L'zi - si L'zr.
 // ---------------------------------------------------------------------------
 
-// Jacobi update for all groups at one point of one slab.
-//   zero_init: z = omega D^{-1} y ; else zout = z + omega D^{-1} (y - A z)
-template <int D, typename T, bool ZERO>
-__device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, long long s, int n, int i, int j,
-                                             int k, T dlap) {
+// One Jacobi sweep at point s of slab n: zout = z + omega D^{-1} (y - A z);
+// with fuse_bt the result is not stored but applied as
+// e = (e_zero ? 0 : e) + omega_bt B zout.
+template <int D, typename T>
+__device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int n, const Nbr& nb) {
   const long long Ns = p.g.Ns;
-  const T ihx = (T)p.g.ih2[0], ihy = (T)p.g.ih2[1], ihz = (T)p.g.ih2[2];
   const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
-  const T dprime = p.nu * dlap + cb;  // diagonal of L'
+  const T dprime = p.sc.k2 + cb;  // diagonal of L'
+  const long long base = (long long)n * p.P * Ns + s;
+  T zn[MAXM];
+#pragma unroll
+  for (int pl = 0; pl < MAXM; ++pl) {
+    const int kd = p.sh.kind[pl];
+    if (kd == SH_REAL || kd == SH_RE) {
+      const T sr = p.sh.sr[pl], si = p.sh.si[pl];
+      const T* zpr = p.z + (long long)(n * p.P + pl) * Ns;
+      const T zr = zpr[s];
+      const T Lr = lap_nb<D, T, T>(zpr, s, nb, zr, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zr);
+      const long long o = base + (long long)pl * Ns;
+      if (kd == SH_REAL) {
+        const T dg = (T)1 - sr * dprime;
+        zn[pl] = zr + p.omega * (p.y[o] - (zr - sr * Lr)) / dg;
+      } else if (pl + 1 < MAXM) {
+        const T* zpi = zpr + Ns;
+        const T zi = zpi[s];
+        const T Li = lap_nb<D, T, T>(zpi, s, nb, zi, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zi);
+        const T rr = p.y[o] - (zr - sr * Lr + si * Li);
+        const T ri = p.y[o + Ns] - (zi - sr * Li - si * Lr);
+        const T dr = (T)1 - sr * dprime, di = -si * dprime;
+        const T inv = p.omega / (dr * dr + di * di);
+        zn[pl] = zr + (rr * dr + ri * di) * inv;
+        zn[pl + 1 < MAXM ? pl + 1 : pl] = zi + (ri * dr - rr * di) * inv;
+      }
+    }
+  }
+  if (!p.fuse_bt) {
+#pragma unroll
+    for (int q = 0; q < MAXM; ++q)
+      if (q < p.P) p.zout[base + (long long)q * Ns] = zn[q];
+  } else {
+#pragma unroll
+    for (int a = 0; a < MAXM; ++a) {
+      if (a < p.P) {
+        T acc = (T)0;
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b)
+          if (b < p.P) acc = fma(p.B[a][b], zn[b], acc);
+        const long long o = base + (long long)a * Ns;
+        p.e[o] = (p.e_zero ? (T)0 : p.e[o]) + p.omega_bt * acc;
+      }
+    }
+  }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_inner_jacobi(InnerParams<T> p) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
+  int n, s, i, j, k;
+  split_index(idx, p.g, n, s, i, j, k);
+  jacobi_point<D, T>(p, s, n, make_nbr<D>(i, j, k, p.g));
+}
+
+// Zero-start Jacobi z = omega D^{-1} y (pointwise).
+template <typename T>
+__global__ void __launch_bounds__(256) k_inner_jacobi_zero(InnerParams<T> p) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
+  const int n = (int)p.g.fNs.div(idx);
+  const int s = (int)(idx - (unsigned)n * (unsigned)p.g.Ns);
+  const long long Ns = p.g.Ns;
+  const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
+  const T dprime = p.sc.k2 + cb;
   const long long base = (long long)n * p.P * Ns + s;
 #pragma unroll
-  for (int q = 0; q < MAXM; ++q) {
-    if (q < p.sh.ngroups) {
-      const int pl = p.sh.plane[q];
-      const T sr = p.sh.sr[q], si = p.sh.si[q];
-      if (!p.sh.cplx[q]) {
-        const T dg = (T)1 - sr * dprime;
-        const long long o = base + (long long)pl * Ns;
-        if (ZERO) {
-          p.zout[o] = p.omega * p.y[o] / dg;
-        } else {
-          const T* zp = p.z + (long long)(n * p.P + pl) * Ns;
-          const T zc = zp[s];
-          const T Lz = p.nu * lap_at<D, T, T>(zp, s, i, j, k, p.g, zc, ihx, ihy, ihz) + cb * zc;
-          const T Az = zc - sr * Lz;
-          p.zout[o] = zc + p.omega * (p.y[o] - Az) / dg;
-        }
-      } else {
-        // D = (1 - sr d') - i si d';  1/D = conj(D)/|D|^2
-        const T dr = (T)1 - sr * dprime, di = -si * dprime;
-        const T inv = (T)1 / (dr * dr + di * di);
-        const long long o_r = base + (long long)pl * Ns, o_i = o_r + Ns;
-        T rr, ri;
-        T zr = (T)0, zi = (T)0;
-        if (ZERO) {
-          rr = p.y[o_r];
-          ri = p.y[o_i];
-        } else {
-          const T* zpr = p.z + (long long)(n * p.P + pl) * Ns;
-          const T* zpi = zpr + Ns;
-          zr = zpr[s];
-          zi = zpi[s];
-          const T Lr = p.nu * lap_at<D, T, T>(zpr, s, i, j, k, p.g, zr, ihx, ihy, ihz) + cb * zr;
-          const T Li = p.nu * lap_at<D, T, T>(zpi, s, i, j, k, p.g, zi, ihx, ihy, ihz) + cb * zi;
-          rr = p.y[o_r] - (zr - sr * Lr + si * Li);
-          ri = p.y[o_i] - (zi - sr * Li - si * Lr);
-        }
-        // (rr + i ri) * (dr - i di) * inv
-        const T qr = (rr * dr + ri * di) * inv;
-        const T qi = (ri * dr - rr * di) * inv;
-        p.zout[o_r] = zr + p.omega * qr;
-        p.zout[o_i] = zi + p.omega * qi;
-      }
+  for (int pl = 0; pl < MAXM; ++pl) {
+    const int kd = p.sh.kind[pl];
+    if (kd == SH_REAL || kd == SH_RE) {
+      const long long o = base + (long long)pl * Ns;
+      T zr, zi;
+      zero_jacobi<T>(p.y[o], kd == SH_RE ? p.y[o + Ns] : (T)0, kd == SH_RE, p.sh.sr[pl], p.sh.si[pl], dprime,
+                     p.omega, zr, zi);
+      p.zout[o] = zr;
+      if (kd == SH_RE) p.zout[o + Ns] = zi;
     }
   }
 }
 
-template <int D, typename T, bool ZERO>
-__global__ void __launch_bounds__(256) k_inner_jacobi(InnerParams<T> p) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p.g.Ns * p.Nt) return;
-  const long long s = idx % p.g.Ns;
-  const int n = (int)(idx / p.g.Ns);
-  int i, j, k;
-  decompose(s, p.g, i, j, k);
-  jacobi_point<D, T, ZERO>(p, s, n, i, j, k, (T)lap_diag<D>(p.g));
-}
-
-// Residual of the shifted systems at one fine point, all groups, into res[P].
+// Residual y - A z of the shifted systems at every (slab, point), all planes,
+// into zout.
 template <int D, typename T>
-__device__ __forceinline__ void shifted_residual(const InnerParams<T>& p, long long s, int n, T* res) {
+__global__ void __launch_bounds__(256) k_shifted_residual(InnerParams<T> p) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
+  int n, s, i, j, k;
+  split_index(idx, p.g, n, s, i, j, k);
+  const Nbr nb = make_nbr<D>(i, j, k, p.g);
   const long long Ns = p.g.Ns;
-  int i, j, k;
-  decompose(s, p.g, i, j, k);
-  const T ihx = (T)p.g.ih2[0], ihy = (T)p.g.ih2[1], ihz = (T)p.g.ih2[2];
   const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
 #pragma unroll
-  for (int q = 0; q < MAXM; ++q) {
-    if (q < p.sh.ngroups) {
-      const int pl = p.sh.plane[q];
-      const T sr = p.sh.sr[q], si = p.sh.si[q];
+  for (int pl = 0; pl < MAXM; ++pl) {
+    const int kd = p.sh.kind[pl];
+    if (kd == SH_REAL || kd == SH_RE) {
+      const T sr = p.sh.sr[pl], si = p.sh.si[pl];
       const T* zr_p = p.z + (long long)(n * p.P + pl) * Ns;
       const T zr = zr_p[s];
-      const T Lr = p.nu * lap_at<D, T, T>(zr_p, s, i, j, k, p.g, zr, ihx, ihy, ihz) + cb * zr;
+      const T Lr = lap_nb<D, T, T>(zr_p, s, nb, zr, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zr);
       const long long o = (long long)(n * p.P + pl) * Ns + s;
-      if (!p.sh.cplx[q]) {
-        res[pl] = p.y[o] - (zr - sr * Lr);
-      } else {
+      if (kd == SH_REAL) {
+        p.zout[o] = p.y[o] - (zr - sr * Lr);
+      } else if (pl + 1 < MAXM) {
         const T* zi_p = zr_p + Ns;
         const T zi = zi_p[s];
-        const T Li = p.nu * lap_at<D, T, T>(zi_p, s, i, j, k, p.g, zi, ihx, ihy, ihz) + cb * zi;
-        res[pl] = p.y[o] - (zr - sr * Lr + si * Li);
-        res[pl + 1] = p.y[o + Ns] - (zi - sr * Li - si * Lr);
+        const T Li = lap_nb<D, T, T>(zi_p, s, nb, zi, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zi);
+        p.zout[o] = p.y[o] - (zr - sr * Lr + si * Li);
+        p.zout[o + Ns] = p.y[o + Ns] - (zi - sr * Li - si * Lr);
       }
     }
   }
 }
 
-// Coarse rhs yc = full weighting of (y - A z); coarse start zc = omega Dc^{-1} yc.
+// Coarse rhs yc = full weighting of the fine residual res; coarse start
+// zc = omega Dc^{-1} yc.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_inner_restrict(InnerParams<T> p) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)p.Nt * (unsigned)p.gc.Ns) return;
+  int n, sc, I, J, K;
+  split_index(idx, p.gc, n, sc, I, J, K);
   const long long Nc = p.gc.Ns;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Nc * p.Nt) return;
-  const long long sc = idx % Nc;
-  const int n = (int)(idx / Nc);
-  int I, J, K;
-  decompose(sc, p.gc, I, J, K);
+  const long long Ns = p.g.Ns;
   int ix[3], iy[3], iz[3];
   float wx[3], wy[3], wz[3];
   restr_1d(I, p.g.n0, p.g.bc, ix, wx);
-  int ny = 1, nz = 1;
-  if (D >= 2) { restr_1d(J, p.g.n1, p.g.bc, iy, wy); ny = 3; } else { iy[0] = 0; wy[0] = 1.f; }
-  if (D >= 3) { restr_1d(K, p.g.n2, p.g.bc, iz, wz); nz = 3; } else { iz[0] = 0; wz[0] = 1.f; }
+  if (D >= 2) restr_1d(J, p.g.n1, p.g.bc, iy, wy);
+  if (D >= 3) restr_1d(K, p.g.n2, p.g.bc, iz, wz);
+  constexpr int NY = D >= 2 ? 3 : 1, NZ = D >= 3 ? 3 : 1;
   T acc[MAXM];
 #pragma unroll
   for (int a = 0; a < MAXM; ++a) acc[a] = (T)0;
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b)
+  const T* rb = p.res + (long long)n * p.P * Ns;
+#pragma unroll
+  for (int cc = 0; cc < NZ; ++cc)
+#pragma unroll
+    for (int b = 0; b < NY; ++b)
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const long long s = ((long long)iz[c] * p.g.n1 + iy[b]) * p.g.n0 + ix[a];
-        const T w = (T)(wx[a] * wy[b] * wz[c]);
-        T res[MAXM];
-        shifted_residual<D, T>(p, s, n, res);
+        const int zz = D >= 3 ? iz[cc] : 0, yy = D >= 2 ? iy[b] : 0;
+        const T w = (T)(wx[a] * (D >= 2 ? wy[b] : 1.f) * (D >= 3 ? wz[cc] : 1.f));
+        const long long s = ((long long)zz * p.g.n1 + yy) * p.g.n0 + ix[a];
 #pragma unroll
         for (int q = 0; q < MAXM; ++q)
-          if (q < p.P) acc[q] += w * res[q];
+          if (q < p.P) acc[q] = fma(w, rb[(long long)q * Ns + s], acc[q]);
       }
-  // write yc and the zero-start Jacobi iterate zc
   const T cb = p.cbarc ? p.cbarc[(long long)n * Nc + sc] : (T)0;
-  const T dprime = p.nu * (T)lap_diag<D>(p.gc) + cb;
+  const T dprime = p.k2c + cb;
   const long long base = (long long)n * p.P * Nc + sc;
 #pragma unroll
-  for (int q = 0; q < MAXM; ++q) {
-    if (q < p.sh.ngroups) {
-      const int pl = p.sh.plane[q];
-      const T sr = p.sh.sr[q], si = p.sh.si[q];
+  for (int pl = 0; pl < MAXM; ++pl) {
+    const int kd = p.sh.kind[pl];
+    if (kd == SH_REAL || kd == SH_RE) {
       const long long o = base + (long long)pl * Nc;
-      if (!p.sh.cplx[q]) {
-        p.yc[o] = acc[pl];
-        p.zc[o] = p.omega * acc[pl] / ((T)1 - sr * dprime);
-      } else {
-        const T dr = (T)1 - sr * dprime, di = -si * dprime;
-        const T inv = (T)1 / (dr * dr + di * di);
-        const T rr = acc[pl], ri = acc[pl + 1];
-        p.yc[o] = rr;
-        p.yc[o + Nc] = ri;
-        p.zc[o] = p.omega * (rr * dr + ri * di) * inv;
-        p.zc[o + Nc] = p.omega * (ri * dr - rr * di) * inv;
+      const T ai = (kd == SH_RE) ? acc[pl + 1 < MAXM ? pl + 1 : pl] : (T)0;
+      T zr, zi;
+      zero_jacobi<T>(acc[pl], ai, kd == SH_RE, p.sh.sr[pl], p.sh.si[pl], dprime, p.omega, zr, zi);
+      p.yc[o] = acc[pl];
+      p.zc[o] = zr;
+      if (kd == SH_RE) {
+        p.yc[o + Nc] = ai;
+        p.zc[o + Nc] = zi;
       }
     }
   }
 }
 
 // Coarsest inner grid: one block per slab runs `iters` Jacobi sweeps on all
-// groups in shared memory, starting from z = 0.
+// groups in shared memory, starting from z = 0; with fuse_bt the last sweep
+// applies the back-transform update instead of storing z.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_inner_coarse(InnerParams<T> p) {
   extern __shared__ unsigned char smem_raw[];
-  T* sz = reinterpret_cast<T*>(smem_raw);          // [P][Ns]
-  T* sz2 = sz + (long long)p.P * p.g.Ns;          // [P][Ns]
-  const long long Ns = p.g.Ns;
+  T* sz = reinterpret_cast<T*>(smem_raw);      // [P][Ns]
+  T* sz2 = sz + (long long)p.P * p.g.Ns;      // [P][Ns]
+  const int Ns = (int)p.g.Ns;
   const int n = blockIdx.x;
-  for (long long t = threadIdx.x; t < p.P * Ns; t += blockDim.x) sz[t] = (T)0;
+  for (int t = threadIdx.x; t < p.P * Ns; t += blockDim.x) sz[t] = (T)0;
   __syncthreads();
   InnerParams<T> q = p;
   q.Nt = 1;
+  q.fuse_bt = 0;
   q.cbar = p.cbar ? p.cbar + (long long)n * Ns : nullptr;
   q.y = p.y + (long long)n * p.P * Ns;
-  const T dl = (T)lap_diag<D>(p.g);
   for (int it = 0; it < p.iters; ++it) {
+    const bool last = (it == p.iters - 1);
     q.z = sz;
     q.zout = sz2;
-    for (long long s = threadIdx.x; s < Ns; s += blockDim.x) {
+    if (last && p.fuse_bt) {
+      q.fuse_bt = 1;
+      q.e = p.e + (long long)n * p.P * Ns;
+    }
+    for (int s = threadIdx.x; s < Ns; s += blockDim.x) {
       int i, j, k;
-      decompose(s, p.g, i, j, k);
-      jacobi_point<D, T, false>(q, s, 0, i, j, k, dl);
+      point_ijk(s, p.g, i, j, k);
+      jacobi_point<D, T>(q, s, 0, make_nbr<D>(i, j, k, p.g));
     }
     __syncthreads();
     T* tmp = sz;
     sz = sz2;
     sz2 = tmp;
   }
-  for (long long t = threadIdx.x; t < p.P * Ns; t += blockDim.x) p.zout[(long long)n * p.P * Ns + t] = sz[t];
+  if (!p.fuse_bt)
+    for (int t = threadIdx.x; t < p.P * Ns; t += blockDim.x) p.zout[(long long)n * p.P * Ns + t] = sz[t];
 }
 
 // ---------------------------------------------------------------------------
 // Spatial transfers of [planes][Ns] fields.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_restrict_space(GridP gf, GridP gc, long long planes,
+__global__ void __launch_bounds__(256) k_restrict_space(GridP gf, GridP gc, int planes,
                                                         const T* __restrict__ fine, T* __restrict__ coarse) {
-  const long long Nc = gc.Ns;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Nc * planes) return;
-  const long long sc = idx % Nc;
-  const long long pl = idx / Nc;
-  int I, J, K;
-  decompose(sc, gc, I, J, K);
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)planes * (unsigned)gc.Ns) return;
+  int pl, sc, I, J, K;
+  split_index(idx, gc, pl, sc, I, J, K);
   int ix[3], iy[3], iz[3];
   float wx[3], wy[3], wz[3];
   restr_1d(I, gf.n0, gf.bc, ix, wx);
-  int ny = 1, nz = 1;
-  if (D >= 2) { restr_1d(J, gf.n1, gf.bc, iy, wy); ny = 3; } else { iy[0] = 0; wy[0] = 1.f; }
-  if (D >= 3) { restr_1d(K, gf.n2, gf.bc, iz, wz); nz = 3; } else { iz[0] = 0; wz[0] = 1.f; }
-  const T* f = fine + pl * gf.Ns;
+  if (D >= 2) restr_1d(J, gf.n1, gf.bc, iy, wy);
+  if (D >= 3) restr_1d(K, gf.n2, gf.bc, iz, wz);
+  constexpr int NY = D >= 2 ? 3 : 1, NZ = D >= 3 ? 3 : 1;
+  const T* f = fine + (long long)pl * gf.Ns;
   T acc = (T)0;
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b)
-      for (int a = 0; a < 3; ++a)
-        acc += (T)(wx[a] * wy[b] * wz[c]) * f[((long long)iz[c] * gf.n1 + iy[b]) * gf.n0 + ix[a]];
-  coarse[idx] = acc;
+#pragma unroll
+  for (int c = 0; c < NZ; ++c)
+#pragma unroll
+    for (int b = 0; b < NY; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int zz = D >= 3 ? iz[c] : 0, yy = D >= 2 ? iy[b] : 0;
+        const float w3 = wx[a] * (D >= 2 ? wy[b] : 1.f) * (D >= 3 ? wz[c] : 1.f);
+        acc = fma((T)w3, f[(zz * gf.n1 + yy) * gf.n0 + ix[a]], acc);
+      }
+  coarse[(long long)pl * gc.Ns + sc] = acc;
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_prolong_space_add(GridP gf, GridP gc, long long planes,
+__global__ void __launch_bounds__(256) k_prolong_space_add(GridP gf, GridP gc, int planes,
                                                            const T* __restrict__ coarse, T* __restrict__ fine) {
-  const long long Nf = gf.Ns;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Nf * planes) return;
-  const long long s = idx % Nf;
-  const long long pl = idx / Nf;
-  int i, j, k;
-  decompose(s, gf, i, j, k);
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)planes * (unsigned)gf.Ns) return;
+  int pl, s, i, j, k;
+  split_index(idx, gf, pl, s, i, j, k);
   int ix[2], iy[2], iz[2];
   float wx[2], wy[2], wz[2];
   const int cx = prol_1d(i, gc.n0, gf.bc, ix, wx);
   int cy = 1, cz = 1;
-  if (D >= 2) cy = prol_1d(j, gc.n1, gf.bc, iy, wy); else { iy[0] = 0; wy[0] = 1.f; }
-  if (D >= 3) cz = prol_1d(k, gc.n2, gf.bc, iz, wz); else { iz[0] = 0; wz[0] = 1.f; }
-  const T* c = coarse + pl * gc.Ns;
+  if (D >= 2) cy = prol_1d(j, gc.n1, gf.bc, iy, wy);
+  if (D >= 3) cz = prol_1d(k, gc.n2, gf.bc, iz, wz);
+  constexpr int NY = D >= 2 ? 2 : 1, NZ = D >= 3 ? 2 : 1;
+  const T* c = coarse + (long long)pl * gc.Ns;
   T acc = (T)0;
-  for (int cc = 0; cc < cz; ++cc)
-    for (int b = 0; b < cy; ++b)
-      for (int a = 0; a < cx; ++a)
-        acc += (T)(wx[a] * wy[b] * wz[cc]) * c[((long long)iz[cc] * gc.n1 + iy[b]) * gc.n0 + ix[a]];
-  fine[idx] += acc;
+#pragma unroll
+  for (int cc = 0; cc < NZ; ++cc)
+#pragma unroll
+    for (int b = 0; b < NY; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        if (a < cx && (D < 2 || b < cy) && (D < 3 || cc < cz)) {
+          const int zz = D >= 3 ? iz[cc] : 0, yy = D >= 2 ? iy[b] : 0;
+          const float w3 = wx[a] * (D >= 2 ? wy[b] : 1.f) * (D >= 3 ? wz[cc] : 1.f);
+          acc = fma((T)w3, c[(zz * gc.n1 + yy) * gc.n0 + ix[a]], acc);
+        }
+      }
+  fine[(long long)pl * gf.Ns + s] += acc;
 }
 
 // Slab bisection: coarse[N][m] = sum_k R[m][k] fine[2N + k/M][k%M]
@@ -381,46 +454,48 @@ struct TimeXfer {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_time(long long Ns, int Ntc, int M, TimeXfer<T> X,
+__global__ void __launch_bounds__(256) k_restrict_time(GridP g, int Ntc, int M, TimeXfer<T> X,
                                                        const T* __restrict__ fine, T* __restrict__ coarse) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Ns * Ntc) return;
-  const long long s = idx % Ns;
-  const long long N = idx / Ns;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
+  const int N = (int)g.fNs.div(idx);
+  const long long s = idx - (unsigned)N * (unsigned)g.Ns;
+  const long long Ns = g.Ns;
   T f[2 * MAXM];
-  for (int kk = 0; kk < 2 * M; ++kk) f[kk] = fine[((2 * N + kk / M) * M + (kk % M)) * Ns + s];
+  for (int kk = 0; kk < 2 * M; ++kk) f[kk] = fine[((long long)(2 * N + kk / M) * M + (kk % M)) * Ns + s];
   for (int m = 0; m < M; ++m) {
     T acc = (T)0;
-    for (int kk = 0; kk < 2 * M; ++kk) acc += X.A[m][kk] * f[kk];
-    coarse[(N * M + m) * Ns + s] = acc;
+    for (int kk = 0; kk < 2 * M; ++kk) acc = fma(X.A[m][kk], f[kk], acc);
+    coarse[((long long)N * M + m) * Ns + s] = acc;
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong_time_add(long long Ns, int Ntc, int M, TimeXfer<T> X,
+__global__ void __launch_bounds__(256) k_prolong_time_add(GridP g, int Ntc, int M, TimeXfer<T> X,
                                                           const T* __restrict__ coarse, T* __restrict__ fine) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Ns * Ntc) return;
-  const long long s = idx % Ns;
-  const long long N = idx / Ns;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
+  const int N = (int)g.fNs.div(idx);
+  const long long s = idx - (unsigned)N * (unsigned)g.Ns;
+  const long long Ns = g.Ns;
   T cv[MAXM];
-  for (int m = 0; m < M; ++m) cv[m] = coarse[(N * M + m) * Ns + s];
+  for (int m = 0; m < M; ++m) cv[m] = coarse[((long long)N * M + m) * Ns + s];
   for (int kk = 0; kk < 2 * M; ++kk) {
     T acc = (T)0;
-    for (int m = 0; m < M; ++m) acc += X.B[kk][m] * cv[m];
-    fine[((2 * N + kk / M) * M + (kk % M)) * Ns + s] += acc;
+    for (int m = 0; m < M; ++m) acc = fma(X.B[kk][m], cv[m], acc);
+    fine[((long long)(2 * N + kk / M) * M + (kk % M)) * Ns + s] += acc;
   }
 }
 
 // cbar of two fine slabs averaged onto the coarse slab.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cbar_time(long long Ns, int Ntc, const T* __restrict__ fine,
+__global__ void __launch_bounds__(256) k_cbar_time(GridP g, int Ntc, const T* __restrict__ fine,
                                                    T* __restrict__ coarse) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Ns * Ntc) return;
-  const long long s = idx % Ns;
-  const long long N = idx / Ns;
-  coarse[idx] = (T)0.5 * (fine[(2 * N) * Ns + s] + fine[(2 * N + 1) * Ns + s]);
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
+  const int N = (int)g.fNs.div(idx);
+  const long long s = idx - (unsigned)N * (unsigned)g.Ns;
+  coarse[idx] = (T)0.5 * (fine[(2LL * N) * g.Ns + s] + fine[(2LL * N + 1) * g.Ns + s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -435,32 +510,37 @@ __global__ void __launch_bounds__(256) k_cbar_time(long long Ns, int Ntc, const 
 
 template <typename T>
 void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st) {
-  const long long nchunks = (p.Nt + p.chunk - 1) / p.chunk;
-  const unsigned nb = nblk(p.g.Ns * nchunks, 256);
+  const unsigned nb = nblk((long long)p.g.Ns * p.nchunks, 256);
   DISPATCH_D(D, (k_lin_residual<DD, T><<<nb, 256, 0, st>>>(p)));
 }
 
 template <typename T>
-void launch_backtransform(long long Ns, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero,
-                          const T* z, T* e, cudaStream_t st) {
+void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero, const T* z,
+                          T* e, cudaStream_t st) {
   BackParams<T> p;
-  p.Ns = Ns; p.Nt = Nt; p.M = M; p.e_zero = e_zero; p.omega = omega; p.z = z; p.e = e;
+  p.g = g; p.Nt = Nt; p.M = M; p.e_zero = e_zero; p.omega = omega; p.z = z; p.e = e;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) p.B[a][b] = B[a][b];
-  k_backtransform<T><<<nblk(Ns * Nt, 256), 256, 0, st>>>(p);
+  k_backtransform<T><<<nblk(g.Ns * Nt, 256), 256, 0, st>>>(p);
 }
 
 template <typename T>
 void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st) {
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
-  if (zero) DISPATCH_D(D, (k_inner_jacobi<DD, T, true><<<nb, 256, 0, st>>>(p)));
-  else DISPATCH_D(D, (k_inner_jacobi<DD, T, false><<<nb, 256, 0, st>>>(p)));
+  if (zero) k_inner_jacobi_zero<T><<<nb, 256, 0, st>>>(p);
+  else DISPATCH_D(D, (k_inner_jacobi<DD, T><<<nb, 256, 0, st>>>(p)));
 }
 
 template <typename T>
 void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st) {
   const unsigned nb = nblk(p.gc.Ns * p.Nt, 256);
   DISPATCH_D(D, (k_inner_restrict<DD, T><<<nb, 256, 0, st>>>(p)));
+}
+
+template <typename T>
+void launch_shifted_residual(int D, const InnerParams<T>& p, cudaStream_t st) {
+  const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
+  DISPATCH_D(D, (k_shifted_residual<DD, T><<<nb, 256, 0, st>>>(p)));
 }
 
 template <typename T>
@@ -480,56 +560,57 @@ template <typename T>
 void launch_restrict_space(int D, const GridP& gf, const GridP& gc, long long planes, const T* f, T* c,
                            cudaStream_t st) {
   const unsigned nb = nblk(gc.Ns * planes, 256);
-  DISPATCH_D(D, (k_restrict_space<DD, T><<<nb, 256, 0, st>>>(gf, gc, planes, f, c)));
+  DISPATCH_D(D, (k_restrict_space<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, f, c)));
 }
 
 template <typename T>
 void launch_prolong_space_add(int D, const GridP& gf, const GridP& gc, long long planes, const T* c, T* f,
                               cudaStream_t st) {
   const unsigned nb = nblk(gf.Ns * planes, 256);
-  DISPATCH_D(D, (k_prolong_space_add<DD, T><<<nb, 256, 0, st>>>(gf, gc, planes, c, f)));
+  DISPATCH_D(D, (k_prolong_space_add<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, c, f)));
 }
 
 template <typename T>
-void launch_restrict_time(long long Ns, int Ntc, int M, const double R[MAXM][2 * MAXM], const T* f, T* c,
+void launch_restrict_time(const GridP& g, int Ntc, int M, const double R[MAXM][2 * MAXM], const T* f, T* c,
                           cudaStream_t st) {
   TimeXfer<T> X;
   for (int m = 0; m < MAXM; ++m)
     for (int kk = 0; kk < 2 * MAXM; ++kk) X.A[m][kk] = (T)R[m][kk];
-  k_restrict_time<T><<<nblk(Ns * Ntc, 256), 256, 0, st>>>(Ns, Ntc, M, X, f, c);
+  k_restrict_time<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, M, X, f, c);
 }
 
 template <typename T>
-void launch_prolong_time_add(long long Ns, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
+void launch_prolong_time_add(const GridP& g, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
                              cudaStream_t st) {
   TimeXfer<T> X;
   for (int kk = 0; kk < 2 * MAXM; ++kk)
     for (int m = 0; m < MAXM; ++m) X.B[kk][m] = (T)P[kk][m];
-  k_prolong_time_add<T><<<nblk(Ns * Ntc, 256), 256, 0, st>>>(Ns, Ntc, M, X, c, f);
+  k_prolong_time_add<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, M, X, c, f);
 }
 
 template <typename T>
-void launch_cbar_time(long long Ns, int Ntc, const T* f, T* c, cudaStream_t st) {
-  k_cbar_time<T><<<nblk(Ns * Ntc, 256), 256, 0, st>>>(Ns, Ntc, f, c);
+void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st) {
+  k_cbar_time<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, f, c);
 }
 
 #define INST(T)                                                                                     \
   template void launch_lin_residual<T>(int, const LinParams<T>&, cudaStream_t);                    \
-  template void launch_backtransform<T>(long long, int, int, const T[MAXM][MAXM], T, int, const T*, \
+  template void launch_backtransform<T>(const GridP&, int, int, const T[MAXM][MAXM], T, int, const T*, \
                                         T*, cudaStream_t);                                         \
   template void launch_inner_jacobi<T>(int, int, const InnerParams<T>&, cudaStream_t);             \
   template void launch_inner_restrict<T>(int, const InnerParams<T>&, cudaStream_t);                \
+  template void launch_shifted_residual<T>(int, const InnerParams<T>&, cudaStream_t);              \
   template size_t inner_coarse_smem<T>(const InnerParams<T>&);                                     \
   template void launch_inner_coarse<T>(int, const InnerParams<T>&, cudaStream_t);                  \
   template void launch_restrict_space<T>(int, const GridP&, const GridP&, long long, const T*, T*, \
                                          cudaStream_t);                                            \
   template void launch_prolong_space_add<T>(int, const GridP&, const GridP&, long long, const T*,  \
                                             T*, cudaStream_t);                                     \
-  template void launch_restrict_time<T>(long long, int, int, const double[MAXM][2 * MAXM], const T*, \
-                                        T*, cudaStream_t);                                         \
-  template void launch_prolong_time_add<T>(long long, int, int, const double[2 * MAXM][MAXM],      \
+  template void launch_restrict_time<T>(const GridP&, int, int, const double[MAXM][2 * MAXM],      \
+                                        const T*, T*, cudaStream_t);                               \
+  template void launch_prolong_time_add<T>(const GridP&, int, int, const double[2 * MAXM][MAXM],   \
                                            const T*, T*, cudaStream_t);                            \
-  template void launch_cbar_time<T>(long long, int, const T*, T*, cudaStream_t);
+  template void launch_cbar_time<T>(const GridP&, int, const T*, T*, cudaStream_t);
 
 INST(float)
 INST(double)

@@ -50,6 +50,7 @@ struct Level {
   int Nt = 0;
   double dt = 0, mu = 0, omega = 1;
   int next = 0;  // 0 coarsest, 1 space, 2 slabs
+  int bottom_sweeps = 2;
   void* e = nullptr;
   void* r = nullptr;
   void* cbar = nullptr;
@@ -83,7 +84,20 @@ GridP make_grid(int d, const int n[3], int bc, double X) {
       g.ih2[a] = 0.0;
     }
   }
+  g.f0 = FastDiv((unsigned)g.n0);
+  g.f1 = FastDiv((unsigned)g.n1);
+  g.fNs = FastDiv((unsigned)std::min<long long>(g.Ns, 0x7fffffffLL));
   return g;
+}
+
+template <typename T>
+StencilC<T> stencil_of(const GridP& g, double nu) {
+  StencilC<T> c;
+  c.cx = (T)(nu * g.ih2[0]);
+  c.cy = (T)(nu * g.ih2[1]);
+  c.cz = (T)(nu * g.ih2[2]);
+  c.k2 = (T)(-2.0 * nu * (g.ih2[0] + g.ih2[1] + g.ih2[2]));
+  return c;
 }
 
 bool can_coarsen_axis(int bc, int n) {
@@ -121,7 +135,28 @@ struct PlanLevel {
   double dt, mu, omega;
   int next;
   std::vector<GridP> inner;
+  int bottom_sweeps;  // Jacobi sweeps on the bottom inner grid when it does not fit one block
 };
+
+// Largest |shift| per unit dt of the slab systems: max |lambda(Q)| and the
+// SDC diagonal entries.
+double max_shift(int M) {
+  Colloc c;
+  if (colloc_setup(M, &c) != 0) return 1.0;
+  double m = 0;
+  for (int q = 0; q < M; ++q) {
+    m = std::max(m, std::abs(c.lam[q]));
+    m = std::max(m, std::max(c.QI_ie[q][q], c.QI_lu[q][q]));
+  }
+  return m;
+}
+
+// Diffusion number of the shifted slab operator on grid g: |s| nu 2 sum 1/h^2.
+double stiffness(const GridP& g, double nu, double dt, double lam) {
+  return lam * dt * nu * 2.0 * (g.ih2[0] + g.ih2[1] + g.ih2[2]);
+}
+
+const double kSigmaStop = 0.25;  // below this Jacobi alone solves the slab systems
 
 double default_omega(const st_solver_opts& o, double mu) {
   if (o.omega > 0) return o.omega;
@@ -141,6 +176,12 @@ int validate(const st_problem* p, const st_solver_opts* o) {
   if (p->reaction < 0 || p->reaction > 2) return ST_ERR_INVALID_ARG;
   if (!(p->X > 0) || !(p->T > 0) || !(p->nu > 0) || !std::isfinite(p->rho)) return ST_ERR_INVALID_ARG;
   if (p->Nt < 1 || p->M < 1 || p->M > ST_MAX_M) return ST_ERR_INVALID_ARG;
+  {
+    long long ns = 1;
+    for (int a = 0; a < p->d; ++a) ns *= p->n[a];
+    // kernels index (slab, point) pairs with 32-bit integers
+    if (ns * (long long)p->Nt >= 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
+  }
   if (o) {
     if (o->precision != ST_PREC_FP64 && o->precision != ST_PREC_FP32_REFINE) return ST_ERR_INVALID_ARG;
     if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU) return ST_ERR_INVALID_ARG;
@@ -193,14 +234,20 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     out.push_back(nx);
   }
   out.back().next = 0;
+  const double lmax = max_shift(p->M);
+  const double wj = d == 1 ? 2.0 / 3.0 : (d == 2 ? 0.8 : 6.0 / 7.0);
   for (auto& L : out) {
     L.mu = p->nu * L.dt * L.g.ih2[0];
     L.omega = default_omega(o, L.mu);
     L.inner.clear();
     L.inner.push_back(L.g);
-    while (L.inner.back().Ns > kInnerCoarseMax && can_coarsen(d, L.inner.back()))
+    while (L.inner.back().Ns > kInnerCoarseMax && can_coarsen(d, L.inner.back()) &&
+           stiffness(L.inner.back(), p->nu, L.dt, lmax) > kSigmaStop)
       L.inner.push_back(coarsen(d, L.inner.back(), p->X));
-    if (L.inner.back().Ns > kInnerCoarseLimit) return ST_ERR_UNSUPPORTED;
+    // sweeps for a 0.05 reduction of the smoothest mode, factor 1 - wj/(1+sigma)
+    const double sig = stiffness(L.inner.back(), p->nu, L.dt, lmax);
+    const double rho = std::max(1e-3, 1.0 - wj / (1.0 + sig));
+    L.bottom_sweeps = std::max(2, std::min(o.inner_coarse_iters, (int)std::ceil(std::log(0.05) / std::log(rho))));
   }
   if (out.back().g.Ns * p->M > kCoarseKMax) return ST_ERR_UNSUPPORTED;
   return ST_OK;
@@ -349,13 +396,29 @@ void build_transforms(st_handle* h) {
 template <typename T>
 Shifts<T> level_shifts(const st_handle* h, double dt) {
   Shifts<T> s;
-  s.ngroups = h->ngroups;
-  for (int q = 0; q < MAXM; ++q) {
-    s.plane[q] = q < h->ngroups ? h->gplane[q] : 0;
-    s.cplx[q] = q < h->ngroups ? h->gcplx[q] : 0;
-    s.sr[q] = q < h->ngroups ? (T)(dt * h->glam[q].real()) : (T)0;
-    s.si[q] = q < h->ngroups ? (T)(dt * h->glam[q].imag()) : (T)0;
+  for (int p = 0; p < MAXM; ++p) {
+    s.kind[p] = SH_NONE;
+    s.sr[p] = s.si[p] = (T)0;
   }
+  for (int q = 0; q < h->ngroups; ++q) {
+    const int p = h->gplane[q];
+    s.kind[p] = h->gcplx[q] ? SH_RE : SH_REAL;
+    if (h->gcplx[q]) s.kind[p + 1] = SH_IM;
+    s.sr[p] = (T)(dt * h->glam[q].real());
+    s.si[p] = (T)(dt * h->glam[q].imag());
+  }
+  return s;
+}
+
+template <typename T>
+Shifts<T> real_shift(T s0) {
+  Shifts<T> s;
+  for (int p = 0; p < MAXM; ++p) {
+    s.kind[p] = SH_NONE;
+    s.sr[p] = s.si[p] = (T)0;
+  }
+  s.kind[0] = SH_REAL;
+  s.sr[0] = s0;
   return s;
 }
 
@@ -373,29 +436,77 @@ InnerParams<T> inner_params(st_handle* h, Level& Lv, int k, int P, const Shifts<
   ip.Nt = Lv.Nt;
   ip.P = P;
   ip.sh = sh;
-  ip.nu = (T)h->p.nu;
+  ip.sc = stencil_of<T>(I.g, h->p.nu);
+  ip.k2c = stencil_of<T>(ip.gc, h->p.nu).k2;
   ip.omega = (T)jacobi_weight(h->D);
+  ip.fuse_bt = 0;
+  ip.e_zero = 0;
+  ip.omega_bt = (T)0;
+  ip.e = nullptr;
+  for (int a2 = 0; a2 < MAXM; ++a2)
+    for (int b = 0; b < MAXM; ++b) ip.B[a2][b] = (T)0;
   ip.cbar = use_cbar ? (const T*)I.cbar : nullptr;
   ip.cbarc = (use_cbar && k + 1 < (int)Lv.in.size()) ? (const T*)Lv.in[k + 1].cbar : nullptr;
   ip.y = (const T*)I.y;
   ip.z = (const T*)I.z;
   ip.zout = (T*)I.t;
+  ip.res = (const T*)I.t;
   ip.yc = (k + 1 < (int)Lv.in.size()) ? (T*)Lv.in[k + 1].y : nullptr;
   ip.zc = (k + 1 < (int)Lv.in.size()) ? (T*)Lv.in[k + 1].z : nullptr;
   ip.iters = h->o.inner_coarse_iters;
   return ip;
 }
 
+// Fused epilogue of the last sweep at inner level 0: e = (e_zero ? 0 : e) + omega B z.
+template <typename T>
+struct BtFuse {
+  bool on = false;
+  int e_zero = 0;
+  T omega = 0;
+  T B[MAXM][MAXM];
+  T* e = nullptr;
+};
+
+template <typename T>
+void apply_fuse(InnerParams<T>& ip, const BtFuse<T>& f) {
+  ip.fuse_bt = 1;
+  ip.e_zero = f.e_zero;
+  ip.omega_bt = f.omega;
+  ip.e = f.e;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) ip.B[a][b] = f.B[a][b];
+}
+
 template <typename T>
 int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, bool use_cbar, bool presmoothed,
-                 cudaStream_t st) {
+                 const BtFuse<T>* fuse, cudaStream_t st) {
   InnerLev& I = Lv.in[k];
   const int last = (int)Lv.in.size() - 1;
   if (k == last) {
-    InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
-    ip.zout = (T*)I.z;
-    launch_inner_coarse<T>(h->D, ip, st);
-    CKL();
+    if (I.g.Ns <= kInnerCoarseLimit) {
+      // one block per slab, all sweeps in shared memory
+      InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+      ip.zout = (T*)I.z;
+      if (fuse) apply_fuse(ip, *fuse);
+      launch_inner_coarse<T>(h->D, ip, st);
+      CKL();
+      return ST_OK;
+    }
+    // non-stiff bottom grid: Jacobi sweeps continuing from z (which holds
+    // the zero-start iterate when `presmoothed`)
+    const int todo = presmoothed ? Lv.bottom_sweeps - 1 : Lv.bottom_sweeps;
+    for (int it = 0; it < todo; ++it) {
+      InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+      if (fuse && it == todo - 1) {
+        apply_fuse(ip, *fuse);
+        launch_inner_jacobi<T>(h->D, 0, ip, st);
+        CKL();
+      } else {
+        launch_inner_jacobi<T>(h->D, 0, ip, st);
+        CKL();
+        std::swap(I.z, I.t);
+      }
+    }
     return ST_OK;
   }
   const int ns = h->o.inner_smooth;
@@ -407,36 +518,54 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, boo
     std::swap(I.z, I.t);
   }
   {
+    // residual of the shifted systems into t, then full weighting to the
+    // coarser grid (with the coarse zero-start Jacobi iterate)
     InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+    launch_shifted_residual<T>(h->D, ip, st);
+    CKL();
     launch_inner_restrict<T>(h->D, ip, st);
     CKL();
   }
-  TRY(inner_vcycle<T>(h, Lv, k + 1, P, sh, use_cbar, true, st));
+  TRY(inner_vcycle<T>(h, Lv, k + 1, P, sh, use_cbar, true, nullptr, st));
   launch_prolong_space_add<T>(h->D, I.g, Lv.in[k + 1].g, (long long)Lv.Nt * P, (const T*)Lv.in[k + 1].z,
                               (T*)I.z, st);
   CKL();
   for (int it = 0; it < ns; ++it) {
     InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
-    launch_inner_jacobi<T>(h->D, 0, ip, st);
-    CKL();
-    std::swap(I.z, I.t);
+    if (fuse && it == ns - 1) {
+      apply_fuse(ip, *fuse);
+      launch_inner_jacobi<T>(h->D, 0, ip, st);
+      CKL();
+    } else {
+      launch_inner_jacobi<T>(h->D, 0, ip, st);
+      CKL();
+      std::swap(I.z, I.t);
+    }
   }
   return ST_OK;
 }
 
-// Solve the shifted systems with rhs in[0].y into in[0].z (zero start).
+// Solve the shifted systems with rhs in[0].y into in[0].z (zero start; when
+// `zero_done`, in[0].z already holds the zero-start Jacobi iterate).  With
+// `fuse` the last sweep applies the back-transform update instead.
 template <typename T>
-int inner_solve(st_handle* h, Level& Lv, int P, const Shifts<T>& sh, bool use_cbar, int cycles, cudaStream_t st) {
+int inner_solve(st_handle* h, Level& Lv, int P, const Shifts<T>& sh, bool use_cbar, int cycles, bool zero_done,
+                const BtFuse<T>* fuse, cudaStream_t st) {
+  const bool smem_bottom_only = Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit;
+  if (smem_bottom_only) cycles = 1;  // the shared-memory solve restarts from zero
   for (int c = 0; c < cycles; ++c) {
-    if (c == 0 && Lv.in.size() > 1) {
-      InnerParams<T> ip = inner_params<T>(h, Lv, 0, P, sh, use_cbar);
-      ip.zout = (T*)Lv.in[0].z;
-      launch_inner_jacobi<T>(h->D, 1, ip, st);  // zero start
-      CKL();
-      TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, true, st));
-    } else {
-      TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, false, st));
+    const BtFuse<T>* f = (c == cycles - 1) ? fuse : nullptr;
+    bool pre = false;
+    if (c == 0 && !smem_bottom_only) {
+      if (!zero_done) {
+        InnerParams<T> ip = inner_params<T>(h, Lv, 0, P, sh, use_cbar);
+        ip.zout = (T*)Lv.in[0].z;
+        launch_inner_jacobi<T>(h->D, 1, ip, st);  // zero start
+        CKL();
+      }
+      pre = true;
     }
+    TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, pre, f, st));
   }
   return ST_OK;
 }
@@ -458,7 +587,11 @@ LinParams<T> lin_params(st_handle* h, const Level& Lv, int adj) {
       lp.W[a][b] = (T)(Lv.dt * q);
       lp.F[a][b] = (T)(adj ? h->Fa[a][b] : h->Ff[a][b]);
     }
-  lp.nu = (T)h->p.nu;
+  lp.sc = stencil_of<T>(Lv.g, h->p.nu);
+  lp.nchunks = (Lv.Nt + lp.chunk - 1) / lp.chunk;
+  lp.zout = nullptr;
+  lp.sh = level_shifts<T>(h, Lv.dt);
+  lp.omega_j = (T)jacobi_weight(h->D);
   lp.e = nullptr;
   lp.r = nullptr;
   lp.cbar = (h->p.reaction != ST_REACTION_NONE) ? (const T*)Lv.cbar : nullptr;
@@ -485,14 +618,27 @@ template <typename T>
 int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   Level& Lv = h->L[l];
   const int M = h->p.M;
-  TRY(level_residual<T>(h, l, adj, e_zero ? nullptr : Lv.e, Lv.r, Lv.in[0].y, 1, st));
+  const bool multi = !(Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit);
+  {
+    // residual + Q-eigenbasis transform (+ zero-start Jacobi of the slab systems)
+    LinParams<T> lp = lin_params<T>(h, Lv, adj);
+    lp.e = e_zero ? nullptr : (const T*)Lv.e;
+    lp.r = (const T*)Lv.r;
+    lp.out = (T*)Lv.in[0].y;
+    lp.transform = 1;
+    lp.zout = multi ? (T*)Lv.in[0].z : nullptr;
+    launch_lin_residual<T>(h->D, lp, st);
+    CKL();
+  }
   const bool use_cbar = h->p.reaction != ST_REACTION_NONE;
-  TRY(inner_solve<T>(h, Lv, M, level_shifts<T>(h, Lv.dt), use_cbar, h->o.inner_cycles, st));
-  T B[MAXM][MAXM];
+  BtFuse<T> f;
+  f.on = true;
+  f.e_zero = e_zero ? 1 : 0;
+  f.omega = (T)Lv.omega;
+  f.e = (T*)Lv.e;
   for (int a = 0; a < MAXM; ++a)
-    for (int b = 0; b < MAXM; ++b) B[a][b] = (T)(adj ? h->Ba[a][b] : h->Bf[a][b]);
-  launch_backtransform<T>(Lv.g.Ns, Lv.Nt, M, B, (T)Lv.omega, e_zero ? 1 : 0, (const T*)Lv.in[0].z, (T*)Lv.e, st);
-  CKL();
+    for (int b = 0; b < MAXM; ++b) f.B[a][b] = (T)(adj ? h->Ba[a][b] : h->Bf[a][b]);
+  TRY(inner_solve<T>(h, Lv, M, level_shifts<T>(h, Lv.dt), use_cbar, h->o.inner_cycles, multi, &f, st));
   return ST_OK;
 }
 
@@ -504,7 +650,7 @@ int restrict_level(st_handle* h, int l, int adj, const void* fine, void* coarse,
   if (Lv.next == 1) {
     launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)coarse, st);
   } else {
-    launch_restrict_time<T>(Lv.g.Ns, Lc.Nt, M, adj ? h->RtT : h->col.Rt, (const T*)fine, (T*)coarse, st);
+    launch_restrict_time<T>(Lv.g, Lc.Nt, M, adj ? h->RtT : h->col.Rt, (const T*)fine, (T*)coarse, st);
   }
   CKL();
   return ST_OK;
@@ -518,7 +664,7 @@ int prolong_level(st_handle* h, int l, int adj, const void* coarse, void* fine, 
   if (Lv.next == 1) {
     launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)coarse, (T*)fine, st);
   } else {
-    launch_prolong_time_add<T>(Lv.g.Ns, Lc.Nt, M, adj ? h->PtT : h->col.Pt, (const T*)coarse, (T*)fine, st);
+    launch_prolong_time_add<T>(Lv.g, Lc.Nt, M, adj ? h->PtT : h->col.Pt, (const T*)coarse, (T*)fine, st);
   }
   CKL();
   return ST_OK;
@@ -589,7 +735,7 @@ int enqueue_linearize(st_handle* h, cudaStream_t st) {
         if (Lv.next == 1)
           launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
         else
-          launch_cbar_time<T>(Lv.g.Ns, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+          launch_cbar_time<T>(Lv.g, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
         CKL();
       }
     }
@@ -674,6 +820,8 @@ ResidParams fine_params(st_handle* h, const double* U, int adj) {
     for (int b = 0; b < MAXM; ++b)
       rp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? L0.dt * (adj ? h->col.Q[b][a] : h->col.Q[a][b]) : 0.0;
   rp.nu = h->p.nu;
+  rp.sc = stencil_of<double>(L0.g, h->p.nu);
+  rp.nchunks = (rp.Nt + rp.chunk - 1) / rp.chunk;
   rp.rho = h->p.rho;
   rp.reaction = h->p.reaction;
   rp.U = U;
@@ -902,6 +1050,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     Lv.mu = pl[l].mu;
     Lv.omega = pl[l].omega;
     Lv.next = pl[l].next;
+    Lv.bottom_sweeps = pl[l].bottom_sweeps;
     const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
     int s = ST_OK;
     s |= alloc_into(h, &Lv.e, D * h->esz);
@@ -1137,13 +1286,11 @@ int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
                      L0.in[0].y, h->stream);
       CKL();
       if (h->fp64) {
-        Shifts<double> sh;
-        sh.ngroups = 1; sh.plane[0] = 0; sh.cplx[0] = 0; sh.sr[0] = L0.dt * QI[m][m]; sh.si[0] = 0;
-        TRY(inner_solve<double>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, h->stream));
+        Shifts<double> sh = real_shift<double>(L0.dt * QI[m][m]);
+        TRY(inner_solve<double>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, false, nullptr, h->stream));
       } else {
-        Shifts<float> sh;
-        sh.ngroups = 1; sh.plane[0] = 0; sh.cplx[0] = 0; sh.sr[0] = (float)(L0.dt * QI[m][m]); sh.si[0] = 0;
-        TRY(inner_solve<float>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, h->stream));
+        Shifts<float> sh = real_shift<float>((float)(L0.dt * QI[m][m]));
+        TRY(inner_solve<float>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, false, nullptr, h->stream));
       }
       launch_scatter_plane(h->fp64, L0.in[0].z, L0.e, L0.g.Ns, L0.Nt, M, m, h->stream);
       CKL();
@@ -1366,7 +1513,8 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
-  if (!h || iters < 1 || which < 0 || which > 4) return ST_ERR_INVALID_ARG;
+  if (!h || iters < 1 || which < 0 || which > 7) return ST_ERR_INVALID_ARG;
+  if (which >= ST_KERNEL_SHIFTED_RESIDUAL && h->L[0].in.size() < 2) return ST_ERR_UNSUPPORTED;
   if (which == ST_KERNEL_FINE_RESIDUAL && (!U || !is_device_ptr(U))) return ST_ERR_INVALID_ARG;
   Level& L0 = h->L[0];
   const bool rx = h->p.reaction != ST_REACTION_NONE;
@@ -1403,17 +1551,33 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
           double B[MAXM][MAXM];
           for (int a2 = 0; a2 < MAXM; ++a2)
             for (int b = 0; b < MAXM; ++b) B[a2][b] = h->Bf[a2][b];
-          launch_backtransform<double>(L0.g.Ns, L0.Nt, h->p.M, B, L0.omega, 0, (const double*)L0.in[0].z,
+          launch_backtransform<double>(L0.g, L0.Nt, h->p.M, B, L0.omega, 0, (const double*)L0.in[0].z,
                                        (double*)L0.e, st);
         } else {
           float B[MAXM][MAXM];
           for (int a2 = 0; a2 < MAXM; ++a2)
             for (int b = 0; b < MAXM; ++b) B[a2][b] = (float)h->Bf[a2][b];
-          launch_backtransform<float>(L0.g.Ns, L0.Nt, h->p.M, B, (float)L0.omega, 0, (const float*)L0.in[0].z,
+          launch_backtransform<float>(L0.g, L0.Nt, h->p.M, B, (float)L0.omega, 0, (const float*)L0.in[0].z,
                                       (float*)L0.e, st);
         }
         CKL();
         return ST_OK;
+      }
+      case ST_KERNEL_SHIFTED_RESIDUAL:
+      case ST_KERNEL_INNER_RESTRICT:
+      case ST_KERNEL_PROLONG: {
+        auto go = [&](auto tag) -> int {
+          using TT = decltype(tag);
+          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(h, L0.dt), rx);
+          if (which == ST_KERNEL_SHIFTED_RESIDUAL) launch_shifted_residual<TT>(h->D, ip, st);
+          else if (which == ST_KERNEL_INNER_RESTRICT) launch_inner_restrict<TT>(h->D, ip, st);
+          else
+            launch_prolong_space_add<TT>(h->D, L0.in[0].g, L0.in[1].g, (long long)L0.Nt * h->p.M,
+                                         (const TT*)L0.in[1].z, (TT*)L0.in[0].z, st);
+          CKL();
+          return ST_OK;
+        };
+        return h->fp64 ? go(double(0)) : go(float(0));
       }
       default:
         return cycle(h, 0);
@@ -1424,6 +1588,17 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_LEVEL_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_JACOBI: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
+    case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_INNER_RESTRICT: {
+      const double Dc = (double)L0.in[1].g.Ns * L0.Nt * h->p.M;
+      bytes = D * es + 2 * Dc * es + (rx ? (double)L0.in[1].g.Ns * L0.Nt * es : 0);
+      break;
+    }
+    case ST_KERNEL_PROLONG: {
+      const double Dc = (double)L0.in[1].g.Ns * L0.Nt * h->p.M;
+      bytes = 2 * D * es + Dc * es;
+      break;
+    }
     default: bytes = 0;
   }
   TRY(one(h->stream));  // warm (and capture, for the cycle)

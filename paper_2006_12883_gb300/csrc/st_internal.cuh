@@ -13,12 +13,27 @@ namespace st {
 
 enum { BC_DIR = ST_BC_DIRICHLET, BC_PER = ST_BC_PERIODIC, BC_NEU = ST_BC_NEUMANN };
 
+// Division of 0 <= n < 2^31 by a fixed divisor d with a multiply-high and a
+// shift: with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(m, n) + n) >> l (Granlund and Montgomery, PLDI 1994).
+struct FastDiv {
+  unsigned d, m, l;
+  __host__ __device__ FastDiv() : d(1), m(1), l(0) {}
+  __host__ explicit FastDiv(unsigned dv) : d(dv ? dv : 1) {
+    l = 0;
+    while ((1ull << l) < d) ++l;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(m, n) + n) >> l; }
+};
+
 // A spatial grid as the kernels see it (x fastest, unused axes have n = 1).
 struct GridP {
   int n0, n1, n2;
   int bc;
   long long Ns;
   double ih2[3];  // 1/h^2 per axis (0 for unused axes)
+  FastDiv f0, f1, fNs;  // division by n0, n1 and Ns
 };
 
 // Index helpers --------------------------------------------------------------
@@ -28,6 +43,108 @@ __host__ __device__ inline void decompose(long long s, const GridP& g, int& i, i
   long long r = s / g.n0;
   j = (int)(r % g.n1);
   k = (int)(r / g.n1);
+}
+
+// Flattened (block, point) index -> block number b, point s and its (i,j,k).
+// idx < 2^31 is guaranteed by the host (Ns * slabs < 2^31).
+__device__ __forceinline__ void split_index(unsigned idx, const GridP& g, int& b, int& s, int& i, int& j,
+                                            int& k) {
+  b = (int)g.fNs.div(idx);
+  s = (int)(idx - (unsigned)b * (unsigned)g.Ns);
+  const int r = (int)g.f0.div((unsigned)s);
+  i = s - r * g.n0;
+  k = (int)g.f1.div((unsigned)r);
+  j = r - k * g.n1;
+}
+
+__device__ __forceinline__ void point_ijk(int s, const GridP& g, int& i, int& j, int& k) {
+  const int r = (int)g.f0.div((unsigned)s);
+  i = s - r * g.n0;
+  k = (int)g.f1.div((unsigned)r);
+  j = r - k * g.n1;
+}
+
+// Sum of the two neighbours of point s along one axis (index q of n, stride
+// st) under the boundary rule: zero (DIRICHLET), wrap (PERIODIC), mirror
+// (NEUMANN).
+template <typename T, typename AT>
+__device__ __forceinline__ AT nbr_sum(const T* __restrict__ p, long long s, int q, int n, long long st, int bc) {
+  AT a, b;
+  if (q > 0) a = (AT)p[s - st];
+  else a = (bc == BC_PER) ? (AT)p[s + (long long)(n - 1) * st] : (bc == BC_NEU ? (AT)p[s + st] : (AT)0);
+  if (q < n - 1) b = (AT)p[s + st];
+  else b = (bc == BC_PER) ? (AT)p[s - (long long)(n - 1) * st] : (bc == BC_NEU ? (AT)p[s - st] : (AT)0);
+  return a + b;
+}
+
+// Neighbour offsets of one point (relative to it) and a validity mask (a
+// cleared bit is a zero DIRICHLET ghost), computed once per point and shared
+// by all planes of a slab.
+struct Nbr {
+  long long o[6];
+  unsigned mask;
+};
+
+template <int D>
+__device__ __forceinline__ Nbr make_nbr(int i, int j, int k, const GridP& g) {
+  Nbr nb;
+  nb.mask = 0x3f;
+  const int q[3] = {i, j, k};
+  const int n[3] = {g.n0, g.n1, g.n2};
+  const long long st[3] = {1, g.n0, (long long)g.n0 * g.n1};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      long long lo = -st[a], hi = st[a];
+      if (q[a] == 0) {
+        if (g.bc == BC_PER) lo = (long long)(n[a] - 1) * st[a];
+        else if (g.bc == BC_NEU) lo = st[a];
+        else { lo = 0; nb.mask &= ~(1u << (2 * a)); }
+      }
+      if (q[a] == n[a] - 1) {
+        if (g.bc == BC_PER) hi = -(long long)(n[a] - 1) * st[a];
+        else if (g.bc == BC_NEU) hi = -st[a];
+        else { hi = 0; nb.mask &= ~(1u << (2 * a + 1)); }
+      }
+      nb.o[2 * a] = lo;
+      nb.o[2 * a + 1] = hi;
+    } else {
+      nb.o[2 * a] = nb.o[2 * a + 1] = 0;
+    }
+  }
+  return nb;
+}
+
+// nu * Lap u + acc from precomputed neighbours (c = nu/h^2 per axis,
+// k2 = -2 (c_x + c_y + c_z)).
+template <int D, typename T, typename AT>
+__device__ __forceinline__ AT lap_nb(const T* __restrict__ p, long long s, const Nbr& nb, AT u, AT cx, AT cy,
+                                     AT cz, AT k2, AT acc) {
+  acc = fma(k2, u, acc);
+  const AT c[3] = {cx, cy, cz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      AT lo = (AT)p[s + nb.o[2 * a]];
+      AT hi = (AT)p[s + nb.o[2 * a + 1]];
+      lo = (nb.mask & (1u << (2 * a))) ? lo : (AT)0;
+      hi = (nb.mask & (1u << (2 * a + 1))) ? hi : (AT)0;
+      acc = fma(c[a], lo + hi, acc);
+    }
+  }
+  return acc;
+}
+
+// c_x (a+b)_x + c_y (a+b)_y + c_z (a+b)_z + k2 u with c = nu/h^2 per axis and
+// k2 = -2 (c_x + c_y + c_z): nu * Lap u, accumulated onto acc.
+template <int D, typename T, typename AT>
+__device__ __forceinline__ AT lap_acc(const T* __restrict__ p, long long s, int i, int j, int k, const GridP& g,
+                                      AT u, AT cx, AT cy, AT cz, AT k2, AT acc) {
+  acc = fma(k2, u, acc);
+  acc = fma(cx, nbr_sum<T, AT>(p, s, i, g.n0, 1, g.bc), acc);
+  if (D >= 2) acc = fma(cy, nbr_sum<T, AT>(p, s, j, g.n1, g.n0, g.bc), acc);
+  if (D >= 3) acc = fma(cz, nbr_sum<T, AT>(p, s, k, g.n2, (long long)g.n0 * g.n1, g.bc), acc);
+  return acc;
 }
 
 // Laplacian (without the diffusion coefficient) of the plane p at point s,
@@ -117,16 +234,18 @@ __device__ __forceinline__ int prol_1d(int i, int nc, int bc, int idx[2], float 
 
 // Reaction terms -------------------------------------------------------------
 
+// R(u) = rho u (1 - u) = u * (rho - rho u);  rho u (1 - u^2) = u * (rho - rho u u)
 template <typename AT>
 __device__ __forceinline__ AT react(int kind, AT rho, AT u) {
-  if (kind == ST_REACTION_LOGISTIC) return rho * u * ((AT)1 - u);
-  if (kind == ST_REACTION_CUBIC) return rho * u * ((AT)1 - u * u);
+  if (kind == ST_REACTION_LOGISTIC) return u * fma(-rho, u, rho);
+  if (kind == ST_REACTION_CUBIC) return u * fma(-rho * u, u, rho);
   return (AT)0;
 }
+// R'(u) = rho - 2 rho u;  rho - 3 rho u^2
 template <typename AT>
 __device__ __forceinline__ AT dreact(int kind, AT rho, AT u) {
-  if (kind == ST_REACTION_LOGISTIC) return rho * ((AT)1 - (AT)2 * u);
-  if (kind == ST_REACTION_CUBIC) return rho * ((AT)1 - (AT)3 * u * u);
+  if (kind == ST_REACTION_LOGISTIC) return fma((AT)-2 * rho, u, rho);
+  if (kind == ST_REACTION_CUBIC) return fma((AT)-3 * rho * u, u, rho);
   return (AT)0;
 }
 template <typename AT>
@@ -153,12 +272,19 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Parameter blocks -----------------------------------------------------------
 
+// Stencil coefficients nu/h^2 per axis and the diagonal -2 sum of them.
+template <typename AT>
+struct StencilC {
+  AT cx, cy, cz, k2;
+};
+
 // Fine FP64 residual (*) and its adjoint; also the SDC right-hand side.
 struct ResidParams {
   GridP g;
-  int Nt, M, chunk;
+  int Nt, M, chunk, nchunks;
   double dtq[MAXM][MAXM];  // dt*Q (forward) or dt*Q^T (adjoint: row = output node)
   double nu, rho;
+  StencilC<double> sc;
   int reaction;
   const double* U;
   const double* u0;    // forward: slab coupling of the first slab
@@ -169,31 +295,36 @@ struct ResidParams {
   double* partial;     // per-block sums of squares (may be null)
 };
 
+// Shifted slab systems of the Q-diagonalised solve, one entry per plane:
+// kind[p] = SH_REAL (a real eigenvalue), SH_RE / SH_IM (real and imaginary
+// part of a complex eigenvalue, planes p and p+1) or SH_NONE.  Plane p with
+// kind SH_REAL or SH_RE solves (I - s (nu*Delta + cbar)) z = y with
+// s = sr[p] + i si[p] = dt_l * lambda.
+enum { SH_REAL = 0, SH_RE = 1, SH_IM = 2, SH_NONE = 3 };
+template <typename T>
+struct Shifts {
+  int kind[MAXM];
+  T sr[MAXM], si[MAXM];
+};
+
 // Level operator A_l e - C e of the cycle (cycle precision T).
 template <typename T>
 struct LinParams {
   GridP g;
-  int Nt, M, chunk;
+  int Nt, M, chunk, nchunks;
   int transpose;       // 0: forward operator, 1: A^T and C^T
   T W[MAXM][MAXM];     // dt_l*Q (forward) or dt_l*Q^T (transpose)
-  T nu;
+  StencilC<T> sc;
   const T* e;          // may be null (= 0)
   const T* r;
   const T* cbar;       // may be null (= 0)
   T* out;
   int transform;       // 1: out = F * res (per point, over the M nodes)
   T F[MAXM][MAXM];
-};
-
-// Shift groups of the Q-diagonalised slab solve: group q occupies plane
-// plane[q] (real) or planes plane[q], plane[q]+1 (re, im) and solves
-// (I - s_q (nu*Delta + cbar)) z = y with s_q = dt_l * lambda_q.
-template <typename T>
-struct Shifts {
-  int ngroups;
-  int plane[MAXM];
-  int cplx[MAXM];
-  T sr[MAXM], si[MAXM];
+  // optional zero-start Jacobi of the shifted slab systems on out (transform = 1)
+  T* zout;
+  Shifts<T> sh;
+  T omega_j;
 };
 
 template <typename T>
@@ -202,15 +333,23 @@ struct InnerParams {
   GridP gc;           // next coarser grid (restriction)
   int Nt, P;          // slabs, planes per slab
   Shifts<T> sh;
-  T nu, omega;        // diffusion, Jacobi weight
+  StencilC<T> sc;     // this grid
+  T k2c;              // diagonal coefficient of the coarser grid
+  T omega;            // Jacobi weight
   const T* cbar;      // [Nt][Ns] (may be null)
   const T* cbarc;     // coarse cbar (may be null)
   const T* y;
   const T* z;
   T* zout;
+  const T* res;       // fine residual of the shifted systems (restriction input)
   T* yc;              // coarse rhs (restriction)
-  T* zc;              // coarse initial guess (restriction) - set to omega*D^-1*yc
+  T* zc;              // coarse start omega*D^-1*yc (restriction)
   int iters;          // coarse kernel sweeps
+  // optional fused epilogue of a Jacobi sweep: e = (e_zero ? 0 : e) + omega_bt B z'
+  int fuse_bt, e_zero;
+  T B[MAXM][MAXM];
+  T omega_bt;
+  T* e;
 };
 
 }  // namespace st

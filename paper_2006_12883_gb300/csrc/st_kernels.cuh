@@ -43,10 +43,11 @@ void launch_scatter_plane(int fp64, const void* src, void* dst, long long Ns, in
 // k_level.cu
 template <typename T> void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st);
 template <typename T>
-void launch_backtransform(long long Ns, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero,
+void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero,
                           const T* z, T* e, cudaStream_t st);
 template <typename T> void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st);
 template <typename T> void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st);
+template <typename T> void launch_shifted_residual(int D, const InnerParams<T>& p, cudaStream_t st);
 template <typename T> size_t inner_coarse_smem(const InnerParams<T>& p);
 template <typename T> void launch_inner_coarse(int D, const InnerParams<T>& p, cudaStream_t st);
 template <typename T>
@@ -56,12 +57,12 @@ template <typename T>
 void launch_prolong_space_add(int D, const GridP& gf, const GridP& gc, long long planes, const T* c, T* f,
                               cudaStream_t st);
 template <typename T>
-void launch_restrict_time(long long Ns, int Ntc, int M, const double R[MAXM][2 * MAXM], const T* f, T* c,
+void launch_restrict_time(const GridP& g, int Ntc, int M, const double R[MAXM][2 * MAXM], const T* f, T* c,
                           cudaStream_t st);
 template <typename T>
-void launch_prolong_time_add(long long Ns, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
+void launch_prolong_time_add(const GridP& g, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
                              cudaStream_t st);
-template <typename T> void launch_cbar_time(long long Ns, int Ntc, const T* f, T* c, cudaStream_t st);
+template <typename T> void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st);
 
 // k_coarse.cu
 template <typename T> size_t coarse_setup_smem(const CoarseParams<T>& p);

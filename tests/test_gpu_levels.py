@@ -156,12 +156,14 @@ def test_smoothing_step_converged_inner(case):
 @pytest.mark.parametrize("case", [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5], ids=lambda c: c.name)
 @pytest.mark.parametrize("transpose", [False, True])
 def test_level_vcycle_contracts(case, transpose):
-    """One V-cycle on A e - C e = r (zero start) reduces the residual."""
+    """One V-cycle on A e - C e = r (zero start) reduces the residual.  Levels
+    with mu_l < 1 smooth with damping 0.5, which bounds the per-cycle
+    contraction of slab-local error near 1/2, hence the 0.6 bound."""
     p, S, U = _setup(case, "fp64")
     shp = S.level_shape(0)
     r = torch.tensor(stgen.random_field(shp, 600), device="cuda")
     e = S.level_vcycle(r, transpose=transpose)
     res = S.level_residual(0, e, r, transpose=transpose)
     ratio = float(res.norm() / r.norm())
-    assert ratio < 0.5, ratio
+    assert ratio < 0.6, ratio
     S.close()
