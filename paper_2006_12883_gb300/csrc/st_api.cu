@@ -62,34 +62,6 @@ struct Alloc {
   size_t bytes;
 };
 
-double spacing(int bc, int n, double X) {
-  if (bc == ST_BC_DIRICHLET) return X / (n + 1);
-  if (bc == ST_BC_PERIODIC) return X / n;
-  return X / (n - 1);
-}
-
-GridP make_grid(int d, const int n[3], int bc, double X) {
-  GridP g;
-  g.n0 = n[0];
-  g.n1 = d >= 2 ? n[1] : 1;
-  g.n2 = d >= 3 ? n[2] : 1;
-  g.bc = bc;
-  g.Ns = (long long)g.n0 * g.n1 * g.n2;
-  const int nn[3] = {g.n0, g.n1, g.n2};
-  for (int a = 0; a < 3; ++a) {
-    if (a < d) {
-      const double h = spacing(bc, nn[a], X);
-      g.ih2[a] = 1.0 / (h * h);
-    } else {
-      g.ih2[a] = 0.0;
-    }
-  }
-  g.f0 = FastDiv((unsigned)g.n0);
-  g.f1 = FastDiv((unsigned)g.n1);
-  g.fNs = FastDiv((unsigned)std::min<long long>(g.Ns, 0x7fffffffLL));
-  return g;
-}
-
 template <typename T>
 StencilC<T> stencil_of(const GridP& g, double nu) {
   StencilC<T> c;

@@ -36,6 +36,36 @@ struct GridP {
   FastDiv f0, f1, fNs;  // division by n0, n1 and Ns
 };
 
+// Grid construction (host) ---------------------------------------------------
+
+inline double spacing(int bc, int n, double X) {
+  if (bc == BC_DIR) return X / (n + 1);
+  if (bc == BC_PER) return X / n;
+  return X / (n - 1);
+}
+
+inline GridP make_grid(int d, const int n[3], int bc, double X) {
+  GridP g;
+  g.n0 = n[0];
+  g.n1 = d >= 2 ? n[1] : 1;
+  g.n2 = d >= 3 ? n[2] : 1;
+  g.bc = bc;
+  g.Ns = (long long)g.n0 * g.n1 * g.n2;
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  for (int a = 0; a < 3; ++a) {
+    if (a < d) {
+      const double h = spacing(bc, nn[a], X);
+      g.ih2[a] = 1.0 / (h * h);
+    } else {
+      g.ih2[a] = 0.0;
+    }
+  }
+  g.f0 = FastDiv((unsigned)g.n0);
+  g.f1 = FastDiv((unsigned)g.n1);
+  g.fNs = FastDiv((unsigned)(g.Ns < 0x7fffffffLL ? g.Ns : 0x7fffffffLL));
+  return g;
+}
+
 // Index helpers --------------------------------------------------------------
 
 __host__ __device__ inline void decompose(long long s, const GridP& g, int& i, int& j, int& k) {
