@@ -308,6 +308,34 @@ typedef struct {
 /* Launch counts of the captured graphs (0 before the first st_vcycle). */
 int st_stats(st_handle* h, st_stats_info* out);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free residual norm (no counterpart in the paper: it exists for
+ * callers that cannot allocate device memory where they need a residual
+ * norm - code running under another framework's fixed-budget memory pool,
+ * code called from inside an allocator callback, or a latency-critical loop
+ * that must not pay cudaMalloc's implicit synchronisation).
+ *
+ * Computes G(U) of (*) in FP64 exactly like st_residual, without a handle
+ * and without allocating: the per-block partial sums of the norm live in a
+ * fixed file-scope device array of 2^18 + 1 doubles (2 MiB) that every GPU
+ * loading the library keeps until process exit.
+ *   p       problem; p->u0 must be a DEVICE pointer (Ns doubles)
+ *   U       device, Nt*M*Ns doubles
+ *   R       device, Nt*M*Ns doubles receiving G(U), or NULL
+ *   norm_out host double receiving ||G(U)||_2, or NULL (then the call does
+ *           not synchronise)
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents:
+ * calls that overlap on the GPU (different streams or devices' host
+ * threads racing on the same device) race on it - serialise them.
+ * Errors: ST_ERR_INVALID_ARG for bad sizes or host pointers;
+ * ST_ERR_UNSUPPORTED when a spatial plane has more than 2^26 points (the
+ * partial sums would not fit) or Ns*Nt >= 2^31; ST_ERR_CUDA on a CUDA error.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+int st_residual_noalloc(const st_problem* p, const double* U, double* R, double* norm_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

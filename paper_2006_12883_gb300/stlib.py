@@ -111,6 +111,7 @@ _SIGS = {
     "st_level_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "st_time_kernel": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_double), POINTER(c_double)]),
     "st_stats": (c_int, [c_void_p, POINTER(StStatsInfo)]),
+    "st_residual_noalloc": (c_int, [POINTER(StProblem), c_void_p, c_void_p, POINTER(c_double), c_void_p]),
 }
 
 KERNEL_FINE_RESIDUAL, KERNEL_LEVEL_RESIDUAL, KERNEL_JACOBI, KERNEL_BACKTRANSFORM, KERNEL_VCYCLE = 0, 1, 2, 3, 4
