@@ -13,7 +13,7 @@ Ranks run independent replicas of the workload (each its own seeded problem,
 no collective on the data path: weak scaling); value = all ranks' dofs per
 step / the slowest rank's time per step.
 
---impl reference times the CPU oracle (slab-by-slab Newton with sparse LU)
+--impl reference times the CPU oracle (slab-by-slab Newton, GMRES slab solves)
 on a bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
@@ -103,6 +103,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one fine-level launch, from an ncu capture of
+# `python bench.py --probe` (profiles/); valid only for the kernel source it
+# was taken on (sha256 of the file that holds the kernel).
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(kernel, dofs):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec:
+        return None
+    path = os.path.join(ROOT, "paper_2006_12883_gb300", "csrc", rec["file"])
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return rec["dram_bytes"] if sha == rec["sha256"] else None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -155,7 +172,7 @@ def oracle_baseline(nslabs=1, reps=1):
     dofs = nslabs * WORKLOAD["M"] * Ns
     t = min(ts)
     return {"value": dofs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"sequential Newton + sparse LU solve of the first {nslabs} of {WORKLOAD['Nt']} slabs "
+            "sample": f"slab-by-slab Newton (GMRES slab solves) of the first {nslabs} of {WORKLOAD['Nt']} slabs "
                       f"({dofs} dofs, {t:.2f} s, best of {len(ts)})"}
 
 
@@ -256,19 +273,22 @@ def run_ours(args):
         kms, kb = S.time_kernel(which, U, iters=max(5, args.steps // 2))
         kernels[name] = {"ms": kms, "bytes": kb, "GBps": (kb / (kms / 1e3) / 1e9) if kb else None}
     hbm, src = measured_peaks()
-    # dominant kernel of the step: the FP64 fine residual (FP64 ALU bound);
-    # the FP32 kernels are HBM bound and reported against the copy peak
-    k = kernels["fine_residual_fp64"]
-    fp64_flops_per_dof = 26.0
-    achieved_tflops = fp64_flops_per_dof * D / (k["ms"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_residual (FP64 fine residual)",
-                "achieved": achieved_tflops, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_TFLOPS_NOMINAL, "traffic": None,
-                "peak_source": "nominal FP64 rate of the pool's hardware notes",
-                "hbm": {"achieved_GBps": k["GBps"], "peak": hbm, "frac": k["GBps"] / hbm,
-                        "peak_source": src}}
+    # dominant kernel (largest share of the cycle's time in the ncu launch
+    # list): the fine-level Jacobi sweep of the shifted slab systems, fused with
+    # the back-transform and the block-Jacobi update; HBM bound
+    k = kernels["slab_jacobi"]
+    roofline = {"bound": "hbm", "kernel": "k_inner4<2,3,1>: fine-level Jacobi sweep + back-transform + update",
+                "achieved": k["GBps"], "peak": hbm, "unit": "GB/s", "frac": k["GBps"] / hbm,
+                "traffic": ncu_traffic("k_inner4", D),
+                "peak_source": f"{src} copy bandwidth (burst; kernel timed alone)",
+                "bytes_per_dof": k["bytes"] / D}
+    kf = kernels["fine_residual_fp64"]
+    fine_residual = {"kernel": "k_residual_ff: FP64-accurate residual in double-float arithmetic",
+                     "ms": kf["ms"], "GBps": kf["GBps"], "frac_of_hbm": kf["GBps"] / hbm,
+                     "note": "issue bound on the FP32/integer pipes (double-float emulation of FP64)"}
     fp32_kernels = {n: {"GBps": kernels[n]["GBps"], "frac_of_" + src + "_hbm": kernels[n]["GBps"] / hbm}
-                    for n in ("level_residual_transform", "slab_jacobi", "backtransform_update")}
+                    for n in ("level_residual_transform", "slab_jacobi", "shifted_residual", "inner_restrict",
+                              "prolong_add")}
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -312,6 +332,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": stats["launches_per_vcycle"] * args.steps,
                 "clocks": clk, "kernels": kernels, "fp32_kernels_hbm": fp32_kernels,
+                "fine_residual": fine_residual,
                 "final_rel_residual": norms[-1] / (math.sqrt(w["M"]) * float((u0 ** 2).sum()) ** 0.5),
                 "extras": extras, "stats": stats}
         print(json.dumps(line), flush=True)
@@ -336,7 +357,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, dofs=WORKLOAD["Nt"] * dofs, parallelism="cpu oracle, 1 thread"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: sequential Newton + sparse LU solve of slab 1 of "
+                             "sample": f"each step: Newton (GMRES slab solves) on slab 1 of "
                                        f"{WORKLOAD['Nt']} ({dofs} dofs)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

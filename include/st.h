@@ -281,7 +281,8 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e);
 enum {
   ST_KERNEL_FINE_RESIDUAL = 0, /* FP64 residual G(U) -> cycle precision + cbar */
   ST_KERNEL_LEVEL_RESIDUAL = 1,/* level-0 residual r - A e + C e with the Q-eigenbasis transform */
-  ST_KERNEL_JACOBI = 2,        /* one Jacobi sweep of the level-0 shifted slab systems */
+  ST_KERNEL_JACOBI = 2,        /* level-0 Jacobi sweep of the shifted slab systems fused with the
+                                  back-transform and damped update of e (the cycle's last sweep) */
   ST_KERNEL_BACKTRANSFORM = 3, /* level-0 back-transform + damped block-Jacobi update */
   ST_KERNEL_VCYCLE = 4,        /* one whole V-cycle (graph replay), not a single kernel */
   ST_KERNEL_SHIFTED_RESIDUAL = 5, /* residual of the level-0 shifted slab systems */

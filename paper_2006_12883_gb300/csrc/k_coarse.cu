@@ -67,9 +67,15 @@ __global__ void __launch_bounds__(256) k_coarse_setup(CoarseParams<T> p) {
     __syncthreads();
     for (int c = threadIdx.x; c < W2; c += blockDim.x) A[col * W2 + c] *= inv;
     __syncthreads();
-    for (int t = threadIdx.x; t < K * W2; t += blockDim.x) {
-      const int r = t / W2, c = t % W2;
-      if (r != col && c != col) A[t] -= A[r * W2 + col] * A[col * W2 + c];
+    {
+      // rows by warp, columns by lane: no per-element index division
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int r = warp; r < K; r += nw) {
+        if (r == col) continue;
+        const T f = A[r * W2 + col];
+        for (int c = lane; c < W2; c += 32)
+          if (c != col) A[r * W2 + c] -= f * A[col * W2 + c];
+      }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < K; r += blockDim.x)

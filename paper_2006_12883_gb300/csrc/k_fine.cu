@@ -11,6 +11,8 @@
 
 namespace st {
 
+long long residual_blocks(const ResidParams& p);
+
 // ---------------------------------------------------------------------------
 // K1: r = G(U),  cbar_n = mean_m R'(U_{n,m}),  partial sums of G^2.
 // ---------------------------------------------------------------------------
@@ -65,6 +67,187 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
     const double t = block_sum(sq);
     if (threadIdx.x == 0) p.partial[blockIdx.x] = t;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same residual in double-float arithmetic on the FP32 pipes, for the
+// FP32 cycle (output rounded to float).  A value is an unevaluated sum
+// hi + lo of two floats (about 48 significant bits).  Error-free
+// transformations: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based
+// exact product error (Dekker 1971); additions use the "sloppy" double-float
+// add whose error is bounded by a few 2^-48 times the operands' magnitudes,
+// which is the scale the residual tolerance is stated in.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// a * c with c = chi + clo
+__device__ __forceinline__ ff ff_mul_c(ff a, float chi, float clo) {
+  const float p = a.hi * chi;
+  float e = fmaf(a.hi, chi, -p);
+  e = fmaf(a.hi, clo, e);
+  e = fmaf(a.lo, chi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) { return ff_mul_c(a, b.hi, b.lo); }
+// acc + a * c
+__device__ __forceinline__ ff ff_madd_c(ff acc, ff a, float chi, float clo) {
+  const float p = a.hi * chi;
+  float e = fmaf(a.hi, chi, -p);
+  e = fmaf(a.hi, clo, e);
+  e = fmaf(a.lo, chi, e);
+  const ff s = two_sum(acc.hi, p);
+  return fast_two_sum(s.hi, s.lo + (acc.lo + e));
+}
+
+// Split a double into hi + lo floats with integer operations only: hi keeps
+// the leading 24 significant bits (truncated), lo the next 29 bits rounded to
+// 24.  Magnitudes below 2^-126 become 0 and lo is dropped below 2^-74; both
+// are far below the residual's rounding level for O(1) data; infinities and
+// NaNs stay infinities and NaNs.
+__device__ __forceinline__ ff split_double(double u) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+  float hi = (e >= 897) ? __uint_as_float(hb) : 0.0f;
+  if (e > 1150) {  // beyond the float range: infinity, or NaN for a NaN input
+    const bool nan = (e == 2047) && (((hw & 0xfffffu) | lw) != 0u);
+    return {__uint_as_float(nan ? 0x7fc00000u : (sign | 0x7f800000u)), 0.0f};
+  }
+  const float scale = __uint_as_float((unsigned)max(e - 948, 0) << 23);  // 2^(e-1075), 0 if subnormal
+  float lo = __uint2float_rn(lw & 0x1fffffffu) * scale;
+  lo = (e >= 949) ? lo : 0.0f;
+  return {hi, sign ? -lo : lo};
+}
+
+struct FFC {
+  float hi, lo;
+};
+struct ResidFF {
+  FFC cx, cy, cz, k2, rho, w[MAXM][MAXM];
+  float rho32;
+};
+
+__device__ __forceinline__ ff nb_ff(const double* __restrict__ p, long long s, long long o, bool valid) {
+  return valid ? split_double(p[s + o]) : ff{0.0f, 0.0f};
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  float sq = 0.0f;
+  if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
+    int ch, s, i, j, k;
+    split_index(idx, p.g, ch, s, i, j, k);
+    const Nbr nb = make_nbr<D>(i, j, k, p.g);
+    const long long Ns = p.g.Ns;
+    const int M = p.M;
+    const int n0 = ch * p.chunk;
+    const int n1 = min(n0 + p.chunk, p.Nt);
+    ff prev = split_double((n0 == 0) ? p.u0[s] : p.U[((long long)(n0 - 1) * M + (M - 1)) * Ns + s]);
+    float* R = (float*)p.R;
+    float* cb = (float*)p.cbar;
+    const float invM = 1.0f / M;
+    for (int n = n0; n < n1; ++n) {
+      const long long base = (long long)n * M * Ns + s;
+      ff u[MAXM], F[MAXM];
+      float cbs = 0.0f;
+      ff ulast = {0.0f, 0.0f};
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          const double* pl = p.U + (long long)n * M * Ns + (long long)m * Ns;
+          const ff um = split_double(pl[s]);
+          u[m] = um;
+          if (m == M - 1) ulast = um;
+          ff acc = ff_mul_c(um, c.k2.hi, c.k2.lo);
+          {
+            const ff a = nb_ff(pl, s, nb.o[0], nb.mask & 1u), b = nb_ff(pl, s, nb.o[1], nb.mask & 2u);
+            acc = ff_madd_c(acc, ff_add(a, b), c.cx.hi, c.cx.lo);
+          }
+          if (D >= 2) {
+            const ff a = nb_ff(pl, s, nb.o[2], nb.mask & 4u), b = nb_ff(pl, s, nb.o[3], nb.mask & 8u);
+            acc = ff_madd_c(acc, ff_add(a, b), c.cy.hi, c.cy.lo);
+          }
+          if (D >= 3) {
+            const ff a = nb_ff(pl, s, nb.o[4], nb.mask & 16u), b = nb_ff(pl, s, nb.o[5], nb.mask & 32u);
+            acc = ff_madd_c(acc, ff_add(a, b), c.cz.hi, c.cz.lo);
+          }
+          if (p.reaction == ST_REACTION_LOGISTIC) {
+            // rho u (1 - u) = u * (rho - rho u)
+            const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul_c(um, c.rho.hi, c.rho.lo)));
+            acc = ff_add(acc, ff_mul(um, t));
+            if (cb) cbs += fmaf(-2.0f * c.rho32, um.hi, c.rho32);
+          } else if (p.reaction == ST_REACTION_CUBIC) {
+            // rho u (1 - u^2) = u * (rho - rho u u)
+            const ff ru = ff_mul_c(um, c.rho.hi, c.rho.lo);
+            const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul(ru, um)));
+            acc = ff_add(acc, ff_mul(um, t));
+            if (cb) cbs += fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
+          }
+          F[m] = acc;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          ff g = ff_add(prev, ff_neg(u[m]));
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q < M) g = ff_madd_c(g, F[q], c.w[m][q].hi, c.w[m][q].lo);
+          const float gf = g.hi + g.lo;
+          sq = fmaf(gf, gf, sq);
+          if (R) R[base + (long long)m * Ns] = gf;
+        }
+      }
+      if (cb) cb[(long long)n * Ns + s] = cbs * invM;
+      prev = ulast;
+    }
+  }
+  if (p.partial) {
+    const double t = block_sum((double)sq);
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = t;
+  }
+}
+
+static FFC split_const(double v) {
+  FFC c;
+  c.hi = (float)v;
+  c.lo = (float)(v - (double)c.hi);
+  return c;
+}
+
+void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
+  ResidFF c;
+  c.cx = split_const(p.sc.cx);
+  c.cy = split_const(p.sc.cy);
+  c.cz = split_const(p.sc.cz);
+  c.k2 = split_const(p.sc.k2);
+  c.rho = split_const(p.rho);
+  c.rho32 = (float)p.rho;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) c.w[a][b] = split_const(p.dtq[a][b]);
+  const unsigned nb = (unsigned)residual_blocks(p);
+  if (D == 1) k_residual_ff<1><<<nb, 256, 0, st>>>(p, c);
+  else if (D == 2) k_residual_ff<2><<<nb, 256, 0, st>>>(p, c);
+  else k_residual_ff<3><<<nb, 256, 0, st>>>(p, c);
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,8 @@
 // Indexing: one thread per (slab or slab chunk, point), flattened into a
 // 32-bit index (the host guarantees Ns * slabs < 2^31); divisions by the grid
 // sizes use precomputed multiply-shift constants.
+#include <type_traits>
+
 #include "st_kernels.cuh"
 
 namespace st {
@@ -510,6 +512,8 @@ __global__ void __launch_bounds__(256) k_cbar_time(GridP g, int Ntc, const T* __
 
 template <typename T>
 void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (launch_lin_residual4(D, p, st)) return;
   const unsigned nb = nblk((long long)p.g.Ns * p.nchunks, 256);
   DISPATCH_D(D, (k_lin_residual<DD, T><<<nb, 256, 0, st>>>(p)));
 }
@@ -526,6 +530,8 @@ void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], 
 
 template <typename T>
 void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (!zero && launch_inner4(D, 1, p, st)) return;
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
   if (zero) k_inner_jacobi_zero<T><<<nb, 256, 0, st>>>(p);
   else DISPATCH_D(D, (k_inner_jacobi<DD, T><<<nb, 256, 0, st>>>(p)));
@@ -533,12 +539,16 @@ void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t 
 
 template <typename T>
 void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (launch_inner_restrict4(D, p, st)) return;
   const unsigned nb = nblk(p.gc.Ns * p.Nt, 256);
   DISPATCH_D(D, (k_inner_restrict<DD, T><<<nb, 256, 0, st>>>(p)));
 }
 
 template <typename T>
 void launch_shifted_residual(int D, const InnerParams<T>& p, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (launch_inner4(D, 0, p, st)) return;
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
   DISPATCH_D(D, (k_shifted_residual<DD, T><<<nb, 256, 0, st>>>(p)));
 }
@@ -559,6 +569,8 @@ void launch_inner_coarse(int D, const InnerParams<T>& p, cudaStream_t st) {
 template <typename T>
 void launch_restrict_space(int D, const GridP& gf, const GridP& gc, long long planes, const T* f, T* c,
                            cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (launch_restrict4(D, gf, gc, planes, f, c, st)) return;
   const unsigned nb = nblk(gc.Ns * planes, 256);
   DISPATCH_D(D, (k_restrict_space<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, f, c)));
 }
@@ -566,6 +578,8 @@ void launch_restrict_space(int D, const GridP& gf, const GridP& gc, long long pl
 template <typename T>
 void launch_prolong_space_add(int D, const GridP& gf, const GridP& gc, long long planes, const T* c, T* f,
                               cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (launch_prolong4(D, gf, gc, planes, c, f, st)) return;
   const unsigned nb = nblk(gf.Ns * planes, 256);
   DISPATCH_D(D, (k_prolong_space_add<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, c, f)));
 }

@@ -811,7 +811,8 @@ int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_
   ResidParams rp = fine_params(h, U, 0);
   rp.R = R;
   rp.cbar = (want_cbar && h->p.reaction != ST_REACTION_NONE) ? h->L[0].cbar : nullptr;
-  launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
+  if (!r_fp64 && !h->fp64) launch_residual_ff(h->D, rp, h->stream);  // FP32 output: double-float kernel
+  else launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
   CKL();
   launch_sum_partials(h->partial, residual_blocks(rp), h->scal + slot, h->stream);
   CKL();
@@ -1501,23 +1502,34 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         ResidParams rp = fine_params(h, U, 0);
         rp.R = L0.r;
         rp.cbar = rx ? L0.cbar : nullptr;
-        launch_residual(h->D, h->fp64, h->fp64, rp, st);
+        if (h->fp64) launch_residual(h->D, 1, 1, rp, st);
+        else launch_residual_ff(h->D, rp, st);
         CKL();
         return ST_OK;
       }
       case ST_KERNEL_LEVEL_RESIDUAL:
         return h->fp64 ? level_residual<double>(h, 0, 0, L0.e, L0.r, L0.in[0].y, 1, st)
                        : level_residual<float>(h, 0, 0, L0.e, L0.r, L0.in[0].y, 1, st);
-      case ST_KERNEL_JACOBI:
-        if (h->fp64) {
-          InnerParams<double> ip = inner_params<double>(h, L0, 0, h->p.M, level_shifts<double>(h, L0.dt), rx);
-          launch_inner_jacobi<double>(h->D, 0, ip, st);
-        } else {
-          InnerParams<float> ip = inner_params<float>(h, L0, 0, h->p.M, level_shifts<float>(h, L0.dt), rx);
-          launch_inner_jacobi<float>(h->D, 0, ip, st);
-        }
-        CKL();
-        return ST_OK;
+      case ST_KERNEL_JACOBI: {
+        // the fine-level sweep as the cycle runs it last: fused with the
+        // back-transform and the damped block-Jacobi update of e
+        auto go = [&](auto tag) -> int {
+          using TT = decltype(tag);
+          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(h, L0.dt), rx);
+          BtFuse<TT> f;
+          f.on = true;
+          f.e_zero = 0;
+          f.omega = (TT)L0.omega;
+          f.e = (TT*)L0.e;
+          for (int a2 = 0; a2 < MAXM; ++a2)
+            for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (TT)h->Bf[a2][b];
+          apply_fuse(ip, f);
+          launch_inner_jacobi<TT>(h->D, 0, ip, st);
+          CKL();
+          return ST_OK;
+        };
+        return h->fp64 ? go(double(0)) : go(float(0));
+      }
       case ST_KERNEL_BACKTRANSFORM: {
         if (h->fp64) {
           double B[MAXM][MAXM];
@@ -1558,7 +1570,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
   switch (which) {
     case ST_KERNEL_FINE_RESIDUAL: bytes = D * (8 + es) + (rx ? planes * es : 0); break;
     case ST_KERNEL_LEVEL_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
-    case ST_KERNEL_JACOBI: bytes = D * 3 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_JACOBI: bytes = D * 4 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
     case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_INNER_RESTRICT: {

@@ -30,6 +30,8 @@ struct CoarseParams {
 long long residual_blocks(const ResidParams& p);
 long long gradient_blocks(const ResidParams& p);
 void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st);
+// double-float variant (float residual and cbar outputs)
+void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st);
 void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st);
 void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st);
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st);
@@ -63,6 +65,15 @@ template <typename T>
 void launch_prolong_time_add(const GridP& g, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
                              cudaStream_t st);
 template <typename T> void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st);
+
+// k_level4.cu: float4 variants (return false when they do not apply)
+bool launch_lin_residual4(int D, const LinParams<float>& p, cudaStream_t st);
+bool launch_inner4(int D, int mode, const InnerParams<float>& p, cudaStream_t st);  // 0 residual, 1 Jacobi
+bool launch_prolong4(int D, const GridP& gf, const GridP& gc, long long planes, const float* c, float* f,
+                     cudaStream_t st);
+bool launch_restrict4(int D, const GridP& gf, const GridP& gc, long long planes, const float* f, float* c,
+                      cudaStream_t st);
+bool launch_inner_restrict4(int D, const InnerParams<float>& p, cudaStream_t st);
 
 // k_coarse.cu
 template <typename T> size_t coarse_setup_smem(const CoarseParams<T>& p);

@@ -64,9 +64,12 @@ CUB3D = Case("cubic3d", (8, 8, 8), P_, 5e-3, 4, 3, reaction=C_, rho=2.0, u0_kind
 DIR2D_M5 = Case("dirichlet2d_m5", (15, 31), D_, 0.05, 6, 5, reaction=L_, rho=0.5)
 RAGGED = Case("ragged_chunks", (96, 128), P_, 1e-2, 10, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=3)
 M1 = Case("m1", (16, 16), P_, 0.02, 5, 1, reaction=C_, rho=1.0)
+# periodic grids with x sizes divisible by 4 at M = 5 (the float4 kernel instances)
+PER2D_M5 = Case("periodic2d_m5", (16, 24), P_, 0.02, 4, 5, reaction=C_, rho=1.0)
+PER3D_M5 = Case("periodic3d_m5", (4, 8, 8), P_, 0.01, 4, 5, reaction=L_, rho=1.0)
 
-RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1]
-SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1]
+RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5]
+SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5]
 
 
 def residual_scale(p: system.Problem, U: np.ndarray) -> float:

@@ -8,7 +8,7 @@ import pytest
 import stgen
 from oracle import multilevel as ml
 from oracle import space, system
-from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, Case
+from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, Case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -17,7 +17,7 @@ P_ = space.PERIODIC
 # a case whose hierarchy mixes space and slab bisection (AUTO_MU) and one
 # with space bisection only (SPACE)
 MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise", seed=5)
-LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5]
+LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5]
 
 
 def _oracle_level(S, case, l, cbar):
@@ -133,7 +133,7 @@ def test_coarse_solve_exact(case, transpose):
     S.close()
 
 
-@pytest.mark.parametrize("case", [HEAT1D, LOG2D, CUB3D], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, CUB3D, PER2D_M5, PER3D_M5], ids=lambda c: c.name)
 def test_smoothing_step_converged_inner(case):
     """With many inner cycles the Q-diagonalised slab solve is exact, so one
     smoothing step equals damped block Jacobi with exact slab solves."""
@@ -153,7 +153,7 @@ def test_smoothing_step_converged_inner(case):
     S.close()
 
 
-@pytest.mark.parametrize("case", [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5], ids=lambda c: c.name)
 @pytest.mark.parametrize("transpose", [False, True])
 def test_level_vcycle_contracts(case, transpose):
     """One V-cycle on A e - C e = r (zero start) reduces the residual.  Levels
