@@ -106,7 +106,10 @@ class ClockSampler:
 # DRAM bytes (read + write) of one fine-level launch, from an ncu capture of
 # `python bench.py --probe` (profiles/); valid only for the kernel source it
 # was taken on (sha256 of the file that holds the kernel).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/hot_kernels_logistic2d_256_Nt256_M3.md: 671.2 MB read + 177.1 MB written
+    "k_inner4": {"file": "k_level4.cu", "sha256": "45927b3bd25219bec6f6b6045bdd05fc68146ab622cfaf444166009f3a195fbd", "dram_bytes": 848358912},
+}
 
 
 def ncu_traffic(kernel, dofs):

@@ -12,6 +12,7 @@
 namespace st {
 
 long long residual_blocks(const ResidParams& p);
+long long residual_blocks4(const ResidParams& p);
 
 // ---------------------------------------------------------------------------
 // K1: r = G(U),  cbar_n = mean_m R'(U_{n,m}),  partial sums of G^2.
@@ -227,11 +228,123 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
   }
 }
 
+// Four consecutive x points per thread (periodic, x size a multiple of 4,
+// M = 3 or 5): the centre and row values are double2 loads and each loaded
+// value is split once for the 4 points.
+template <int D, int M>
+__global__ void __launch_bounds__(256) k_residual_ff4(ResidParams p, ResidFF c, FastDiv fG) {
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  float sq = 0.0f;
+  const unsigned G = (unsigned)(p.g.Ns >> 2);
+  if (idx < (unsigned)p.nchunks * G) {
+    const int ch = (int)fG.div(idx);
+    const int s0 = (int)(idx - (unsigned)ch * G) << 2;
+    int i0, j, k;
+    point_ijk(s0, p.g, i0, j, k);
+    Nbr nb = make_nbr<D>(i0, j, k, p.g);  // periodic: every mask bit set
+    const long long xl = (i0 == 0) ? (long long)(p.g.n0 - 1) : -1;
+    const long long xr = (i0 + 4 == p.g.n0) ? (long long)(4 - p.g.n0) : 4;
+    const long long Ns = p.g.Ns;
+    const int n0 = ch * p.chunk;
+    const int n1 = min(n0 + p.chunk, p.Nt);
+    ff prev[4];
+    {
+      const double* pp = (n0 == 0) ? p.u0 + s0 : p.U + ((long long)(n0 - 1) * M + (M - 1)) * Ns + s0;
+      const double2 a = *reinterpret_cast<const double2*>(pp), b = *reinterpret_cast<const double2*>(pp + 2);
+      prev[0] = split_double(a.x); prev[1] = split_double(a.y);
+      prev[2] = split_double(b.x); prev[3] = split_double(b.y);
+    }
+    float* R = (float*)p.R;
+    float* cb = (float*)p.cbar;
+    for (int n = n0; n < n1; ++n) {
+      const long long base = (long long)n * M * Ns + s0;
+      ff u[M][4], F[M][4];
+      float cbs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double* pl = p.U + base + (long long)m * Ns;
+        {
+          const double2 a = *reinterpret_cast<const double2*>(pl), b = *reinterpret_cast<const double2*>(pl + 2);
+          u[m][0] = split_double(a.x); u[m][1] = split_double(a.y);
+          u[m][2] = split_double(b.x); u[m][3] = split_double(b.y);
+        }
+        const ff vl = split_double(pl[xl]), vr = split_double(pl[xr]);
+        const ff v[6] = {vl, u[m][0], u[m][1], u[m][2], u[m][3], vr};
+        ff acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = ff_mul_c(u[m][q], c.k2.hi, c.k2.lo);
+          acc[q] = ff_madd_c(acc[q], ff_add(v[q], v[q + 2]), c.cx.hi, c.cx.lo);
+        }
+#pragma unroll
+        for (int ax = 1; ax < D; ++ax) {
+          const double* lo = pl + nb.o[2 * ax];
+          const double* hi = pl + nb.o[2 * ax + 1];
+          const double2 la = *reinterpret_cast<const double2*>(lo), lb = *reinterpret_cast<const double2*>(lo + 2);
+          const double2 ha = *reinterpret_cast<const double2*>(hi), hb = *reinterpret_cast<const double2*>(hi + 2);
+          const double lv[4] = {la.x, la.y, lb.x, lb.y}, hv[4] = {ha.x, ha.y, hb.x, hb.y};
+          const FFC cc = (ax == 1) ? c.cy : c.cz;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            acc[q] = ff_madd_c(acc[q], ff_add(split_double(lv[q]), split_double(hv[q])), cc.hi, cc.lo);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const ff um = u[m][q];
+          if (p.reaction == ST_REACTION_LOGISTIC) {
+            const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul_c(um, c.rho.hi, c.rho.lo)));
+            acc[q] = ff_add(acc[q], ff_mul(um, t));
+            cbs[q] += fmaf(-2.0f * c.rho32, um.hi, c.rho32);
+          } else if (p.reaction == ST_REACTION_CUBIC) {
+            const ff ru = ff_mul_c(um, c.rho.hi, c.rho.lo);
+            const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul(ru, um)));
+            acc[q] = ff_add(acc[q], ff_mul(um, t));
+            cbs[q] += fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
+          }
+          F[m][q] = acc[q];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ff g = ff_add(prev[q], ff_neg(u[m][q]));
+#pragma unroll
+          for (int b = 0; b < M; ++b) g = ff_madd_c(g, F[b][q], c.w[m][b].hi, c.w[m][b].lo);
+          out[q] = g.hi + g.lo;
+          sq = fmaf(out[q], out[q], sq);
+        }
+        if (R) *reinterpret_cast<float4*>(R + base + (long long)m * Ns) = make_float4(out[0], out[1], out[2], out[3]);
+      }
+      if (cb) {
+        const float invM = 1.0f / M;
+        *reinterpret_cast<float4*>(cb + (long long)n * Ns + s0) =
+            make_float4(cbs[0] * invM, cbs[1] * invM, cbs[2] * invM, cbs[3] * invM);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) prev[q] = u[M - 1][q];
+    }
+  }
+  if (p.partial) {
+    const double t = block_sum((double)sq);
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = t;
+  }
+}
+
 static FFC split_const(double v) {
   FFC c;
   c.hi = (float)v;
   c.lo = (float)(v - (double)c.hi);
   return c;
+}
+
+static bool ff4_ok(int D, const ResidParams& p) {
+  return D >= 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 >= 4 && p.g.n0 % 4 == 0;
+}
+
+long long residual_ff_blocks(int D, const ResidParams& p) {
+  return ff4_ok(D, p) ? residual_blocks4(p) : residual_blocks(p);
 }
 
 void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
@@ -244,11 +357,23 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
   c.rho32 = (float)p.rho;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) c.w[a][b] = split_const(p.dtq[a][b]);
+  if (ff4_ok(D, p)) {
+    const FastDiv fG((unsigned)(p.g.Ns >> 2));
+    const unsigned nb4 = (unsigned)residual_blocks4(p);
+    if (D == 2 && p.M == 3) k_residual_ff4<2, 3><<<nb4, 256, 0, st>>>(p, c, fG);
+    else if (D == 2) k_residual_ff4<2, 5><<<nb4, 256, 0, st>>>(p, c, fG);
+    else if (p.M == 3) k_residual_ff4<3, 3><<<nb4, 256, 0, st>>>(p, c, fG);
+    else k_residual_ff4<3, 5><<<nb4, 256, 0, st>>>(p, c, fG);
+    return;
+  }
   const unsigned nb = (unsigned)residual_blocks(p);
   if (D == 1) k_residual_ff<1><<<nb, 256, 0, st>>>(p, c);
   else if (D == 2) k_residual_ff<2><<<nb, 256, 0, st>>>(p, c);
   else k_residual_ff<3><<<nb, 256, 0, st>>>(p, c);
 }
+
+// blocks of the 4-point double-float residual (one partial sum per block)
+long long residual_blocks4(const ResidParams& p) { return ((p.g.Ns >> 2) * p.nchunks + 255) / 256; }
 
 // ---------------------------------------------------------------------------
 // Adjoint residual rho = g - A^T lambda + C^T lambda with the exact Jacobian:

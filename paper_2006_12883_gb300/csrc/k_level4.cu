@@ -193,8 +193,13 @@ __global__ void __launch_bounds__(256) k_lin_residual4(LinParams<float> p, FastD
 // Shifted-system operator at 4 points of all planes: out[pl][q] = y - A z
 // (mode 0: residual into zout) or a Jacobi sweep (mode 1) with optional
 // fused back-transform into e.
+// 2D, M = 3 fits 64 registers (4 blocks of 256 per SM); larger instances
+// keep their registers rather than spill.
+template <int D, int M>
+constexpr int inner4_min_blocks() { return (D == 2 && M == 3) ? 4 : 1; }
+
 template <int D, int M, int MODE>
-__global__ void __launch_bounds__(256) k_inner4(InnerParams<float> p, FastDiv fG) {
+__global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(InnerParams<float> p, FastDiv fG) {
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)(p.g.Ns >> 2)) return;
   int n, s0, i0, j, k;

@@ -811,10 +811,15 @@ int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_
   ResidParams rp = fine_params(h, U, 0);
   rp.R = R;
   rp.cbar = (want_cbar && h->p.reaction != ST_REACTION_NONE) ? h->L[0].cbar : nullptr;
-  if (!r_fp64 && !h->fp64) launch_residual_ff(h->D, rp, h->stream);  // FP32 output: double-float kernel
-  else launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
+  long long nparts = residual_blocks(rp);
+  if (!r_fp64 && !h->fp64) {  // FP32 output: double-float kernel
+    launch_residual_ff(h->D, rp, h->stream);
+    nparts = residual_ff_blocks(h->D, rp);
+  } else {
+    launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
+  }
   CKL();
-  launch_sum_partials(h->partial, residual_blocks(rp), h->scal + slot, h->stream);
+  launch_sum_partials(h->partial, nparts, h->scal + slot, h->stream);
   CKL();
   return ST_OK;
 }

@@ -28,6 +28,8 @@ struct CoarseParams {
 
 // k_fine.cu
 long long residual_blocks(const ResidParams& p);
+// blocks (= partial sums) the FP32-output residual launches for this problem
+long long residual_ff_blocks(int D, const ResidParams& p);
 long long gradient_blocks(const ResidParams& p);
 void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st);
 // double-float variant (float residual and cbar outputs)
