@@ -33,13 +33,60 @@ sys.path.insert(0, ROOT)
 
 METRIC = "space-time dof-updates/s per V-cycle"
 UNIT = "dof/s"
-WORKLOAD = dict(workload="logistic2d_256x256_Nt256_M3", grid=[256, 256], bc="periodic", Nt=256, M=3,
-                nu=1e-2, rho=1.0, T=1.0, reaction="logistic rho*u*(1-u)", seed=12884,
-                u0="uniform[0,1) noise smoothed by 10 neighbour-averaging passes")
+NOISE = "uniform[0,1) noise smoothed by 10 neighbour-averaging passes"
+WORKLOADS = {
+    # the default: 2D logistic, 256^2 periodic, 256 slabs, 3 nodes (50.3M dofs)
+    "logistic2d_256": dict(workload="logistic2d_256x256_Nt256_M3", grid=[256, 256], bc="periodic", Nt=256, M=3,
+                           nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12884, u0=NOISE),
+    "heat1d_63": dict(workload="heat1d_dirichlet63_Nt16_M2", grid=[63], bc="dirichlet", Nt=16, M=2, nu=1.0,
+                      rho=0.0, T=1.0, reaction="none", seed=0, u0="sin(pi x) + 0.5 sin(3 pi x)"),
+    "logistic2d_1024_m3": dict(workload="logistic2d_1024x1024_Nt1024_M3", grid=[1024, 1024], bc="periodic",
+                               Nt=1024, M=3, nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12885, u0=NOISE),
+    "logistic2d_1024_m5": dict(workload="logistic2d_1024x1024_Nt1024_M5", grid=[1024, 1024], bc="periodic",
+                               Nt=1024, M=5, nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12885, u0=NOISE),
+    "cubic3d_128": dict(workload="cubic3d_128x128x128_Nt128_M3", grid=[128, 128, 128], bc="periodic", Nt=128, M=3,
+                        nu=5e-3, rho=2.0, T=1.0, reaction="cubic", seed=12886,
+                        u0="8 periodic Gaussian bumps, sigma 0.05, amplitude 1"),
+    "logistic2d_512": dict(workload="logistic2d_512x512_Nt512_M3", grid=[512, 512], bc="periodic", Nt=512, M=3,
+                           nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12887, u0=NOISE),
+}
+WORKLOAD = WORKLOADS["logistic2d_256"]
+
+
+def make_u0(w, rank=0):
+    import stgen
+    shape = tuple(w["grid"])
+    if w["bc"] == "dirichlet":
+        return stgen.sine_modes(shape[0])
+    if w["reaction"] == "cubic":
+        return stgen.gaussian_bumps(shape, w["seed"] + rank).ravel()
+    return stgen.smoothed_noise(shape, w["seed"] + rank).ravel()
+
+
+def make_solver(stlib, w, u0, **opts):
+    bc = {"periodic": stlib.PERIODIC, "dirichlet": stlib.DIRICHLET}[w["bc"]]
+    rx = {"none": stlib.NONE, "logistic": stlib.LOGISTIC, "cubic": stlib.CUBIC}[w["reaction"]]
+    return stlib.Solver(tuple(w["grid"]), bc, w["nu"], w["Nt"], w["M"], u0, T=w["T"], reaction=rx,
+                        rho=w["rho"], opts=stlib.make_opts(**opts))
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor) per the pool's hardware notes
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
                  ("prolong_add", 7), ("vcycle_graph", 4))
+
+
+def reduce_max(x, dist, device):
+    """Maximum of a per-rank float over all ranks (x itself without a group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, dofs_per_rank, ms_per_step):
+    """Whole-job throughput: every rank's dofs per step over the slowest rank's time."""
+    return world * dofs_per_rank / (ms_per_step / 1e3)
 
 
 def env_int(name, default):
@@ -143,9 +190,15 @@ from oracle import space, system
 w = json.loads({wl!r})
 nslabs = int({nslabs})
 shape = tuple(w["grid"])
-p = system.Problem(shape=shape, bc=space.PERIODIC, nu=w["nu"], Nt=w["Nt"], M=w["M"], T=w["T"],
-                   reaction=space.LOGISTIC, rho=w["rho"])
-u0 = stgen.smoothed_noise(shape, w["seed"]).ravel()
+bc = dict(periodic=space.PERIODIC, dirichlet=space.DIRICHLET)[w["bc"]]
+rx = dict(none=space.NONE, logistic=space.LOGISTIC, cubic=space.CUBIC)[w["reaction"]]
+p = system.Problem(shape=shape, bc=bc, nu=w["nu"], Nt=w["Nt"], M=w["M"], T=w["T"], reaction=rx, rho=w["rho"])
+if w["bc"] == "dirichlet":
+    u0 = stgen.sine_modes(shape[0])
+elif w["reaction"] == "cubic":
+    u0 = stgen.gaussian_bumps(shape, w["seed"]).ravel()
+else:
+    u0 = stgen.smoothed_noise(shape, w["seed"]).ravel()
 out = []
 for rep in range(int({reps})):
     t = time.perf_counter()
@@ -155,13 +208,13 @@ print(json.dumps(out))
 """
 
 
-def time_oracle(nslabs=1, reps=1):
+def time_oracle(w, nslabs=1, reps=1):
     """Seconds per oracle solve of the first `nslabs` slabs, in a fresh
     single-threaded process (BLAS / OpenMP pinned to one thread)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, wl=json.dumps(WORKLOAD), nslabs=nslabs, reps=reps)
+    code = ORACLE_SNIPPET.format(root=ROOT, wl=json.dumps(w), nslabs=nslabs, reps=reps)
     r = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
                        text=True, timeout=1800)
     if r.returncode != 0:
@@ -169,14 +222,14 @@ def time_oracle(nslabs=1, reps=1):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_baseline(nslabs=1, reps=1):
-    ts = time_oracle(nslabs, reps)
-    Ns = WORKLOAD["grid"][0] * WORKLOAD["grid"][1]
-    dofs = nslabs * WORKLOAD["M"] * Ns
+def oracle_baseline(w, nslabs=1, reps=1):
+    ts = time_oracle(w, nslabs, reps)
+    Ns = int(math.prod(w["grid"]))
+    dofs = nslabs * w["M"] * Ns
     t = min(ts)
     return {"value": dofs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"slab-by-slab Newton (GMRES slab solves) of the first {nslabs} of {WORKLOAD['Nt']} slabs "
-                      f"({dofs} dofs, {t:.2f} s, best of {len(ts)})"}
+            "sample": f"slab-by-slab Newton (GMRES / sparse-LU slab solves) of the first {nslabs} of {w['Nt']} "
+                      f"slabs ({dofs} dofs, {t:.2f} s, best of {len(ts)})"}
 
 
 # ------------------------------------------------------------------ ours
@@ -194,16 +247,13 @@ def run_ours(args):
         build()
     if dist:
         dist.barrier()
-    import stgen
     from paper_2006_12883_gb300 import stlib
 
-    w = WORKLOAD
+    w = WORKLOADS[args.config]
     shape = tuple(w["grid"])
-    u0 = stgen.smoothed_noise(shape, w["seed"] + rank).ravel()
-    opts = stlib.make_opts(precision=stlib.FP32_REFINE, tol=1e-8)
-    S = stlib.Solver(shape, stlib.PERIODIC, w["nu"], w["Nt"], w["M"], u0, T=w["T"], reaction=stlib.LOGISTIC,
-                     rho=w["rho"], opts=opts)
-    D = w["Nt"] * w["M"] * shape[0] * shape[1]
+    u0 = make_u0(w, rank)
+    S = make_solver(stlib, w, u0, precision=stlib.FP32_REFINE, tol=1e-8)
+    D = w["Nt"] * w["M"] * int(math.prod(shape))
     U = S.zeros()
     stream = torch.cuda.current_stream()
     if args.probe:
@@ -238,12 +288,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * D / (ms / 1e3)
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    value = job_value(world, D, ms)
     if args.only_steps:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
@@ -261,12 +307,8 @@ def run_ours(args):
     for _ in range(args.steps):
         S.vcycle(Uh)
     torch.cuda.synchronize()
-    ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * D / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": D * 8,
+    ms_e2e = reduce_max((time.perf_counter() - t0) * 1e3 / args.steps, dist, "cuda")
+    e2e = {"value": job_value(world, D, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": D * 8,
            "d2h_bytes_per_step": D * 8 + 8}
 
     stats = S.stats()
@@ -296,9 +338,7 @@ def run_ours(args):
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         for name, prec in (("fp32_refine", stlib.FP32_REFINE), ("fp64", stlib.FP64)):
-            S2 = stlib.Solver(shape, stlib.PERIODIC, w["nu"], w["Nt"], w["M"], u0, T=w["T"],
-                              reaction=stlib.LOGISTIC, rho=w["rho"],
-                              opts=stlib.make_opts(precision=prec, tol=1e-8, max_iters=100))
+            S2 = make_solver(stlib, w, u0, precision=prec, tol=1e-8, max_iters=100)
             V = S2.zeros()
             S2.solve(V)  # warm (graph capture)
             V.zero_()
@@ -308,8 +348,7 @@ def run_ours(args):
                                               "rel_residual": info["rel_residual"]}
             S2.close()
         # SDC sweep throughput on the same workload
-        S3 = stlib.Solver(shape, stlib.PERIODIC, w["nu"], w["Nt"], w["M"], u0, T=w["T"],
-                          reaction=stlib.LOGISTIC, rho=w["rho"], opts=stlib.make_opts())
+        S3 = make_solver(stlib, w, u0)
         V = S3.zeros()
         S3.sdc_sweep(V, 2)
         torch.cuda.synchronize()
@@ -318,11 +357,32 @@ def run_ours(args):
         torch.cuda.synchronize()
         extras["sdc_sweep_dof_per_s"] = D * 5 / (time.perf_counter() - t0)
         S3.close()
+        if w["bc"] == "periodic":
+            # adjoint: gradient of 1/2 h^d |u(T) - u_target|^2 w.r.t. nu, rho, u0
+            S4 = make_solver(stlib, w, u0, tol=1e-8)
+            S4.set_params(1.3e-2, 0.8)
+            V = S4.zeros()
+            S4.solve(V)
+            target = V[-1, -1].reshape(-1).clone()
+            S4.set_params(w["nu"], w["rho"])
+            V.zero_()
+            S4.solve(V)
+            du0 = torch.empty_like(target)
+            S4.adjoint(V, target=target, du0=du0)  # warm (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dnu, drho, ainfo = S4.adjoint(V, target=target, du0=du0)
+            torch.cuda.synchronize()
+            extras["adjoint_solve"] = {"seconds": time.perf_counter() - t0, "iterations": ainfo["iterations"],
+                                       "rel_residual": ainfo["rel_residual"], "dPhi_dnu": dnu, "dPhi_drho": drho}
+            S4.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = oracle_baseline(nslabs=4, reps=1)
+            # about 10-30 s of single-core oracle work
+            ns = {"logistic2d_256": 4, "heat1d_63": 16}.get(args.config, 1)
+            cpu = oracle_baseline(w, nslabs=ns, reps=1)
         except Exception as ex:  # the GPU number stands without it
             cpu = {"error": str(ex)[:200]}
 
@@ -330,7 +390,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": dict(WORKLOAD, dofs=D, precision="fp32 cycle + fp64 residual/update",
+                "config": dict(w, dofs=D, precision="fp32 cycle + FP64-accurate residual/update",
                                parallelism=f"replicas{world}", l2="inputs larger than L2 (no flush)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": stats["launches_per_vcycle"] * args.steps,
@@ -349,19 +409,20 @@ def run_reference(args):
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     if rank != 0:
         return
-    ts = time_oracle(nslabs=1, reps=args.warmup + args.steps)
+    w = WORKLOADS[args.config]
+    ts = time_oracle(w, nslabs=1, reps=args.warmup + args.steps)
     timed = ts[args.warmup:]
-    Ns = WORKLOAD["grid"][0] * WORKLOAD["grid"][1]
-    dofs = WORKLOAD["M"] * Ns
+    Ns = int(math.prod(w["grid"]))
+    dofs = w["M"] * Ns
     t = sum(timed) / len(timed)
     value = dofs / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, dofs=WORKLOAD["Nt"] * dofs, parallelism="cpu oracle, 1 thread"),
+            "config": dict(w, dofs=w["Nt"] * dofs, parallelism="cpu oracle, 1 thread"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: Newton (GMRES slab solves) on slab 1 of "
-                                       f"{WORKLOAD['Nt']} ({dofs} dofs)"},
+                             "sample": f"each step: Newton (GMRES / sparse-LU slab solves) on slab 1 of "
+                                       f"{w['Nt']} ({dofs} dofs)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -372,6 +433,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="logistic2d_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="warm-up and timed steps only (profiling)")

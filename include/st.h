@@ -219,6 +219,11 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT,
                               double* dnu, double* drho, double* du0,
                               st_solve_info* info);
 
+/* Copy the adjoint state lambda of the last st_adjoint_solve* call (layout
+ * of U, Nt*M*Ns doubles, host or device) into out.  ST_ERR_INVALID_ARG if no
+ * adjoint solve has run on this handle. */
+int st_adjoint_lambda(st_handle* h, double* out);
+
 const char* st_status_str(int status);
 
 /* Text of the last CUDA error seen by this thread ("" if none). */

@@ -262,6 +262,7 @@ struct st_handle {
   double* scal = nullptr;   // device scalars
   double* hscal = nullptr;  // pinned host scalars
   double* Ustage = nullptr;
+  double* Rstage = nullptr;  // FP64 residual staging for host output on an FP32 handle
   double* lam = nullptr;
   double* plane = nullptr;  // staging for one plane (gT / target / du0)
   double* plane2 = nullptr;
@@ -1186,10 +1187,10 @@ int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* n
   const bool host_R = R && !is_device_ptr(R);
   if (host_R) Rd = h->L[0].r;  // device staging (may need a double-size buffer)
   if (host_R && r64 && !h->fp64) {
-    // FP64 output for an FP32 handle on the host: use the y/z pair of level 0
-    // only if large enough; otherwise stage through Ustage-sized buffer
-    if (!h->lam) TRY(alloc_typed(h, &h->lam, h->D_total * sizeof(double)));
-    Rd = h->lam;
+    // FP64 output for an FP32 handle on the host: level 0's residual buffer
+    // holds floats, so stage through a buffer of its own
+    if (!h->Rstage) TRY(alloc_typed(h, &h->Rstage, h->D_total * sizeof(double)));
+    Rd = h->Rstage;
   }
   TRY(fine_residual(h, Ud, Rd, r64, false, 0));
   if (host_R)
@@ -1343,6 +1344,13 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, d
   }
   fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
   return status;
+}
+
+int st_adjoint_lambda(st_handle* h, double* out) {
+  if (!h || !out || !h->lam) return ST_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(out, h->lam, h->D_total * sizeof(double), cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ST_OK;
 }
 
 int st_adjoint_solve(st_handle* h, const double* U, const double* u_target, double* dnu, double* drho,

@@ -95,6 +95,7 @@ _SIGS = {
                                  c_void_p, POINTER(StSolveInfo)]),
     "st_adjoint_solve_terminal": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double),
                                           POINTER(c_double), c_void_p, POINTER(StSolveInfo)]),
+    "st_adjoint_lambda": (c_int, [c_void_p, c_void_p]),
     "st_status_str": (ctypes.c_char_p, [c_int]),
     "st_last_error": (ctypes.c_char_p, []),
     "st_collocation": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -355,6 +356,11 @@ class Solver:
         check(lib().st_stats(self.h, ctypes.byref(st)), "st_stats")
         return dict(levels=st.levels, cycle_graph_nodes=st.cycle_graph_nodes,
                     linearize_graph_nodes=st.linearize_graph_nodes, launches_per_vcycle=st.launches_per_vcycle)
+
+    def adjoint_lambda(self, out=None):
+        out = self.zeros() if out is None else out
+        check(lib().st_adjoint_lambda(self.h, self._ptr(out)), "st_adjoint_lambda")
+        return out
 
     # level diagnostics ----------------------------------------------------
     def num_levels(self):

@@ -82,6 +82,11 @@ def test_adjoint_terminal_gradient_and_host_pointers():
     rnu, rrho, rdu0 = oadj.gradients(p, U.cpu().numpy().reshape(p.Nt, p.M, -1), lam)
     assert abs(dnu - rnu) <= 1e-8 * abs(rnu)
     assert np.linalg.norm(du0.numpy() - rdu0) <= 1e-8 * np.linalg.norm(rdu0)
+    # the adjoint state itself, read back to host memory, after a host FP64
+    # residual (which must not disturb it)
+    S.residual(U.cpu(), torch.empty(U.shape, dtype=torch.float64), fp64=True)
+    lam_h = S.adjoint_lambda(torch.empty(U.shape, dtype=torch.float64))
+    assert np.linalg.norm(lam_h.numpy().reshape(lam.shape) - lam) <= 1e-8 * np.linalg.norm(lam)
     S.close()
 
 
