@@ -109,6 +109,26 @@ typedef struct {
   int newton;           /* 1: relinearise (cbar from the current U) every
                            iteration; 0: keep the first linearisation */
   int use_graphs;       /* 1 (default): replay the cycle as a CUDA graph */
+  int use_pdl;          /* 1 (default): programmatic dependent launch, so each
+                           kernel is scheduled while its predecessor drains */
+  int smooth_inner_levels; /* depth of the spatial multigrid inside the
+                           block-Jacobi smoother's slab solves: 1 (default) =
+                           Jacobi sweeps on the level's own grid, 0 = the full
+                           hierarchy (coarsened until non-stiff).  SDC node
+                           solves always use the full hierarchy. */
+  int smooth_sweeps;    /* Jacobi sweeps of a depth-capped smoother slab solve
+                           (>= 2, default 2; the first is the zero-start one) */
+  int line_search;      /* 1 (default): st_solve halves the step of a Newton
+                           iteration (reaction != NONE) until ||G|| decreases
+                           by the factor 1 - 1e-4 * step; DIVERGED below 2^-20 */
+  int exact_jacobian;   /* 1: the finest level's linear operator uses R'(U) at
+                           every node (the exact Jacobian of G; one more array
+                           of the size of U), so a cycle that reduces the
+                           linear residual gives a descent direction for
+                           ||G||; the smoother and coarser levels keep the
+                           node average.  0 (default): node average
+                           everywhere (quasi-Newton; same rate per cycle on
+                           the bench workloads, about 2.5 % less traffic). */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must

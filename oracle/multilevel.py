@@ -38,6 +38,9 @@ class Level:
     nu: float
     X: float
     cbar: np.ndarray  # (Nt, Ns)
+    # optional R'(U) at every node, (Nt, M, Ns): the finest level's operator
+    # is then the exact Jacobian, A e - C e = -dG/dU e; slab solves keep cbar
+    cnode: np.ndarray | None = None
 
     @property
     def Ns(self):
@@ -57,9 +60,11 @@ def _apply_L(L, E):
 
 
 def apply_A(lev: Level, e: np.ndarray) -> np.ndarray:
-    """A_l e (block diagonal part, no slab coupling)."""
+    """A_l e (block diagonal part, no slab coupling); with cnode the reaction
+    term of node j is R'(U_{n,j}) e_j instead of cbar_n e_j."""
     e = e.reshape(lev.Nt, lev.M, lev.Ns)
-    Fe = _apply_L(lev.L, e) + lev.cbar[:, None, :] * e
+    c = lev.cbar[:, None, :] if lev.cnode is None else lev.cnode.reshape(e.shape)
+    Fe = _apply_L(lev.L, e) + c * e
     return e - lev.dt * np.einsum("mj,njs->nms", lev.Q, Fe)
 
 
@@ -136,6 +141,38 @@ def smoothing_step_exact(lev: Level, e: np.ndarray, r: np.ndarray, omega: float)
     out = e.reshape(res.shape).copy()
     for n in range(lev.Nt):
         out[n] += omega * spla.spsolve(slab_matrix(lev, n), res[n].ravel()).reshape(lev.M, lev.Ns)
+    return out
+
+
+def smoothing_step_jacobi(lev: Level, e: np.ndarray, r: np.ndarray, omega: float, sweeps: int,
+                          omega_j: float) -> np.ndarray:
+    """Damped block Jacobi in time whose slab solves are replaced by ``sweeps``
+    weighted-Jacobi sweeps (weight omega_j, zero start) on the M systems that
+    the eigen-decomposition Q = V diag(lambda) V^{-1} decouples:
+
+        (I - dt lambda_q (L + diag cbar_n)) z_q = (V^{-1} res_n)_q,
+
+    then e_n += omega * Re(V z).  Complex arithmetic throughout.
+    Parity unpinned: the sweep count and weights are solver parameters.  It
+    tends to ``smoothing_step_exact`` as sweeps grows, and equals it after one
+    sweep with omega_j = 1 when L + diag cbar vanishes."""
+    res = linear_residual(lev, e, r)
+    lam, V = np.linalg.eig(lev.Q)
+    Vinv = np.linalg.inv(V)
+    out = e.reshape(res.shape).copy()
+    Ldiag = lev.L.diagonal()
+    I = sp.identity(lev.Ns, format="csr")
+    for n in range(lev.Nt):
+        Ln = (lev.L + sp.diags(lev.cbar[n])).tocsr()
+        Y = Vinv @ res[n]
+        Z = np.zeros_like(Y, dtype=complex)
+        for q in range(lev.M):
+            s = lev.dt * lam[q]
+            Aq = I - s * Ln
+            d = 1.0 - s * (Ldiag + lev.cbar[n])
+            for _ in range(sweeps):
+                Z[q] = Z[q] + omega_j * (Y[q] - Aq @ Z[q]) / d
+        out[n] += omega * (V @ Z).real
     return out
 
 

@@ -18,6 +18,7 @@ namespace st {
 // the inverse and the coupling matrices.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_setup(CoarseParams<T> p) {
+  grid_dep_wait();
   extern __shared__ unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);  // [K][2K]
   const int K = p.K, Nc = p.Nc, M = p.M;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(256) k_coarse_setup(CoarseParams<T> p) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_apply(CoarseParams<T> p, int transpose, const T* __restrict__ r,
                                                       T* __restrict__ e) {
+  grid_dep_wait();
   const int n = blockIdx.x, K = p.K;
   const T* Ai = p.Ainv + (long long)n * K * K;
   const T* rn = r + (long long)n * K;
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply(CoarseParams<T> p, int tra
 template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_recur(CoarseParams<T> p, int transpose, const T* __restrict__ f,
                                                       T* __restrict__ in) {
+  grid_dep_wait();
   const int K = p.K, Nc = p.Nc, M = p.M, Nt = p.Nt;
   const int q = threadIdx.x;
   if (!transpose) {
@@ -171,6 +174,7 @@ __global__ void __launch_bounds__(128) k_coarse_recur(CoarseParams<T> p, int tra
 template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_finish(CoarseParams<T> p, int transpose, const T* __restrict__ in,
                                                        T* __restrict__ e) {
+  grid_dep_wait();
   const int n = blockIdx.x, K = p.K, Nc = p.Nc;
   const T* W = (transpose ? p.Wt : p.Wf) + (long long)n * K * Nc;
   const T* v = in + (long long)n * Nc;
@@ -194,14 +198,14 @@ cudaError_t prepare_coarse_setup(const CoarseParams<T>& p) {
 
 template <typename T>
 void launch_coarse_setup(const CoarseParams<T>& p, cudaStream_t st) {
-  k_coarse_setup<T><<<p.Nt, 256, coarse_setup_smem(p), st>>>(p);
+  st_launch(k_coarse_setup<T>, p.Nt, 256, coarse_setup_smem(p), st, p);
 }
 
 template <typename T>
 void launch_coarse_solve(const CoarseParams<T>& p, int transpose, const T* r, T* e, T* in, cudaStream_t st) {
-  k_coarse_apply<T><<<p.Nt, 128, 0, st>>>(p, transpose, r, e);
-  k_coarse_recur<T><<<1, 128, 0, st>>>(p, transpose, e, in);
-  k_coarse_finish<T><<<p.Nt, 128, 0, st>>>(p, transpose, in, e);
+  st_launch(k_coarse_apply<T>, p.Nt, 128, 0, st, p, transpose, r, e);
+  st_launch(k_coarse_recur<T>, 1, 128, 0, st, p, transpose, e, in);
+  st_launch(k_coarse_finish<T>, p.Nt, 128, 0, st, p, transpose, in, e);
 }
 
 #define INSTC(T)                                                                       \

@@ -19,6 +19,7 @@ long long residual_blocks4(const ResidParams& p);
 // ---------------------------------------------------------------------------
 template <int D, typename TR, typename TC>
 __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   double sq = 0.0;
   if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
@@ -32,6 +33,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
     double prev = (n0 == 0) ? p.u0[s] : p.U[((long long)(n0 - 1) * M + (M - 1)) * Ns + s];
     TR* R = (TR*)p.R;
     TC* cb = (TC*)p.cbar;
+    TC* cn = (TC*)p.cnode;
     const double invM = 1.0 / M;
     for (int n = n0; n < n1; ++n) {
       const long long base = (long long)n * M * Ns + s;
@@ -46,7 +48,11 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
           if (m == M - 1) ulast = um;
           F[m] = lap_nb<D, double, double>(pl, s, nb, um, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2,
                                             react<double>(p.reaction, p.rho, um));
-          if (cb) cbs += dreact<double>(p.reaction, p.rho, um);
+          if (cb || cn) {
+            const double dr = dreact<double>(p.reaction, p.rho, um);
+            cbs += dr;
+            if (cn) cn[base + (long long)m * Ns] = (TC)dr;
+          }
         }
       }
 #pragma unroll
@@ -152,6 +158,7 @@ __device__ __forceinline__ ff nb_ff(const double* __restrict__ p, long long s, l
 
 template <int D>
 __global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   float sq = 0.0f;
   if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
@@ -165,6 +172,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
     ff prev = split_double((n0 == 0) ? p.u0[s] : p.U[((long long)(n0 - 1) * M + (M - 1)) * Ns + s]);
     float* R = (float*)p.R;
     float* cb = (float*)p.cbar;
+    float* cn = (float*)p.cnode;
     const float invM = 1.0f / M;
     for (int n = n0; n < n1; ++n) {
       const long long base = (long long)n * M * Ns + s;
@@ -195,13 +203,17 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
             // rho u (1 - u) = u * (rho - rho u)
             const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul_c(um, c.rho.hi, c.rho.lo)));
             acc = ff_add(acc, ff_mul(um, t));
-            if (cb) cbs += fmaf(-2.0f * c.rho32, um.hi, c.rho32);
+            const float dr = fmaf(-2.0f * c.rho32, um.hi, c.rho32);
+            cbs += dr;
+            if (cn) cn[base + (long long)m * Ns] = dr;
           } else if (p.reaction == ST_REACTION_CUBIC) {
             // rho u (1 - u^2) = u * (rho - rho u u)
             const ff ru = ff_mul_c(um, c.rho.hi, c.rho.lo);
             const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul(ru, um)));
             acc = ff_add(acc, ff_mul(um, t));
-            if (cb) cbs += fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
+            const float dr = fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
+            cbs += dr;
+            if (cn) cn[base + (long long)m * Ns] = dr;
           }
           F[m] = acc;
         }
@@ -233,6 +245,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(ResidParams p, ResidFF c) {
 // value is split once for the 4 points.
 template <int D, int M>
 __global__ void __launch_bounds__(256) k_residual_ff4(ResidParams p, ResidFF c, FastDiv fG) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   float sq = 0.0f;
   const unsigned G = (unsigned)(p.g.Ns >> 2);
@@ -256,6 +269,7 @@ __global__ void __launch_bounds__(256) k_residual_ff4(ResidParams p, ResidFF c, 
     }
     float* R = (float*)p.R;
     float* cb = (float*)p.cbar;
+    float* cn = (float*)p.cnode;
     for (int n = n0; n < n1; ++n) {
       const long long base = (long long)n * M * Ns + s0;
       ff u[M][4], F[M][4];
@@ -288,21 +302,24 @@ __global__ void __launch_bounds__(256) k_residual_ff4(ResidParams p, ResidFF c, 
           for (int q = 0; q < 4; ++q)
             acc[q] = ff_madd_c(acc[q], ff_add(split_double(lv[q]), split_double(hv[q])), cc.hi, cc.lo);
         }
+        float dr[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const ff um = u[m][q];
           if (p.reaction == ST_REACTION_LOGISTIC) {
             const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul_c(um, c.rho.hi, c.rho.lo)));
             acc[q] = ff_add(acc[q], ff_mul(um, t));
-            cbs[q] += fmaf(-2.0f * c.rho32, um.hi, c.rho32);
+            dr[q] = fmaf(-2.0f * c.rho32, um.hi, c.rho32);
           } else if (p.reaction == ST_REACTION_CUBIC) {
             const ff ru = ff_mul_c(um, c.rho.hi, c.rho.lo);
             const ff t = ff_add({c.rho.hi, c.rho.lo}, ff_neg(ff_mul(ru, um)));
             acc[q] = ff_add(acc[q], ff_mul(um, t));
-            cbs[q] += fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
+            dr[q] = fmaf(-3.0f * c.rho32 * um.hi, um.hi, c.rho32);
           }
+          cbs[q] += dr[q];
           F[m][q] = acc[q];
         }
+        if (cn) *reinterpret_cast<float4*>(cn + base + (long long)m * Ns) = make_float4(dr[0], dr[1], dr[2], dr[3]);
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) {
@@ -360,16 +377,16 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
   if (ff4_ok(D, p)) {
     const FastDiv fG((unsigned)(p.g.Ns >> 2));
     const unsigned nb4 = (unsigned)residual_blocks4(p);
-    if (D == 2 && p.M == 3) k_residual_ff4<2, 3><<<nb4, 256, 0, st>>>(p, c, fG);
-    else if (D == 2) k_residual_ff4<2, 5><<<nb4, 256, 0, st>>>(p, c, fG);
-    else if (p.M == 3) k_residual_ff4<3, 3><<<nb4, 256, 0, st>>>(p, c, fG);
-    else k_residual_ff4<3, 5><<<nb4, 256, 0, st>>>(p, c, fG);
+    if (D == 2 && p.M == 3) st_launch(k_residual_ff4<2, 3>, nb4, 256, 0, st, p, c, fG);
+    else if (D == 2) st_launch(k_residual_ff4<2, 5>, nb4, 256, 0, st, p, c, fG);
+    else if (p.M == 3) st_launch(k_residual_ff4<3, 3>, nb4, 256, 0, st, p, c, fG);
+    else st_launch(k_residual_ff4<3, 5>, nb4, 256, 0, st, p, c, fG);
     return;
   }
   const unsigned nb = (unsigned)residual_blocks(p);
-  if (D == 1) k_residual_ff<1><<<nb, 256, 0, st>>>(p, c);
-  else if (D == 2) k_residual_ff<2><<<nb, 256, 0, st>>>(p, c);
-  else k_residual_ff<3><<<nb, 256, 0, st>>>(p, c);
+  if (D == 1) st_launch(k_residual_ff<1>, nb, 256, 0, st, p, c);
+  else if (D == 2) st_launch(k_residual_ff<2>, nb, 256, 0, st, p, c);
+  else st_launch(k_residual_ff<3>, nb, 256, 0, st, p, c);
 }
 
 // blocks of the 4-point double-float residual (one partial sum per block)
@@ -384,6 +401,7 @@ long long residual_blocks4(const ResidParams& p) { return ((p.g.Ns >> 2) * p.nch
 // ---------------------------------------------------------------------------
 template <int D, typename TR>
 __global__ void __launch_bounds__(256) k_adj_residual(ResidParams p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   double sq = 0.0;
   if (idx < (unsigned)p.nchunks * (unsigned)p.g.Ns) {
@@ -451,6 +469,7 @@ __global__ void __launch_bounds__(256) k_adj_residual(ResidParams p) {
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256) k_gradients(ResidParams p, double* partial2, double* du0) {
+  grid_dep_wait();
   const long long Ns = p.g.Ns;
   const int M = p.M;
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -491,6 +510,7 @@ __global__ void __launch_bounds__(256) k_gradients(ResidParams p, double* partia
 // Sum n partials in a fixed order into out[0] (single block of 1024).
 __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ part, long long n,
                                                        double* out) {
+  grid_dep_wait();
   double v = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
   v = block_sum(v);
@@ -499,10 +519,37 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict_
 
 // U += e (e in the cycle precision), optionally scaled.
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(double* __restrict__ U, const T* __restrict__ e,
-                                                long long n) {
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ U, const T* __restrict__ e, long long n,
+                                                double alpha) {
+  grid_dep_wait();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) U[i] += (double)e[i];
+  if (i < n) U[i] += alpha * (double)e[i];
+}
+
+// Four values per thread; U and e 16-byte aligned (checked by the launcher).
+template <typename T>
+__global__ void __launch_bounds__(256) k_update4(double* __restrict__ U, const T* __restrict__ e, long long n,
+                                                 double alpha) {
+  grid_dep_wait();
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i + 4 <= n) {
+    double2 a = *reinterpret_cast<const double2*>(U + i);
+    double2 b = *reinterpret_cast<const double2*>(U + i + 2);
+    double e0, e1, e2, e3;
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(e + i);
+      e0 = v.x; e1 = v.y; e2 = v.z; e3 = v.w;
+    } else {
+      const double2 v0 = *reinterpret_cast<const double2*>(e + i);
+      const double2 v1 = *reinterpret_cast<const double2*>(e + i + 2);
+      e0 = v0.x; e1 = v0.y; e2 = v1.x; e3 = v1.y;
+    }
+    a.x += alpha * e0; a.y += alpha * e1; b.x += alpha * e2; b.y += alpha * e3;
+    *reinterpret_cast<double2*>(U + i) = a;
+    *reinterpret_cast<double2*>(U + i + 2) = b;
+  } else {
+    for (long long q = i; q < n; ++q) U[q] += alpha * (double)e[q];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -515,6 +562,7 @@ __global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, 
                                                  double rho, SdcCoef cf,
                                                  const T* __restrict__ G, const T* __restrict__ delta,
                                                  const double* __restrict__ U, T* __restrict__ y) {
+  grid_dep_wait();
   const long long Ns = g.Ns;
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)Nt * (unsigned)g.Ns) return;
@@ -538,6 +586,7 @@ __global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter_plane(const T* __restrict__ src, T* __restrict__ dst,
                                                        long long Ns, int Nt, int M, int m) {
+  grid_dep_wait();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Ns * Nt) return;
   const long long s = idx % Ns;
@@ -555,9 +604,9 @@ long long residual_blocks(const ResidParams& p) { return (p.g.Ns * p.nchunks + 2
 template <typename TR, typename TC>
 static void launch_res_t(int D, const ResidParams& p, cudaStream_t st) {
   const unsigned nb = (unsigned)residual_blocks(p);
-  if (D == 1) k_residual<1, TR, TC><<<nb, 256, 0, st>>>(p);
-  else if (D == 2) k_residual<2, TR, TC><<<nb, 256, 0, st>>>(p);
-  else k_residual<3, TR, TC><<<nb, 256, 0, st>>>(p);
+  if (D == 1) st_launch(k_residual<1, TR, TC>, nb, 256, 0, st, p);
+  else if (D == 2) st_launch(k_residual<2, TR, TC>, nb, 256, 0, st, p);
+  else st_launch(k_residual<3, TR, TC>, nb, 256, 0, st, p);
 }
 
 void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st) {
@@ -569,13 +618,13 @@ void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaSt
 void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st) {
   const unsigned nb = (unsigned)residual_blocks(p);
   if (r_fp64) {
-    if (D == 1) k_adj_residual<1, double><<<nb, 256, 0, st>>>(p);
-    else if (D == 2) k_adj_residual<2, double><<<nb, 256, 0, st>>>(p);
-    else k_adj_residual<3, double><<<nb, 256, 0, st>>>(p);
+    if (D == 1) st_launch(k_adj_residual<1, double>, nb, 256, 0, st, p);
+    else if (D == 2) st_launch(k_adj_residual<2, double>, nb, 256, 0, st, p);
+    else st_launch(k_adj_residual<3, double>, nb, 256, 0, st, p);
   } else {
-    if (D == 1) k_adj_residual<1, float><<<nb, 256, 0, st>>>(p);
-    else if (D == 2) k_adj_residual<2, float><<<nb, 256, 0, st>>>(p);
-    else k_adj_residual<3, float><<<nb, 256, 0, st>>>(p);
+    if (D == 1) st_launch(k_adj_residual<1, float>, nb, 256, 0, st, p);
+    else if (D == 2) st_launch(k_adj_residual<2, float>, nb, 256, 0, st, p);
+    else st_launch(k_adj_residual<3, float>, nb, 256, 0, st, p);
   }
 }
 
@@ -583,18 +632,24 @@ long long gradient_blocks(const ResidParams& p) { return (p.g.Ns * p.Nt + 255) /
 
 void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st) {
   const unsigned nb = (unsigned)gradient_blocks(p);
-  if (D == 1) k_gradients<1><<<nb, 256, 0, st>>>(p, partial2, du0);
-  else if (D == 2) k_gradients<2><<<nb, 256, 0, st>>>(p, partial2, du0);
-  else k_gradients<3><<<nb, 256, 0, st>>>(p, partial2, du0);
+  if (D == 1) st_launch(k_gradients<1>, nb, 256, 0, st, p, partial2, du0);
+  else if (D == 2) st_launch(k_gradients<2>, nb, 256, 0, st, p, partial2, du0);
+  else st_launch(k_gradients<3>, nb, 256, 0, st, p, partial2, du0);
 }
 
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st) {
-  k_sum_partials<<<1, 1024, 0, st>>>(part, n, out);
+  st_launch(k_sum_partials, 1, 1024, 0, st, part, n, out);
 }
 
-void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st) {
-  if (fp64) k_update<double><<<blocks_for(n, 256), 256, 0, st>>>(U, (const double*)e, n);
-  else k_update<float><<<blocks_for(n, 256), 256, 0, st>>>(U, (const float*)e, n);
+void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha) {
+  if (((uintptr_t)U & 15) == 0 && ((uintptr_t)e & 15) == 0) {
+    const unsigned nb = blocks_for((n + 3) / 4, 256);
+    if (fp64) st_launch(k_update4<double>, nb, 256, 0, st, U, (const double*)e, n, alpha);
+    else st_launch(k_update4<float>, nb, 256, 0, st, U, (const float*)e, n, alpha);
+    return;
+  }
+  if (fp64) st_launch(k_update<double>, blocks_for(n, 256), 256, 0, st, U, (const double*)e, n, alpha);
+  else st_launch(k_update<float>, blocks_for(n, 256), 256, 0, st, U, (const float*)e, n, alpha);
 }
 
 void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,
@@ -602,7 +657,7 @@ void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, doubl
                     const double* U, void* y, cudaStream_t st) {
   const unsigned nb = blocks_for(g.Ns * Nt, 256);
 #define SDC_L(DD, TT)                                                                              \
-  k_sdc_rhs<DD, TT><<<nb, 256, 0, st>>>(g, Nt, M, m, nu, reaction, rho, cf, (const TT*)G,     \
+  st_launch(k_sdc_rhs<DD, TT>, nb, 256, 0, st, g, Nt, M, m, nu, reaction, rho, cf, (const TT*)G,     \
                                         (const TT*)delta, U, (TT*)y)
   if (fp64) {
     if (D == 1) SDC_L(1, double); else if (D == 2) SDC_L(2, double); else SDC_L(3, double);
@@ -615,8 +670,8 @@ void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, doubl
 void launch_scatter_plane(int fp64, const void* src, void* dst, long long Ns, int Nt, int M, int m,
                           cudaStream_t st) {
   const unsigned nb = blocks_for(Ns * Nt, 256);
-  if (fp64) k_scatter_plane<double><<<nb, 256, 0, st>>>((const double*)src, (double*)dst, Ns, Nt, M, m);
-  else k_scatter_plane<float><<<nb, 256, 0, st>>>((const float*)src, (float*)dst, Ns, Nt, M, m);
+  if (fp64) st_launch(k_scatter_plane<double>, nb, 256, 0, st, (const double*)src, (double*)dst, Ns, Nt, M, m);
+  else st_launch(k_scatter_plane<float>, nb, 256, 0, st, (const float*)src, (float*)dst, Ns, Nt, M, m);
 }
 
 }  // namespace st

@@ -39,6 +39,7 @@ __device__ __forceinline__ void zero_jacobi(T yr, T yi, int cplx, T sr, T si, T 
 // ---------------------------------------------------------------------------
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.nchunks * (unsigned)p.g.Ns) return;
   int c, s, i, j, k;
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
           const T* pl = p.e + (long long)n * M * Ns + (long long)b * Ns;
           const T eb = pl[s];
           ev[b] = eb;
-          Fe[b] = lap_nb<D, T, T>(pl, s, nb, eb, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * eb);
+          const T cr = p.cnode ? p.cnode[base + (long long)b * Ns] : cb;
+          Fe[b] = lap_nb<D, T, T>(pl, s, nb, eb, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cr * eb);
           sum += eb;
           if (b == M - 1) last = eb;
         }
@@ -142,6 +144,7 @@ struct BackParams {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_backtransform(BackParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
   const int n = (int)p.g.fNs.div(idx);
@@ -228,6 +231,7 @@ __device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_inner_jacobi(InnerParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
   int n, s, i, j, k;
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(256) k_inner_jacobi(InnerParams<T> p) {
 // Zero-start Jacobi z = omega D^{-1} y (pointwise).
 template <typename T>
 __global__ void __launch_bounds__(256) k_inner_jacobi_zero(InnerParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
   const int n = (int)p.g.fNs.div(idx);
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(256) k_inner_jacobi_zero(InnerParams<T> p) {
 // into zout.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_shifted_residual(InnerParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)p.g.Ns) return;
   int n, s, i, j, k;
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(256) k_shifted_residual(InnerParams<T> p) {
 // zc = omega Dc^{-1} yc.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_inner_restrict(InnerParams<T> p) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)p.gc.Ns) return;
   int n, sc, I, J, K;
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(256) k_inner_restrict(InnerParams<T> p) {
 // applies the back-transform update instead of storing z.
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_inner_coarse(InnerParams<T> p) {
+  grid_dep_wait();
   extern __shared__ unsigned char smem_raw[];
   T* sz = reinterpret_cast<T*>(smem_raw);      // [P][Ns]
   T* sz2 = sz + (long long)p.P * p.g.Ns;      // [P][Ns]
@@ -392,6 +400,7 @@ __global__ void __launch_bounds__(256) k_inner_coarse(InnerParams<T> p) {
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_restrict_space(GridP gf, GridP gc, int planes,
                                                         const T* __restrict__ fine, T* __restrict__ coarse) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)planes * (unsigned)gc.Ns) return;
   int pl, sc, I, J, K;
@@ -420,6 +429,7 @@ __global__ void __launch_bounds__(256) k_restrict_space(GridP gf, GridP gc, int 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_prolong_space_add(GridP gf, GridP gc, int planes,
                                                            const T* __restrict__ coarse, T* __restrict__ fine) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)planes * (unsigned)gf.Ns) return;
   int pl, s, i, j, k;
@@ -458,6 +468,7 @@ struct TimeXfer {
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_time(GridP g, int Ntc, int M, TimeXfer<T> X,
                                                        const T* __restrict__ fine, T* __restrict__ coarse) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
   const int N = (int)g.fNs.div(idx);
@@ -475,6 +486,7 @@ __global__ void __launch_bounds__(256) k_restrict_time(GridP g, int Ntc, int M, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_time_add(GridP g, int Ntc, int M, TimeXfer<T> X,
                                                           const T* __restrict__ coarse, T* __restrict__ fine) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
   const int N = (int)g.fNs.div(idx);
@@ -493,6 +505,7 @@ __global__ void __launch_bounds__(256) k_prolong_time_add(GridP g, int Ntc, int 
 template <typename T>
 __global__ void __launch_bounds__(256) k_cbar_time(GridP g, int Ntc, const T* __restrict__ fine,
                                                    T* __restrict__ coarse) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)Ntc * (unsigned)g.Ns) return;
   const int N = (int)g.fNs.div(idx);
@@ -515,7 +528,7 @@ void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value)
     if (launch_lin_residual4(D, p, st)) return;
   const unsigned nb = nblk((long long)p.g.Ns * p.nchunks, 256);
-  DISPATCH_D(D, (k_lin_residual<DD, T><<<nb, 256, 0, st>>>(p)));
+  DISPATCH_D(D, (st_launch(k_lin_residual<DD, T>, nb, 256, 0, st, p)));
 }
 
 template <typename T>
@@ -525,7 +538,7 @@ void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], 
   p.g = g; p.Nt = Nt; p.M = M; p.e_zero = e_zero; p.omega = omega; p.z = z; p.e = e;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) p.B[a][b] = B[a][b];
-  k_backtransform<T><<<nblk(g.Ns * Nt, 256), 256, 0, st>>>(p);
+  st_launch(k_backtransform<T>, nblk(g.Ns * Nt, 256), 256, 0, st, p);
 }
 
 template <typename T>
@@ -533,8 +546,8 @@ void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t 
   if constexpr (std::is_same<T, float>::value)
     if (!zero && launch_inner4(D, 1, p, st)) return;
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
-  if (zero) k_inner_jacobi_zero<T><<<nb, 256, 0, st>>>(p);
-  else DISPATCH_D(D, (k_inner_jacobi<DD, T><<<nb, 256, 0, st>>>(p)));
+  if (zero) st_launch(k_inner_jacobi_zero<T>, nb, 256, 0, st, p);
+  else DISPATCH_D(D, (st_launch(k_inner_jacobi<DD, T>, nb, 256, 0, st, p)));
 }
 
 template <typename T>
@@ -542,7 +555,7 @@ void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value)
     if (launch_inner_restrict4(D, p, st)) return;
   const unsigned nb = nblk(p.gc.Ns * p.Nt, 256);
-  DISPATCH_D(D, (k_inner_restrict<DD, T><<<nb, 256, 0, st>>>(p)));
+  DISPATCH_D(D, (st_launch(k_inner_restrict<DD, T>, nb, 256, 0, st, p)));
 }
 
 template <typename T>
@@ -550,7 +563,7 @@ void launch_shifted_residual(int D, const InnerParams<T>& p, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value)
     if (launch_inner4(D, 0, p, st)) return;
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
-  DISPATCH_D(D, (k_shifted_residual<DD, T><<<nb, 256, 0, st>>>(p)));
+  DISPATCH_D(D, (st_launch(k_shifted_residual<DD, T>, nb, 256, 0, st, p)));
 }
 
 template <typename T>
@@ -563,7 +576,7 @@ void launch_inner_coarse(int D, const InnerParams<T>& p, cudaStream_t st) {
   const size_t sm = inner_coarse_smem(p);
   int bs = (int)((p.g.Ns + 31) / 32 * 32);
   if (bs > 256) bs = 256;
-  DISPATCH_D(D, (k_inner_coarse<DD, T><<<p.Nt, bs, sm, st>>>(p)));
+  DISPATCH_D(D, (st_launch(k_inner_coarse<DD, T>, p.Nt, bs, sm, st, p)));
 }
 
 template <typename T>
@@ -572,7 +585,7 @@ void launch_restrict_space(int D, const GridP& gf, const GridP& gc, long long pl
   if constexpr (std::is_same<T, float>::value)
     if (launch_restrict4(D, gf, gc, planes, f, c, st)) return;
   const unsigned nb = nblk(gc.Ns * planes, 256);
-  DISPATCH_D(D, (k_restrict_space<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, f, c)));
+  DISPATCH_D(D, (st_launch(k_restrict_space<DD, T>, nb, 256, 0, st, gf, gc, (int)planes, f, c)));
 }
 
 template <typename T>
@@ -581,7 +594,7 @@ void launch_prolong_space_add(int D, const GridP& gf, const GridP& gc, long long
   if constexpr (std::is_same<T, float>::value)
     if (launch_prolong4(D, gf, gc, planes, c, f, st)) return;
   const unsigned nb = nblk(gf.Ns * planes, 256);
-  DISPATCH_D(D, (k_prolong_space_add<DD, T><<<nb, 256, 0, st>>>(gf, gc, (int)planes, c, f)));
+  DISPATCH_D(D, (st_launch(k_prolong_space_add<DD, T>, nb, 256, 0, st, gf, gc, (int)planes, c, f)));
 }
 
 template <typename T>
@@ -590,7 +603,7 @@ void launch_restrict_time(const GridP& g, int Ntc, int M, const double R[MAXM][2
   TimeXfer<T> X;
   for (int m = 0; m < MAXM; ++m)
     for (int kk = 0; kk < 2 * MAXM; ++kk) X.A[m][kk] = (T)R[m][kk];
-  k_restrict_time<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, M, X, f, c);
+  st_launch(k_restrict_time<T>, nblk(g.Ns * Ntc, 256), 256, 0, st, g, Ntc, M, X, f, c);
 }
 
 template <typename T>
@@ -599,12 +612,12 @@ void launch_prolong_time_add(const GridP& g, int Ntc, int M, const double P[2 * 
   TimeXfer<T> X;
   for (int kk = 0; kk < 2 * MAXM; ++kk)
     for (int m = 0; m < MAXM; ++m) X.B[kk][m] = (T)P[kk][m];
-  k_prolong_time_add<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, M, X, c, f);
+  st_launch(k_prolong_time_add<T>, nblk(g.Ns * Ntc, 256), 256, 0, st, g, Ntc, M, X, c, f);
 }
 
 template <typename T>
 void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st) {
-  k_cbar_time<T><<<nblk(g.Ns * Ntc, 256), 256, 0, st>>>(g, Ntc, f, c);
+  st_launch(k_cbar_time<T>, nblk(g.Ns * Ntc, 256), 256, 0, st, g, Ntc, f, c);
 }
 
 #define INST(T)                                                                                     \

@@ -93,6 +93,7 @@ __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float
 // ---------------------------------------------------------------------------
 template <int D, int M>
 __global__ void __launch_bounds__(256) k_lin_residual4(LinParams<float> p, FastDiv fG) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.nchunks * (unsigned)(p.g.Ns >> 2)) return;
   int c, s0, i0, j, k;
@@ -129,9 +130,11 @@ __global__ void __launch_bounds__(256) k_lin_residual4(LinParams<float> p, FastD
       for (int b = 0; b < M; ++b) {
         const float* pl = p.e + base + (long long)b * Ns - s0;
         to4(ld4(pl + s0), ev[b]);
+        float cr[4] = {cb[0], cb[1], cb[2], cb[3]};
+        if (p.cnode) to4(ld4(p.cnode + base + (long long)b * Ns), cr);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          Fe[b][q] = cb[q] * ev[b][q];
+          Fe[b][q] = cr[q] * ev[b][q];
           sum[q] += ev[b][q];
         }
         lap4<D>(pl, s0, nb, ev[b], p.sc, Fe[b]);
@@ -200,6 +203,7 @@ constexpr int inner4_min_blocks() { return (D == 2 && M == 3) ? 4 : 1; }
 
 template <int D, int M, int MODE>
 __global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(InnerParams<float> p, FastDiv fG) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)(p.g.Ns >> 2)) return;
   int n, s0, i0, j, k;
@@ -279,6 +283,7 @@ __global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(Inner
 template <int D>
 __global__ void __launch_bounds__(256) k_prolong4(GridP gf, GridP gc, int planes, FastDiv fG,
                                                   const float* __restrict__ coarse, float* __restrict__ fine) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)planes * (unsigned)(gf.Ns >> 2)) return;
   int pl, s0, i0, j, k;
@@ -355,6 +360,7 @@ __device__ __forceinline__ void restrict4_point(const float* __restrict__ f, con
 template <int D>
 __global__ void __launch_bounds__(256) k_restrict4(GridP gf, GridP gc, int planes, FastDiv fG,
                                                    const float* __restrict__ fine, float* __restrict__ coarse) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)planes * (unsigned)(gc.Ns >> 2)) return;
   int pl, s0, I0, J, K;
@@ -368,6 +374,7 @@ __global__ void __launch_bounds__(256) k_restrict4(GridP gf, GridP gc, int plane
 // with the coarse zero-start Jacobi iterate.
 template <int D, int M>
 __global__ void __launch_bounds__(256) k_inner_restrict4(InnerParams<float> p, FastDiv fG) {
+  grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)(p.gc.Ns >> 2)) return;
   int n, s0, I0, J, K;
@@ -415,10 +422,10 @@ bool launch_lin_residual4(int D, const LinParams<float>& p, cudaStream_t st) {
   if (!vec4_ok(p.g, D, p.M)) return false;
   const FastDiv fG((unsigned)(p.g.Ns >> 2));
   const unsigned nb = nblk4((p.g.Ns >> 2) * p.nchunks);
-  if (D == 2 && p.M == 3) k_lin_residual4<2, 3><<<nb, 256, 0, st>>>(p, fG);
-  else if (D == 2 && p.M == 5) k_lin_residual4<2, 5><<<nb, 256, 0, st>>>(p, fG);
-  else if (D == 3 && p.M == 3) k_lin_residual4<3, 3><<<nb, 256, 0, st>>>(p, fG);
-  else k_lin_residual4<3, 5><<<nb, 256, 0, st>>>(p, fG);
+  if (D == 2 && p.M == 3) st_launch(k_lin_residual4<2, 3>, nb, 256, 0, st, p, fG);
+  else if (D == 2 && p.M == 5) st_launch(k_lin_residual4<2, 5>, nb, 256, 0, st, p, fG);
+  else if (D == 3 && p.M == 3) st_launch(k_lin_residual4<3, 3>, nb, 256, 0, st, p, fG);
+  else st_launch(k_lin_residual4<3, 5>, nb, 256, 0, st, p, fG);
   return true;
 }
 
@@ -428,8 +435,8 @@ bool launch_inner4(int D, int mode, const InnerParams<float>& p, cudaStream_t st
   const unsigned nb = nblk4((p.g.Ns >> 2) * p.Nt);
 #define K4(DD, MM)                                                         \
   do {                                                                     \
-    if (mode == 0) k_inner4<DD, MM, 0><<<nb, 256, 0, st>>>(p, fG);         \
-    else k_inner4<DD, MM, 1><<<nb, 256, 0, st>>>(p, fG);                   \
+    if (mode == 0) st_launch(k_inner4<DD, MM, 0>, nb, 256, 0, st, p, fG);         \
+    else st_launch(k_inner4<DD, MM, 1>, nb, 256, 0, st, p, fG);                   \
   } while (0)
   if (D == 2 && p.P == 3) K4(2, 3);
   else if (D == 2 && p.P == 5) K4(2, 5);
@@ -448,8 +455,8 @@ bool launch_restrict4(int D, const GridP& gf, const GridP& gc, long long planes,
   if (!restrict4_ok(D, gf, gc)) return false;
   const FastDiv fG((unsigned)(gc.Ns >> 2));
   const unsigned nb = nblk4((gc.Ns >> 2) * planes);
-  if (D == 2) k_restrict4<2><<<nb, 256, 0, st>>>(gf, gc, (int)planes, fG, f, c);
-  else k_restrict4<3><<<nb, 256, 0, st>>>(gf, gc, (int)planes, fG, f, c);
+  if (D == 2) st_launch(k_restrict4<2>, nb, 256, 0, st, gf, gc, (int)planes, fG, f, c);
+  else st_launch(k_restrict4<3>, nb, 256, 0, st, gf, gc, (int)planes, fG, f, c);
   return true;
 }
 
@@ -457,10 +464,10 @@ bool launch_inner_restrict4(int D, const InnerParams<float>& p, cudaStream_t st)
   if (!restrict4_ok(D, p.g, p.gc) || !(p.P == 3 || p.P == 5)) return false;
   const FastDiv fG((unsigned)(p.gc.Ns >> 2));
   const unsigned nb = nblk4((p.gc.Ns >> 2) * p.Nt);
-  if (D == 2 && p.P == 3) k_inner_restrict4<2, 3><<<nb, 256, 0, st>>>(p, fG);
-  else if (D == 2) k_inner_restrict4<2, 5><<<nb, 256, 0, st>>>(p, fG);
-  else if (p.P == 3) k_inner_restrict4<3, 3><<<nb, 256, 0, st>>>(p, fG);
-  else k_inner_restrict4<3, 5><<<nb, 256, 0, st>>>(p, fG);
+  if (D == 2 && p.P == 3) st_launch(k_inner_restrict4<2, 3>, nb, 256, 0, st, p, fG);
+  else if (D == 2) st_launch(k_inner_restrict4<2, 5>, nb, 256, 0, st, p, fG);
+  else if (p.P == 3) st_launch(k_inner_restrict4<3, 3>, nb, 256, 0, st, p, fG);
+  else st_launch(k_inner_restrict4<3, 5>, nb, 256, 0, st, p, fG);
   return true;
 }
 
@@ -469,8 +476,8 @@ bool launch_prolong4(int D, const GridP& gf, const GridP& gc, long long planes, 
   if (!(D >= 2 && gf.bc == BC_PER && gf.n0 >= 4 && gf.n0 % 4 == 0 && gc.n0 * 2 == gf.n0)) return false;
   const FastDiv fG((unsigned)(gf.Ns >> 2));
   const unsigned nb = nblk4((gf.Ns >> 2) * planes);
-  if (D == 2) k_prolong4<2><<<nb, 256, 0, st>>>(gf, gc, (int)planes, fG, c, f);
-  else k_prolong4<3><<<nb, 256, 0, st>>>(gf, gc, (int)planes, fG, c, f);
+  if (D == 2) st_launch(k_prolong4<2>, nb, 256, 0, st, gf, gc, (int)planes, fG, c, f);
+  else st_launch(k_prolong4<3>, nb, 256, 0, st, gf, gc, (int)planes, fG, c, f);
   return true;
 }
 

@@ -14,6 +14,10 @@
 
 using namespace st;
 
+namespace st {
+thread_local int tl_pdl = 1;
+}
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -51,6 +55,10 @@ struct Level {
   double dt = 0, mu = 0, omega = 1;
   int next = 0;  // 0 coarsest, 1 space, 2 slabs
   int bottom_sweeps = 2;
+  // depth of the inner multigrid the block-Jacobi smoother uses, and the
+  // Jacobi sweeps at its bottom
+  int smooth_depth = 1;
+  int smooth_sweeps = 2;
   void* e = nullptr;
   void* r = nullptr;
   void* cbar = nullptr;
@@ -123,12 +131,22 @@ double max_shift(int M) {
   return m;
 }
 
+// max |lambda(Q)|.
+double max_eig(int M) {
+  Colloc c;
+  if (colloc_setup(M, &c) != 0) return 1.0;
+  double m = 0;
+  for (int q = 0; q < M; ++q) m = std::max(m, std::abs(c.lam[q]));
+  return m;
+}
+
 // Diffusion number of the shifted slab operator on grid g: |s| nu 2 sum 1/h^2.
 double stiffness(const GridP& g, double nu, double dt, double lam) {
   return lam * dt * nu * 2.0 * (g.ih2[0] + g.ih2[1] + g.ih2[2]);
 }
 
-const double kSigmaStop = 0.25;  // below this Jacobi alone solves the slab systems
+const double kSigmaStop = 0.25;
+const double kMinStep = 1.0 / (1 << 20);  // smallest line-search step before DIVERGED  // below this Jacobi alone solves the slab systems
 
 double default_omega(const st_solver_opts& o, double mu) {
   if (o.omega > 0) return o.omega;
@@ -159,6 +177,7 @@ int validate(const st_problem* p, const st_solver_opts* o) {
     if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU) return ST_ERR_INVALID_ARG;
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) return ST_ERR_INVALID_ARG;
     if (o->inner_cycles < 1 || o->inner_smooth < 1 || o->inner_coarse_iters < 1) return ST_ERR_INVALID_ARG;
+    if (o->smooth_inner_levels < 0 || o->smooth_sweeps < 2) return ST_ERR_INVALID_ARG;
     if (o->sdc_inner_cycles < 1 || o->max_iters < 0 || !(o->tol >= 0)) return ST_ERR_INVALID_ARG;
     if (o->max_levels < 1 || o->coarse_max_points < 1 || o->coarse_max_slabs < 1) return ST_ERR_INVALID_ARG;
     if (o->sdc_qdelta != ST_SDC_IE && o->sdc_qdelta != ST_SDC_LU) return ST_ERR_INVALID_ARG;
@@ -175,10 +194,15 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
   L0.dt = p->T / p->Nt;
   out.push_back(L0);
   const int maxl = std::min(o.max_levels, ST_MAX_LEVELS);
+  const double lam_q = max_eig(p->M);
   while ((int)out.size() < maxl) {
     PlanLevel& cur = out.back();
     const bool cs = can_coarsen(d, cur.g);
-    const bool ct = (cur.Nt % 2 == 0) && cur.Nt >= 2;
+    // Slab bisection doubles dt; with a growing reaction (R' up to |rho|) the
+    // coarse slab systems stay well conditioned only while 2 dt |rho| max|lambda(Q)|
+    // stays below 1/2.
+    const bool ct = (cur.Nt % 2 == 0) && cur.Nt >= 2 &&
+                    (p->reaction == ST_REACTION_NONE || 2.0 * cur.dt * std::fabs(p->rho) * lam_q <= 0.5);
     const double mu = p->nu * cur.dt * cur.g.ih2[0];
     int kind = 0;
     if (o.coarsening == ST_COARSEN_SPACE) {
@@ -264,6 +288,7 @@ struct st_handle {
   double* Ustage = nullptr;
   double* Rstage = nullptr;  // FP64 residual staging for host output on an FP32 handle
   double* lam = nullptr;
+  void* cnode = nullptr;  // R'(U) per node (exact finest-level Jacobian), layout of U
   double* plane = nullptr;  // staging for one plane (gT / target / du0)
   double* plane2 = nullptr;
   std::vector<Alloc> allocs;
@@ -274,6 +299,13 @@ struct st_handle {
 };
 
 namespace {
+
+// Launch mode of the calling thread for the duration of one API call.
+struct PdlScope {
+  int saved;
+  explicit PdlScope(const st_handle* h) : saved(tl_pdl) { if (h) tl_pdl = h->o.use_pdl ? 1 : 0; }
+  ~PdlScope() { tl_pdl = saved; }
+};
 
 void* dev_alloc(st_handle* h, size_t bytes) {
   bytes = round_up(std::max<size_t>(bytes, 256));
@@ -451,12 +483,12 @@ void apply_fuse(InnerParams<T>& ip, const BtFuse<T>& f) {
 }
 
 template <typename T>
-int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, bool use_cbar, bool presmoothed,
-                 const BtFuse<T>* fuse, cudaStream_t st) {
+int inner_vcycle(st_handle* h, Level& Lv, int k, int depth, int sweeps, int P, const Shifts<T>& sh, bool use_cbar,
+                 bool presmoothed, const BtFuse<T>* fuse, cudaStream_t st) {
   InnerLev& I = Lv.in[k];
-  const int last = (int)Lv.in.size() - 1;
+  const int last = depth - 1;
   if (k == last) {
-    if (I.g.Ns <= kInnerCoarseLimit) {
+    if (k == (int)Lv.in.size() - 1 && I.g.Ns <= kInnerCoarseLimit) {
       // one block per slab, all sweeps in shared memory
       InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
       ip.zout = (T*)I.z;
@@ -467,7 +499,7 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, boo
     }
     // non-stiff bottom grid: Jacobi sweeps continuing from z (which holds
     // the zero-start iterate when `presmoothed`)
-    const int todo = presmoothed ? Lv.bottom_sweeps - 1 : Lv.bottom_sweeps;
+    const int todo = presmoothed ? sweeps - 1 : sweeps;
     for (int it = 0; it < todo; ++it) {
       InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
       if (fuse && it == todo - 1) {
@@ -499,7 +531,7 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, boo
     launch_inner_restrict<T>(h->D, ip, st);
     CKL();
   }
-  TRY(inner_vcycle<T>(h, Lv, k + 1, P, sh, use_cbar, true, nullptr, st));
+  TRY(inner_vcycle<T>(h, Lv, k + 1, depth, sweeps, P, sh, use_cbar, true, nullptr, st));
   launch_prolong_space_add<T>(h->D, I.g, Lv.in[k + 1].g, (long long)Lv.Nt * P, (const T*)Lv.in[k + 1].z,
                               (T*)I.z, st);
   CKL();
@@ -522,8 +554,8 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, boo
 // `zero_done`, in[0].z already holds the zero-start Jacobi iterate).  With
 // `fuse` the last sweep applies the back-transform update instead.
 template <typename T>
-int inner_solve(st_handle* h, Level& Lv, int P, const Shifts<T>& sh, bool use_cbar, int cycles, bool zero_done,
-                const BtFuse<T>* fuse, cudaStream_t st) {
+int inner_solve(st_handle* h, Level& Lv, int depth, int sweeps, int P, const Shifts<T>& sh, bool use_cbar,
+                int cycles, bool zero_done, const BtFuse<T>* fuse, cudaStream_t st) {
   const bool smem_bottom_only = Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit;
   if (smem_bottom_only) cycles = 1;  // the shared-memory solve restarts from zero
   for (int c = 0; c < cycles; ++c) {
@@ -538,7 +570,7 @@ int inner_solve(st_handle* h, Level& Lv, int P, const Shifts<T>& sh, bool use_cb
       }
       pre = true;
     }
-    TRY(inner_vcycle<T>(h, Lv, 0, P, sh, use_cbar, pre, f, st));
+    TRY(inner_vcycle<T>(h, Lv, 0, depth, sweeps, P, sh, use_cbar, pre, f, st));
   }
   return ST_OK;
 }
@@ -568,6 +600,8 @@ LinParams<T> lin_params(st_handle* h, const Level& Lv, int adj) {
   lp.e = nullptr;
   lp.r = nullptr;
   lp.cbar = (h->p.reaction != ST_REACTION_NONE) ? (const T*)Lv.cbar : nullptr;
+  // the finest level's operator is the exact Jacobian (R' per node) when kept
+  lp.cnode = (&Lv == &h->L[0] && !adj) ? (const T*)h->cnode : nullptr;
   lp.out = nullptr;
   lp.transform = 0;
   return lp;
@@ -611,7 +645,8 @@ int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   f.e = (T*)Lv.e;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) f.B[a][b] = (T)(adj ? h->Ba[a][b] : h->Bf[a][b]);
-  TRY(inner_solve<T>(h, Lv, M, level_shifts<T>(h, Lv.dt), use_cbar, h->o.inner_cycles, multi, &f, st));
+  TRY(inner_solve<T>(h, Lv, Lv.smooth_depth, Lv.smooth_sweeps, M, level_shifts<T>(h, Lv.dt), use_cbar,
+                     h->o.inner_cycles, multi, &f, st));
   return ST_OK;
 }
 
@@ -803,6 +838,7 @@ ResidParams fine_params(st_handle* h, const double* U, int adj) {
   rp.gT = nullptr;
   rp.R = nullptr;
   rp.cbar = nullptr;
+  rp.cnode = nullptr;
   rp.partial = h->partial;
   return rp;
 }
@@ -812,6 +848,7 @@ int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_
   ResidParams rp = fine_params(h, U, 0);
   rp.R = R;
   rp.cbar = (want_cbar && h->p.reaction != ST_REACTION_NONE) ? h->L[0].cbar : nullptr;
+  rp.cnode = rp.cbar ? h->cnode : nullptr;
   long long nparts = residual_blocks(rp);
   if (!r_fp64 && !h->fp64) {  // FP32 output: double-float kernel
     launch_residual_ff(h->D, rp, h->stream);
@@ -928,6 +965,11 @@ void st_default_opts(st_solver_opts* o) {
   o->max_iters = 1000;
   o->newton = 1;
   o->use_graphs = 1;
+  o->use_pdl = 1;
+  o->smooth_inner_levels = 1;
+  o->smooth_sweeps = 2;
+  o->line_search = 1;
+  o->exact_jacobian = 0;
 }
 
 const char* st_status_str(int s) {
@@ -982,6 +1024,7 @@ int st_plan(const st_problem* p, const st_solver_opts* oin, st_plan_info* out) {
   const size_t Kc = (size_t)C.g.Ns * p->M;
   bytes += round_up(C.Nt * Kc * Kc * esz) + 2 * round_up(C.Nt * Kc * C.g.Ns * esz) +
            2 * round_up(C.Nt * C.g.Ns * C.g.Ns * esz) + round_up(C.Nt * C.g.Ns * esz);
+  if (rx && o.exact_jacobian) bytes += round_up((size_t)pl[0].g.Ns * p->Nt * p->M * esz);
   out->workspace_bytes = bytes;
   out->coarse_points = (int)C.g.Ns;
   return ST_OK;
@@ -1030,6 +1073,16 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     Lv.omega = pl[l].omega;
     Lv.next = pl[l].next;
     Lv.bottom_sweeps = pl[l].bottom_sweeps;
+    {
+      // A level whose next coarser level is coarser in space leaves the
+      // smooth spatial error to that level, so its slab solves need only damp
+      // the oscillatory part; elsewhere (time coarsening or the coarsest
+      // level follows) they keep the full spatial multigrid.
+      const int full = (int)pl[l].inner.size();
+      const int cap = h->o.smooth_inner_levels;
+      Lv.smooth_depth = (cap > 0 && cap < full && pl[l].next == 1) ? cap : full;
+      Lv.smooth_sweeps = Lv.smooth_depth < full ? h->o.smooth_sweeps : Lv.bottom_sweeps;
+    }
     const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
     int s = ST_OK;
     s |= alloc_into(h, &Lv.e, D * h->esz);
@@ -1050,6 +1103,9 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   }
   h->D_total = (long long)h->L[0].g.Ns * pin->Nt * M;
   h->chunk = (h->L[0].g.Ns >= 4096 && pin->Nt >= 8) ? 4 : 1;
+  if (rx && h->o.exact_jacobian) {
+    if (alloc_into(h, &h->cnode, (size_t)h->D_total * h->esz) != ST_OK) return fail(ST_ERR_OOM);
+  }
   // coarsest level
   {
     Level& C = h->L.back();
@@ -1154,6 +1210,7 @@ void st_destroy(st_handle* h) {
 }
 
 int st_set_params(st_handle* h, double nu, double rho) {
+  PdlScope pdl_scope(h);
   if (!h || !(nu > 0) || !std::isfinite(rho)) return ST_ERR_INVALID_ARG;
   h->p.nu = nu;
   h->p.rho = rho;
@@ -1168,6 +1225,7 @@ int st_set_params(st_handle* h, double nu, double rho) {
 }
 
 int st_set_u0(st_handle* h, const double* u0) {
+  PdlScope pdl_scope(h);
   if (!h || !u0) return ST_ERR_INVALID_ARG;
   const long long Ns = h->L[0].g.Ns;
   h->u0_host.assign(Ns, 0.0);
@@ -1179,6 +1237,7 @@ int st_set_u0(st_handle* h, const double* u0) {
 }
 
 int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* norm_out) {
+  PdlScope pdl_scope(h);
   if (!h || !U) return ST_ERR_INVALID_ARG;
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
@@ -1201,6 +1260,7 @@ int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* n
 }
 
 int st_vcycle(st_handle* h, double* U, double* norm_out) {
+  PdlScope pdl_scope(h);
   if (!h || !U) return ST_ERR_INVALID_ARG;
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
@@ -1212,6 +1272,7 @@ int st_vcycle(st_handle* h, double* U, double* norm_out) {
 }
 
 int st_solve(st_handle* h, double* U, st_solve_info* info) {
+  PdlScope pdl_scope(h);
   if (!h || !U) return ST_ERR_INVALID_ARG;
   const double t0 = now_s();
   double* Ud = nullptr;
@@ -1221,12 +1282,23 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
   int status = ST_ERR_NOT_CONVERGED;
   double rel = 0, nrm = 0;
   int it = 0;
-  for (;; ++it) {
+  // Backtracking on ||G|| (non-linear problems): the step U += alpha e of an
+  // iteration is halved until ||G|| drops by the factor 1 - 1e-4 alpha.
+  const bool ls = h->o.line_search && h->p.reaction != ST_REACTION_NONE;
+  double alpha = 0.0, prev = 0.0;
+  for (;;) {
     TRY(fine_residual(h, Ud, h->L[0].r, h->fp64,
                       h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized), 0));
     TRY(read_scalars(h, 1));
     nrm = std::sqrt(h->hscal[0]);
     rel = nrm / ref;
+    if (ls && alpha > 0.0 && !(nrm <= (1.0 - 1e-4 * alpha) * prev)) {
+      if (alpha < kMinStep) { status = ST_ERR_DIVERGED; break; }
+      launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream, -0.5 * alpha);
+      CKL();
+      alpha *= 0.5;
+      continue;
+    }
     hist.push_back(rel);
     if (!std::isfinite(rel) || rel > 1e8) { status = ST_ERR_DIVERGED; break; }
     if (rel <= h->o.tol) { status = ST_OK; break; }
@@ -1239,6 +1311,9 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
     TRY(cycle(h, 0));
     launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
     CKL();
+    prev = nrm;
+    alpha = 1.0;
+    ++it;
   }
   TRY(stage_out(h, U, Ud));
   CK(cudaStreamSynchronize(h->stream));
@@ -1247,6 +1322,7 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
 }
 
 int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
+  PdlScope pdl_scope(h);
   if (!h || !U || nsweeps < 1) return ST_ERR_INVALID_ARG;
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
@@ -1266,10 +1342,12 @@ int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
       CKL();
       if (h->fp64) {
         Shifts<double> sh = real_shift<double>(L0.dt * QI[m][m]);
-        TRY(inner_solve<double>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, false, nullptr, h->stream));
+        TRY(inner_solve<double>(h, L0, (int)L0.in.size(), L0.bottom_sweeps, 1, sh, false, h->o.sdc_inner_cycles,
+                                false, nullptr, h->stream));
       } else {
         Shifts<float> sh = real_shift<float>((float)(L0.dt * QI[m][m]));
-        TRY(inner_solve<float>(h, L0, 1, sh, false, h->o.sdc_inner_cycles, false, nullptr, h->stream));
+        TRY(inner_solve<float>(h, L0, (int)L0.in.size(), L0.bottom_sweeps, 1, sh, false, h->o.sdc_inner_cycles,
+                                false, nullptr, h->stream));
       }
       launch_scatter_plane(h->fp64, L0.in[0].z, L0.e, L0.g.Ns, L0.Nt, M, m, h->stream);
       CKL();
@@ -1285,6 +1363,7 @@ int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
 
 int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, double* dnu, double* drho,
                               double* du0, st_solve_info* info) {
+  PdlScope pdl_scope(h);
   if (!h || !U || !gT) return ST_ERR_INVALID_ARG;
   if (h->p.bc == ST_BC_NEUMANN) return ST_ERR_UNSUPPORTED;
   const double t0 = now_s();
@@ -1347,6 +1426,7 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, d
 }
 
 int st_adjoint_lambda(st_handle* h, double* out) {
+  PdlScope pdl_scope(h);
   if (!h || !out || !h->lam) return ST_ERR_INVALID_ARG;
   CK(cudaMemcpyAsync(out, h->lam, h->D_total * sizeof(double), cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1355,6 +1435,7 @@ int st_adjoint_lambda(st_handle* h, double* out) {
 
 int st_adjoint_solve(st_handle* h, const double* U, const double* u_target, double* dnu, double* drho,
                      double* du0, st_solve_info* info) {
+  PdlScope pdl_scope(h);
   if (!h || !U || !u_target) return ST_ERR_INVALID_ARG;
   // gT = h^d (u_{Nt,M} - target), formed on the host from the last plane
   const long long Ns = h->L[0].g.Ns;
@@ -1416,6 +1497,7 @@ int st_level_info_get(const st_handle* h, int level, st_level_info* out) {
 }
 
 int st_linearize(st_handle* h, const double* U) {
+  PdlScope pdl_scope(h);
   if (!h || !U) return ST_ERR_INVALID_ARG;
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
@@ -1431,6 +1513,7 @@ static size_t level_elems(const st_handle* h, int l) {
 }
 
 int st_level_cbar(st_handle* h, int level, void* out) {
+  PdlScope pdl_scope(h);
   if (!h || !out || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
   const Level& Lv = h->L[level];
   const size_t n = (size_t)Lv.g.Ns * Lv.Nt * h->esz;
@@ -1441,6 +1524,7 @@ int st_level_cbar(st_handle* h, int level, void* out) {
 }
 
 int st_level_residual(st_handle* h, int level, int transpose, const void* e, const void* r, void* out) {
+  PdlScope pdl_scope(h);
   if (!h || !r || !out || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
   if (h->fp64) TRY(level_residual<double>(h, level, transpose, e, r, out, 0, h->stream));
   else TRY(level_residual<float>(h, level, transpose, e, r, out, 0, h->stream));
@@ -1449,6 +1533,7 @@ int st_level_residual(st_handle* h, int level, int transpose, const void* e, con
 }
 
 int st_level_smooth(st_handle* h, int level, int transpose, void* e, const void* r) {
+  PdlScope pdl_scope(h);
   if (!h || !e || !r || level < 0 || level >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
   Level& Lv = h->L[level];
   const size_t n = level_elems(h, level) * h->esz;
@@ -1462,6 +1547,7 @@ int st_level_smooth(st_handle* h, int level, int transpose, void* e, const void*
 }
 
 int st_level_restrict(st_handle* h, int level, int transpose, const void* fine, void* coarse) {
+  PdlScope pdl_scope(h);
   if (!h || !fine || !coarse || level < 0 || level + 1 >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
   if (h->fp64) TRY(restrict_level<double>(h, level, transpose, fine, coarse, h->stream));
   else TRY(restrict_level<float>(h, level, transpose, fine, coarse, h->stream));
@@ -1470,6 +1556,7 @@ int st_level_restrict(st_handle* h, int level, int transpose, const void* fine, 
 }
 
 int st_level_prolong(st_handle* h, int level, int transpose, const void* coarse, void* fine) {
+  PdlScope pdl_scope(h);
   if (!h || !fine || !coarse || level < 0 || level + 1 >= (int)h->L.size()) return ST_ERR_INVALID_ARG;
   if (h->fp64) TRY(prolong_level<double>(h, level, transpose, coarse, fine, h->stream));
   else TRY(prolong_level<float>(h, level, transpose, coarse, fine, h->stream));
@@ -1478,6 +1565,7 @@ int st_level_prolong(st_handle* h, int level, int transpose, const void* coarse,
 }
 
 int st_coarse_solve(st_handle* h, int transpose, const void* r, void* e) {
+  PdlScope pdl_scope(h);
   if (!h || !r || !e) return ST_ERR_INVALID_ARG;
   if (!h->coarse_ready) TRY(linearize_levels(h));
   if (h->fp64) TRY(coarse_solve<double>(h, transpose, r, e, h->stream));
@@ -1487,6 +1575,7 @@ int st_coarse_solve(st_handle* h, int transpose, const void* r, void* e) {
 }
 
 int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
+  PdlScope pdl_scope(h);
   if (!h || !r || !e) return ST_ERR_INVALID_ARG;
   if (!h->coarse_ready) TRY(linearize_levels(h));
   const size_t n = level_elems(h, 0) * h->esz;
@@ -1499,6 +1588,7 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
+  PdlScope pdl_scope(h);
   if (!h || iters < 1 || which < 0 || which > 7) return ST_ERR_INVALID_ARG;
   if (which >= ST_KERNEL_SHIFTED_RESIDUAL && h->L[0].in.size() < 2) return ST_ERR_UNSUPPORTED;
   if (which == ST_KERNEL_FINE_RESIDUAL && (!U || !is_device_ptr(U))) return ST_ERR_INVALID_ARG;
@@ -1515,6 +1605,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         ResidParams rp = fine_params(h, U, 0);
         rp.R = L0.r;
         rp.cbar = rx ? L0.cbar : nullptr;
+        rp.cnode = rx ? h->cnode : nullptr;
         if (h->fp64) launch_residual(h->D, 1, 1, rp, st);
         else launch_residual_ff(h->D, rp, st);
         CKL();
@@ -1623,6 +1714,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
 }
 
 int st_stats(st_handle* h, st_stats_info* out) {
+  PdlScope pdl_scope(h);
   if (!h || !out) return ST_ERR_INVALID_ARG;
   out->levels = (int)h->L.size();
   out->cycle_graph_nodes = (int)h->gnodes[0];

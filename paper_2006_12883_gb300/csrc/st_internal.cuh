@@ -11,6 +11,16 @@
 
 namespace st {
 
+// Every kernel is launched with programmatic stream serialisation (see
+// st_launch): its blocks may become resident while the previous kernel on the
+// stream drains, so each kernel begins by waiting for that kernel's completion
+// and memory flush, and then lets its own successor be scheduled.  Without the
+// launch attribute both instructions are no-ops.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 enum { BC_DIR = ST_BC_DIRICHLET, BC_PER = ST_BC_PERIODIC, BC_NEU = ST_BC_NEUMANN };
 
 // Division of 0 <= n < 2^31 by a fixed divisor d with a multiply-high and a
@@ -322,6 +332,7 @@ struct ResidParams {
   const double* gT;    // adjoint: terminal gradient on node M of slab Nt (may be null)
   void* R;             // output residual (float or double, may be null)
   void* cbar;          // output mean_m R'(U) (may be null)
+  void* cnode;         // output R'(U) at every node, layout of U (may be null)
   double* partial;     // per-block sums of squares (may be null)
 };
 
@@ -348,6 +359,7 @@ struct LinParams {
   const T* e;          // may be null (= 0)
   const T* r;
   const T* cbar;       // may be null (= 0)
+  const T* cnode;      // forward only: R'(U) per node replacing cbar in A e (exact Jacobian; may be null)
   T* out;
   int transform;       // 1: out = F * res (per point, over the M nodes)
   T F[MAXM][MAXM];

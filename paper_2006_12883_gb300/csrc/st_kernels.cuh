@@ -1,9 +1,35 @@
 // Launcher declarations of the CUDA kernels (one translation unit per group).
 #pragma once
 
+#include <utility>
+
 #include "st_internal.cuh"
 
 namespace st {
+
+// 1 (default): launches carry the programmatic-stream-serialisation attribute,
+// which hides most of the launch latency of the many small kernels of a cycle;
+// set per call from the handle's options.
+extern thread_local int tl_pdl;
+
+// Kernel launch used by every launcher: the kernel's first instruction is
+// grid_dep_wait(), so ordering against the previous launch on `st` holds with or
+// without the attribute.  Errors surface through cudaGetLastError.
+template <typename... KArgs, typename... Args>
+inline void st_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = tl_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // SDC node coefficients: qi[q] = dt*QI[m][q], qe[q] = dt*QE[m][q] for q < m.
 struct SdcCoef {
@@ -37,7 +63,8 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st);
 void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st);
 void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st);
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st);
-void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st);
+// U += alpha * e (n values)
+void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha = 1.0);
 void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,
                     double rho, const SdcCoef& cf, const void* G, const void* delta, const double* U,
                     void* y, cudaStream_t st);

@@ -37,7 +37,10 @@ class StSolverOpts(ctypes.Structure):
                 ("nu2", c_int), ("omega", c_double), ("mu_crit", c_double), ("inner_cycles", c_int),
                 ("inner_smooth", c_int), ("inner_coarse_iters", c_int), ("coarse_max_points", c_int),
                 ("coarse_max_slabs", c_int), ("sdc_qdelta", c_int), ("sdc_inner_cycles", c_int),
-                ("tol", c_double), ("max_iters", c_int), ("newton", c_int), ("use_graphs", c_int)]
+                ("tol", c_double), ("max_iters", c_int), ("newton", c_int), ("use_graphs", c_int),
+                ("use_pdl", c_int), ("smooth_inner_levels", c_int),
+                ("smooth_sweeps", c_int), ("line_search", c_int),
+                ("exact_jacobian", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -417,3 +420,59 @@ class Solver:
         e = _torch().empty_like(r)
         check(lib().st_level_vcycle(self.h, int(transpose), self._ptr(r), self._ptr(e)), "st_level_vcycle")
         return e
+
+
+# ------------------------------------------------------- differentiable solve
+
+_STSOLVE = None
+
+
+def _stsolve_function():
+    global _STSOLVE
+    if _STSOLVE is not None:
+        return _STSOLVE
+    torch = _torch()
+
+    class _STSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, solver, nu, rho, u0):
+            solver.set_params(float(nu), float(rho))
+            solver.set_u0(u0.detach().to(solver.device))
+            U = solver.zeros()
+            solver.solve(U)
+            ctx.solver = solver
+            ctx.theta = (float(nu), float(rho))
+            ctx.u0 = u0.detach()
+            ctx.save_for_backward(U)
+            return U[-1, -1].clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            (U,) = ctx.saved_tensors
+            S = ctx.solver
+            S.set_params(*ctx.theta)
+            S.set_u0(ctx.u0.to(S.device))
+            gT = g.detach().to(device=S.device, dtype=torch.float64).contiguous().reshape(-1)
+            du0 = torch.empty(S.Ns, dtype=torch.float64, device=S.device)
+            dnu, drho, _ = S.adjoint(U, gT=gT, du0=du0)
+            dev, dt = ctx.u0.device, torch.float64
+            return (None, torch.tensor(dnu, dtype=dt, device=dev), torch.tensor(drho, dtype=dt, device=dev),
+                    du0.reshape(ctx.u0.shape).to(dev))
+
+    _STSOLVE = _STSolve
+    return _STSOLVE
+
+
+class STSolve:
+    """u(T) = STSolve.apply(solver, nu, rho, u0): the final node plane of the
+    all-at-once collocation solution (Eq. 3.4) as a differentiable function of
+    the diffusion coefficient, the reaction rate and the initial value.  The
+    backward pass is the discrete adjoint (transposed all-at-once system,
+    solved by the same multigrid) with the incoming gradient as the terminal
+    data, returning (dnu, drho, du0).  nu and rho are 0-d float64 tensors, u0
+    a float64 tensor of the grid's shape; the solver's own problem sizes,
+    boundary and reaction kind are used."""
+
+    @staticmethod
+    def apply(solver, nu, rho, u0):
+        return _stsolve_function().apply(solver, nu, rho, u0)

@@ -98,3 +98,28 @@ def test_adjoint_neumann_unsupported():
     _, _, info = S.adjoint(U, target=torch.zeros(17, dtype=torch.float64, device="cuda"), raise_on_error=False)
     assert info["status"] == stlib.ST_ERR_UNSUPPORTED
     S.close()
+
+
+def test_stsolve_autograd_matches_oracle_gradients():
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    S = case.solver(precision=stlib.FP64, tol=1e-12)
+    target = torch.tensor(_target(case), device="cuda")
+    nu = torch.tensor(case.nu, dtype=torch.float64, requires_grad=True)
+    rho = torch.tensor(case.rho, dtype=torch.float64, requires_grad=True)
+    u0 = torch.tensor(case.u0(), device="cuda").reshape(case.shape).requires_grad_(True)
+    uT = stlib.STSolve.apply(S, nu, rho, u0)
+    h2 = float(np.prod([space.spacing(case.bc, n, case.X) for n in case.shape]))
+    loss = 0.5 * h2 * ((uT.reshape(-1) - target) ** 2).sum()
+    loss.backward()
+    U = S.zeros()
+    S.solve(U)
+    Uh = U.cpu().numpy().reshape(p.Nt, p.M, -1)
+    gT = h2 * (Uh[-1, -1] - target.cpu().numpy())
+    lam = oadj.adjoint_solve(p, Uh, gT)
+    rnu, rrho, rdu0 = oadj.gradients(p, Uh, lam)
+    assert abs(nu.grad.item() - rnu) <= 1e-8 * abs(rnu)
+    assert abs(rho.grad.item() - rrho) <= 1e-8 * abs(rrho)
+    assert np.linalg.norm(u0.grad.cpu().numpy().ravel() - rdu0) <= 1e-8 * np.linalg.norm(rdu0)
+    S.close()

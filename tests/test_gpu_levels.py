@@ -20,12 +20,18 @@ MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=
 LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5]
 
 
-def _oracle_level(S, case, l, cbar):
+def _oracle_level(S, case, l, cbar, U=None):
+    """The oracle's level l; with U (the linearisation point) level 0 carries
+    R'(U) per node, as the library's finest level does by default."""
     li = S.level_info(l)
     d = len(case.shape)
     shape = tuple(li["n"][:d][::-1])
+    cnode = None
+    if U is not None and l == 0 and case.reaction != space.NONE:
+        p = case.problem()
+        cnode = p.dR(np.asarray(U).reshape(p.Nt, p.M, p.Ns))
     return ml.Level(shape=shape, bc=case.bc, Nt=li["Nt"], M=case.M, dt=li["dt"], nu=case.nu, X=case.X,
-                    cbar=cbar)
+                    cbar=cbar, cnode=cnode)
 
 
 def _setup(case, prec, **opts):
@@ -63,13 +69,15 @@ def test_cbar_hierarchy(case, prec):
 
 @pytest.mark.parametrize("case", LEVEL_CASES, ids=lambda c: c.name)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_level_residual_and_transfers(case, prec):
-    p, S, U = _setup(case, prec)
+@pytest.mark.parametrize("ej", [0, 1], ids=["cbar", "exactJ"])
+def test_level_residual_and_transfers(case, prec, ej):
+    p, S, U = _setup(case, prec, exact_jacobian=ej)
     dt = S.cycle_dtype
     for l in range(S.num_levels()):
         cb = S.level_cbar(l).double().cpu().numpy()
         cb = cb.reshape(cb.shape[0], -1)
         lev = _oracle_level(S, case, l, cb)
+        lev_fwd = _oracle_level(S, case, l, cb, U if ej else None)
         shp = S.level_shape(l)
         e = stgen.random_field(shp, 100 + l)
         r = stgen.random_field(shp, 200 + l)
@@ -80,7 +88,11 @@ def test_level_residual_and_transfers(case, prec):
             if tr and case.bc == space.NEUMANN:
                 continue
             got = S.level_residual(l, et, rt, transpose=tr).double().cpu().numpy().reshape(lev.Nt, p.M, -1)
-            ref = (ml.linear_residual_T if tr else ml.linear_residual)(lev, e_, r_)
+            ref = ml.linear_residual_T(lev, e_, r_) if tr else ml.linear_residual(lev_fwd, e_, r_)
+            if l == 0 and not tr and ej:
+                # the finest level's operator is minus the exact Jacobian of G
+                ref2 = r_.reshape(ref.shape) + system.jacobian_apply(p, U, e_).reshape(ref.shape)
+                assert np.abs(ref - ref2).max() <= 1e-12 * (np.abs(ref).max() + 1)
             scale = np.abs(e_).max() * (1 + lev.dt * case.nu * 4 * len(case.shape) / min(S.level_info(l)["h"][:len(case.shape)]) ** 2) + np.abs(r_).max()
             assert np.abs(got - ref).max() <= _tol(prec) * scale, (l, tr)
         if l + 1 < S.num_levels():
@@ -134,13 +146,17 @@ def test_coarse_solve_exact(case, transpose):
 
 
 @pytest.mark.parametrize("case", [HEAT1D, LOG2D, CUB3D, PER2D_M5, PER3D_M5], ids=lambda c: c.name)
-def test_smoothing_step_converged_inner(case):
+@pytest.mark.parametrize("ej", [0, 1], ids=["cbar", "exactJ"])
+def test_smoothing_step_converged_inner(case, ej):
     """With many inner cycles the Q-diagonalised slab solve is exact, so one
-    smoothing step equals damped block Jacobi with exact slab solves."""
-    p, S, U = _setup(case, "fp64", inner_cycles=40, inner_coarse_iters=60)
+    smoothing step equals damped block Jacobi with exact slab solves (of the
+    node-averaged slab matrices; with the exact Jacobian only the residual
+    uses R' per node)."""
+    p, S, U = _setup(case, "fp64", inner_cycles=40, inner_coarse_iters=60, smooth_inner_levels=0,
+                     exact_jacobian=ej)
     l = 0
     cb = S.level_cbar(l).cpu().numpy()
-    lev = _oracle_level(S, case, l, cb.reshape(cb.shape[0], -1))
+    lev = _oracle_level(S, case, l, cb.reshape(cb.shape[0], -1), U if ej else None)
     shp = S.level_shape(l)
     e = stgen.random_field(shp, 500)
     r = stgen.random_field(shp, 501)
@@ -150,6 +166,31 @@ def test_smoothing_step_converged_inner(case):
                                   S.level_info(l)["omega"])
     err = np.abs(et.cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max()
     assert err < 1e-9, err
+    S.close()
+
+
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, DIR2D_M5, PER2D_M5], ids=lambda c: c.name)
+@pytest.mark.parametrize("sweeps", [2, 3, 5])
+def test_smoothing_step_jacobi_slab_solves(case, sweeps):
+    """On a level that coarsens in space next, the default smoother replaces
+    each slab solve by a few weighted-Jacobi sweeps on the eigen-decoupled
+    shifted systems (no inner multigrid): compared with the oracle's
+    complex-arithmetic version of exactly that step."""
+    p, S, U = _setup(case, "fp64", smooth_inner_levels=1, smooth_sweeps=sweeps, exact_jacobian=sweeps % 2)
+    info = S.level_info(0)
+    assert info["next_kind"] == 1
+    cb = S.level_cbar(0).cpu().numpy()
+    lev = _oracle_level(S, case, 0, cb.reshape(cb.shape[0], -1), U if sweeps % 2 else None)
+    shp = S.level_shape(0)
+    e = stgen.random_field(shp, 510)
+    r = stgen.random_field(shp, 511)
+    et = torch.tensor(e, device="cuda")
+    S.level_smooth(0, et, torch.tensor(r, device="cuda"))
+    omega_j = {1: 2.0 / 3.0, 2: 0.8, 3: 6.0 / 7.0}[len(case.shape)]
+    ref = ml.smoothing_step_jacobi(lev, e.reshape(lev.Nt, p.M, -1), r.reshape(lev.Nt, p.M, -1), info["omega"],
+                                   sweeps, omega_j)
+    err = np.abs(et.cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max()
+    assert err < 1e-12, err
     S.close()
 
 

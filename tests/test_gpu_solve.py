@@ -51,7 +51,7 @@ def test_heat_closed_form_and_vcycle_api():
     case = HEAT1D
     S = case.solver(precision=stlib.FP64, tol=1e-13)
     U = S.zeros()
-    norms = [S.vcycle(U) for _ in range(12)]
+    norms = [S.vcycle(U) for _ in range(30)]
     assert norms[-1] < 1e-11 * norms[0]
     x = stgen.coords1d(space.DIRICHLET, 63)
     p = case.problem()
@@ -196,3 +196,31 @@ def test_allocator_failure_is_oom():
     h = ctypes.c_void_p()
     s = stlib.lib().st_create(ctypes.byref(prob), None, ctypes.byref(rt), ctypes.byref(h))
     assert s == stlib.ST_ERR_OOM and not h.value
+
+
+# The paper's monodomain problem (Section 5.4: X = 10, T = 2, gamma = 5, a
+# narrow stimulus) on a coarser grid.  From the zero initial guess the first
+# Newton correction follows the linearisation at u = 0, which grows like
+# e^{5t}; only a damped step keeps the iteration in range.
+MONO_LS = Case("monodomain_ls", (257,), space.NEUMANN, 1.0, 256, 3, T=2.0, X=10.0, reaction=space.CUBIC,
+               rho=5.0, u0_kind="stimulus")
+
+
+@pytest.mark.parametrize("ej", [0, 1], ids=["cbar", "exactJ"])
+def test_monodomain_with_line_search(ej):
+    from paper_2006_12883_gb300 import stlib
+    case = MONO_LS
+    S = case.solver(precision=stlib.FP64, tol=1e-11, max_iters=200, exact_jacobian=ej)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0, info
+    ref = _oracle_solution(case)
+    got = U.cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    # without the line search the first full step leaves the basin
+    S2 = case.solver(precision=stlib.FP64, tol=1e-11, max_iters=200, exact_jacobian=ej, line_search=0)
+    U2 = S2.zeros()
+    info2 = S2.solve(U2, raise_on_error=False)
+    assert info2["status"] != 0 or info2["iterations"] >= info["iterations"]
+    S.close()
+    S2.close()

@@ -227,6 +227,68 @@ def test_exact_block_jacobi_with_omega1_is_nilpotent():
     assert np.abs(e - ml.coarse_solve_exact(lev, r)).max() < 1e-13
 
 
+@pytest.mark.parametrize("reaction", [space.LOGISTIC, space.CUBIC])
+def test_level_with_node_derivatives_is_exact_jacobian(reaction):
+    """A level carrying R'(U) per node is minus the exact Jacobian of G:
+    r - A e + C e = r + dG(U)[e], and dG(U)[e] matches a central difference
+    of G (exact up to rounding for the quadratic logistic term; O(eps^2)
+    for the cubic)."""
+    p = system.Problem(shape=(6, 5), bc=P, nu=0.1, Nt=3, M=3, T=0.3, reaction=reaction, rho=2.0)
+    U = stgen.random_field((3, 3, 30), 34, 0.4) + 0.3
+    u0 = stgen.random_field((30,), 35)
+    lev = ml.Level(shape=p.shape, bc=P, Nt=3, M=3, dt=p.dt, nu=p.nu, X=1.0,
+                   cbar=system.cbar(p, U), cnode=p.dR(U))
+    e = stgen.random_field((3, 3, 30), 36)
+    r = stgen.random_field((3, 3, 30), 37)
+    got = ml.linear_residual(lev, e, r)
+    Je = system.jacobian_apply(p, U, e)
+    assert np.abs(got - (r + Je)).max() < 1e-13
+    h = 1e-5
+    fd = (system.residual(p, U + h * e, u0) - system.residual(p, U - h * e, u0)) / (2 * h)
+    assert np.abs(fd.reshape(Je.shape) - Je).max() < 1e-8
+
+
+@pytest.mark.parametrize("M", [2, 3, 5])
+def test_jacobi_smoothing_step_tends_to_exact(M):
+    """Many Jacobi sweeps on the eigen-decoupled slab systems (complex shifts
+    for M >= 2) reproduce the exact slab solve of the assembled matrix."""
+    lev = ml.Level(shape=(6, 5), bc=P, Nt=3, M=M, dt=0.05, nu=0.1, X=1.0,
+                   cbar=stgen.random_field((3, 30), 28, 0.3))
+    r = stgen.random_field((3, M, 30), 29)
+    e = stgen.random_field((3, M, 30), 30)
+    ref = ml.smoothing_step_exact(lev, e, r, 0.8)
+    got = ml.smoothing_step_jacobi(lev, e, r, 0.8, 200, 0.8)
+    assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_jacobi_smoothing_step_without_spatial_operator():
+    """With L + diag cbar = 0 every slab system is the identity, so a single
+    undamped sweep is already the exact slab solve."""
+    lev = ml.Level(shape=(5,), bc=P, Nt=4, M=3, dt=0.1, nu=0.0, X=1.0, cbar=np.zeros((4, 5)))
+    r = stgen.random_field((4, 3, 5), 32)
+    e = stgen.random_field((4, 3, 5), 33)
+    ref = ml.smoothing_step_exact(lev, e, r, 0.7)
+    got = ml.smoothing_step_jacobi(lev, e, r, 0.7, 1, 1.0)
+    assert np.abs(got - ref).max() < 1e-13
+
+
+def test_jacobi_smoothing_step_damps_oscillatory_error():
+    """A few sweeps remove most of a checkerboard slab error (the part the
+    smoother is responsible for) but leave most of a spatially constant one
+    (which Jacobi reduces only through the shift's diagonal, 1 + 4 dt lambda nu / h^2)."""
+    n = 16
+    lev = ml.Level(shape=(n, n), bc=P, Nt=1, M=3, dt=0.1, nu=0.05, X=1.0, cbar=np.zeros((1, n * n)))
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r = np.zeros((1, 3, n * n))
+    checker = ((-1.0) ** (ii + jj)).ravel()
+    for u, expect_small in ((checker, True), (np.ones(n * n), False)):
+        e_true = np.tile(u, (1, 3, 1))
+        r = ml.apply_A(lev, e_true)          # A e_true = r with a single slab
+        e = ml.smoothing_step_jacobi(lev, np.zeros_like(r), r, 1.0, 5, 0.8)
+        rel = np.abs(e - e_true).max() / np.abs(e_true).max()
+        assert (rel < 0.05) if expect_small else (rel > 0.5), rel
+
+
 # -------------------------------------------------------------------- sdc
 
 def test_sdc_m1_is_implicit_euler():
