@@ -112,12 +112,14 @@ typedef struct {
   int use_pdl;          /* 1 (default): programmatic dependent launch, so each
                            kernel is scheduled while its predecessor drains */
   int smooth_inner_levels; /* depth of the spatial multigrid inside the
-                           block-Jacobi smoother's slab solves: 1 (default) =
-                           Jacobi sweeps on the level's own grid, 0 = the full
-                           hierarchy (coarsened until non-stiff).  SDC node
-                           solves always use the full hierarchy. */
+                           block-Jacobi smoother's slab solves on levels above
+                           the last space bisection: 1 (default) = Jacobi
+                           sweeps on the level's own grid, 0 = the full
+                           hierarchy (coarsened until non-stiff).  Levels below
+                           the last space bisection and SDC node solves always
+                           use the full hierarchy. */
   int smooth_sweeps;    /* Jacobi sweeps of a depth-capped smoother slab solve
-                           (>= 2, default 2; the first is the zero-start one) */
+                           (>= 2, default 3; the first is the zero-start one) */
   int line_search;      /* 1 (default): st_solve halves the step of a Newton
                            iteration (reaction != NONE) until ||G|| decreases
                            by the factor 1 - 1e-4 * step; DIVERGED below 2^-20 */

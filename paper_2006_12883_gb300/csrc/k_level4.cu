@@ -91,8 +91,18 @@ __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// 2D, M = 3 fits 64 registers (4 blocks of 256 per SM); larger instances
+// keep their registers rather than spill.
 template <int D, int M>
-__global__ void __launch_bounds__(256) k_lin_residual4(LinParams<float> p, FastDiv fG) {
+constexpr int inner4_min_blocks() { return (D == 2 && M == 3) ? 4 : 1; }
+
+// The level residual keeps M planes of e and their stencil sums live: at most
+// 128 registers (2 blocks per SM) except 2D, M = 3 (64, 4 blocks).
+template <int D, int M>
+constexpr int lin4_min_blocks() { return (D == 2 && M == 3) ? 4 : 2; }
+
+template <int D, int M>
+__global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(LinParams<float> p, FastDiv fG) {
   grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.nchunks * (unsigned)(p.g.Ns >> 2)) return;
@@ -196,10 +206,6 @@ __global__ void __launch_bounds__(256) k_lin_residual4(LinParams<float> p, FastD
 // Shifted-system operator at 4 points of all planes: out[pl][q] = y - A z
 // (mode 0: residual into zout) or a Jacobi sweep (mode 1) with optional
 // fused back-transform into e.
-// 2D, M = 3 fits 64 registers (4 blocks of 256 per SM); larger instances
-// keep their registers rather than spill.
-template <int D, int M>
-constexpr int inner4_min_blocks() { return (D == 2 && M == 3) ? 4 : 1; }
 
 template <int D, int M, int MODE>
 __global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(InnerParams<float> p, FastDiv fG) {

@@ -967,7 +967,7 @@ void st_default_opts(st_solver_opts* o) {
   o->use_graphs = 1;
   o->use_pdl = 1;
   o->smooth_inner_levels = 1;
-  o->smooth_sweeps = 2;
+  o->smooth_sweeps = 3;
   o->line_search = 1;
   o->exact_jacobian = 0;
 }
@@ -1074,13 +1074,16 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     Lv.next = pl[l].next;
     Lv.bottom_sweeps = pl[l].bottom_sweeps;
     {
-      // A level whose next coarser level is coarser in space leaves the
-      // smooth spatial error to that level, so its slab solves need only damp
-      // the oscillatory part; elsewhere (time coarsening or the coarsest
-      // level follows) they keep the full spatial multigrid.
+      // While some coarser level of the hierarchy is coarser in space, the
+      // smooth spatial error is left to it, so the slab solves need only damp
+      // the oscillatory part; below the last space bisection (only slab
+      // bisection or the coarsest level follows) they keep the full spatial
+      // multigrid.
+      bool space_below = false;
+      for (size_t q = l; q < pl.size(); ++q) space_below = space_below || pl[q].next == 1;
       const int full = (int)pl[l].inner.size();
       const int cap = h->o.smooth_inner_levels;
-      Lv.smooth_depth = (cap > 0 && cap < full && pl[l].next == 1) ? cap : full;
+      Lv.smooth_depth = (cap > 0 && cap < full && space_below) ? cap : full;
       Lv.smooth_sweeps = Lv.smooth_depth < full ? h->o.smooth_sweeps : Lv.bottom_sweeps;
     }
     const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
