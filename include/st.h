@@ -131,6 +131,19 @@ typedef struct {
                            node average.  0 (default): node average
                            everywhere (quasi-Newton; same rate per cycle on
                            the bench workloads, about 2.5 % less traffic). */
+  int krylov;           /* 0 (default): one V-cycle per outer iteration.
+                           m in 1..30: each st_solve iteration solves the
+                           finest-level linear system by right-preconditioned
+                           flexible GMRES with one V-cycle per Krylov step, at
+                           most m steps (2m + 1 extra vectors of the size of U
+                           in the cycle precision, allocated at first use);
+                           use with exact_jacobian = 1 for a Newton method */
+  double krylov_rtol;   /* GMRES stops when its residual estimate falls by
+                           this factor (default 1e-2) */
+  int krylov_fallback;  /* with krylov = 0: when the line search finds no
+                           decrease along a cycle's correction, st_solve
+                           continues with the exact Jacobian and FGMRES of
+                           this many steps (default 10; 0 = report DIVERGED) */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -154,6 +167,7 @@ typedef struct {
   double seconds;          /* wall time of the call */
   int history_len;
   double history[ST_MAX_HISTORY]; /* relative residual per iteration */
+  int cycles;              /* V-cycles applied (= iterations unless krylov > 0) */
 } st_solve_info;
 
 typedef struct {

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
 #pragma unroll
       for (int a = 0; a < MAXM; ++a) {
         if (a < M) {
-          T acc = p.r[base + (long long)a * Ns] - ev[a];
+          T acc = (p.r ? p.r[base + (long long)a * Ns] : (T)0) - ev[a];
 #pragma unroll
           for (int b = 0; b < MAXM; ++b)
             if (b < M) acc = fma(p.W[a][b], Fe[b], acc);
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_lin_residual(LinParams<T> p) {
     } else {
 #pragma unroll
       for (int a = 0; a < MAXM; ++a)
-        if (a < M) res[a] = p.r[base + (long long)a * Ns];
+        if (a < M) res[a] = p.r ? p.r[base + (long long)a * Ns] : (T)0;
     }
     if (p.transform) {
       T y[MAXM];

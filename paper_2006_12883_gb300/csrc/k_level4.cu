@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         float r4[4];
-        to4(ld4(p.r + base + (long long)a * Ns), r4);
+        if (p.r) to4(ld4(p.r + base + (long long)a * Ns), r4);
+        else r4[0] = r4[1] = r4[2] = r4[3] = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float acc = r4[q] - ev[a][q];
@@ -166,7 +167,10 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
       for (int q = 0; q < 4; ++q) carry[q] = p.transpose ? sum[q] : ev[M - 1][q];
     } else {
 #pragma unroll
-      for (int a = 0; a < M; ++a) to4(ld4(p.r + base + (long long)a * Ns), res[a]);
+      for (int a = 0; a < M; ++a) {
+        if (p.r) to4(ld4(p.r + base + (long long)a * Ns), res[a]);
+        else res[a][0] = res[a][1] = res[a][2] = res[a][3] = 0.f;
+      }
     }
     if (p.transform) {
       float y[M][4];

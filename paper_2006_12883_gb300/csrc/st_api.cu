@@ -178,6 +178,8 @@ int validate(const st_problem* p, const st_solver_opts* o) {
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) return ST_ERR_INVALID_ARG;
     if (o->inner_cycles < 1 || o->inner_smooth < 1 || o->inner_coarse_iters < 1) return ST_ERR_INVALID_ARG;
     if (o->smooth_inner_levels < 0 || o->smooth_sweeps < 2) return ST_ERR_INVALID_ARG;
+    if (o->krylov < 0 || o->krylov > 30 || !(o->krylov_rtol > 0.0)) return ST_ERR_INVALID_ARG;
+    if (o->krylov_fallback < 0 || o->krylov_fallback > 30) return ST_ERR_INVALID_ARG;
     if (o->sdc_inner_cycles < 1 || o->max_iters < 0 || !(o->tol >= 0)) return ST_ERR_INVALID_ARG;
     if (o->max_levels < 1 || o->coarse_max_points < 1 || o->coarse_max_slabs < 1) return ST_ERR_INVALID_ARG;
     if (o->sdc_qdelta != ST_SDC_IE && o->sdc_qdelta != ST_SDC_LU) return ST_ERR_INVALID_ARG;
@@ -251,6 +253,11 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
 
 size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
 
+// pinned host doubles: [0, 8) scalars read back after reductions, [16, 80)
+// Krylov dot products
+const int kHostScalars = 80;
+const int kHostKrylov = 16;
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -289,6 +296,12 @@ struct st_handle {
   double* Rstage = nullptr;  // FP64 residual staging for host output on an FP32 handle
   double* lam = nullptr;
   void* cnode = nullptr;  // R'(U) per node (exact finest-level Jacobian), layout of U
+  // Krylov-accelerated Newton step: bases V (m+1 vectors) and Z (m vectors)
+  void* kV = nullptr;
+  void* kZ = nullptr;
+  double* kpart = nullptr;  // dot-product partial sums
+  double* kdots = nullptr;  // 64 device doubles
+  int kdim = 0;             // Krylov steps the bases hold
   double* plane = nullptr;  // staging for one plane (gT / target / du0)
   double* plane2 = nullptr;
   std::vector<Alloc> allocs;
@@ -916,6 +929,7 @@ void fill_info(st_solve_info* info, int it, int status, double rel, double abs_,
   info->abs_residual = abs_;
   info->ref_norm = ref;
   info->seconds = secs;
+  info->cycles = it;
   info->history_len = (int)std::min<size_t>(hist.size(), ST_MAX_HISTORY);
   const size_t off = hist.size() > ST_MAX_HISTORY ? hist.size() - ST_MAX_HISTORY : 0;
   for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[off + i];
@@ -935,6 +949,116 @@ int outer_step(st_handle* h, double* Ud, bool do_cycle) {
   TRY(cycle(h, 0));
   launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
   CKL();
+  return ST_OK;
+}
+
+// Switch the finest level's operator to the exact Jacobian (allocates R'
+// per node; the captured cycle graphs hold the old operator).
+int enable_exact_jacobian(st_handle* h) {
+  if (h->cnode || h->p.reaction == ST_REACTION_NONE) return ST_OK;
+  TRY(alloc_into(h, &h->cnode, (size_t)h->D_total * h->esz));
+  invalidate_graphs(h);
+  return ST_OK;
+}
+
+// Right-preconditioned flexible GMRES (Saad 1993) on the finest level's
+// linear system (A - C) d = r with r = G(U) in L0.r, one V-cycle as the
+// preconditioner; at most o.krylov iterations or until the preconditioned
+// residual estimate drops by o.krylov_rtol.  The correction is left in L0.e.
+int krylov_step(st_handle* h, int m, int* its) {
+  Level& L0 = h->L[0];
+  const long long n = h->D_total;
+  const size_t es = h->esz;
+  const int f64 = h->fp64 ? 1 : 0;
+  cudaStream_t st = h->stream;
+  double* hk = h->hscal + kHostKrylov;
+  if (h->kdim < m) {  // bases for m steps (earlier, smaller ones stay with the handle)
+    TRY(alloc_into(h, &h->kV, (size_t)(m + 1) * n * es));
+    TRY(alloc_into(h, &h->kZ, (size_t)m * n * es));
+    if (!h->kpart) TRY(alloc_typed(h, &h->kpart, (size_t)krylov_partials(n) * sizeof(double)));
+    if (!h->kdots) TRY(alloc_typed(h, &h->kdots, 64 * sizeof(double)));
+    h->kdim = m;
+  }
+  auto V = [&](int i) { return (void*)((char*)h->kV + (size_t)i * n * es); };
+  auto Z = [&](int i) { return (void*)((char*)h->kZ + (size_t)i * n * es); };
+  // hk[0..k) = <w, B_i>, B_i = B + i n
+  auto dots = [&](const void* w, const void* B, int k) -> int {
+    launch_mdot(f64, w, B, n, k, n, h->kpart, h->kdots, st);
+    CKL();
+    CK(cudaMemcpyAsync(hk, h->kdots, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return ST_OK;
+  };
+  auto apply = [&](const void* z, void* out) -> int {  // out = -(A - C) z
+    if (f64) return level_residual<double>(h, 0, 0, z, nullptr, out, 0, st);
+    return level_residual<float>(h, 0, 0, z, nullptr, out, 0, st);
+  };
+  TRY(dots(L0.r, L0.r, 1));
+  const double beta = std::sqrt(hk[0]);
+  *its = 0;
+  if (!(beta > 0.0) || !std::isfinite(beta)) {
+    CK(cudaMemsetAsync(L0.e, 0, n * es, st));
+    return std::isfinite(beta) ? ST_OK : ST_ERR_DIVERGED;
+  }
+  launch_axpby(f64, V(0), L0.r, 1.0 / beta, 0.0, n, st);
+  CKL();
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+  g[0] = beta;
+  int j = 0;
+  while (j < m) {
+    CK(cudaMemcpyAsync(L0.r, V(j), n * es, cudaMemcpyDeviceToDevice, st));
+    TRY(cycle(h, 0));
+    CK(cudaMemcpyAsync(Z(j), L0.e, n * es, cudaMemcpyDeviceToDevice, st));
+    TRY(apply(Z(j), V(j + 1)));  // w = -(A - C) z_j
+    // classical Gram-Schmidt, twice; H(i, j) = <(A - C) z_j, v_i> = -<w, v_i>
+    for (int pass = 0; pass < 2; ++pass) {
+      TRY(dots(V(j + 1), h->kV, j + 1));
+      KrylovCoef c;
+      c.k = j + 1;
+      for (int i = 0; i <= j; ++i) {
+        c.c[i] = hk[i];
+        Hc(i, j) -= hk[i];
+      }
+      launch_maxpy(f64, V(j + 1), h->kV, n, c, n, st);
+      CKL();
+    }
+    TRY(dots(V(j + 1), V(j + 1), 1));
+    const double nrm = std::sqrt(hk[0]);
+    if (!std::isfinite(nrm)) return ST_ERR_DIVERGED;
+    Hc(j + 1, j) = nrm;
+    if (nrm > 0.0) {
+      launch_axpby(f64, V(j + 1), V(j + 1), -1.0 / nrm, 0.0, n, st);
+      CKL();
+    }
+    for (int i = 0; i < j; ++i) {
+      const double a0 = Hc(i, j), a1 = Hc(i + 1, j);
+      Hc(i, j) = cs[i] * a0 + sn[i] * a1;
+      Hc(i + 1, j) = -sn[i] * a0 + cs[i] * a1;
+    }
+    const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
+    cs[j] = den > 0.0 ? Hc(j, j) / den : 1.0;
+    sn[j] = den > 0.0 ? Hc(j + 1, j) / den : 0.0;
+    Hc(j, j) = den;
+    Hc(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    ++j;
+    if (std::fabs(g[j]) <= h->o.krylov_rtol * beta || nrm == 0.0) break;
+  }
+  std::vector<double> y(j, 0.0);
+  for (int i = j - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int q = i + 1; q < j; ++q) s -= Hc(i, q) * y[q];
+    y[i] = Hc(i, i) != 0.0 ? s / Hc(i, i) : 0.0;
+  }
+  CK(cudaMemsetAsync(L0.e, 0, n * es, st));
+  KrylovCoef c;
+  c.k = j;
+  for (int i = 0; i < j; ++i) c.c[i] = -y[i];
+  launch_maxpy(f64, L0.e, h->kZ, n, c, n, st);
+  CKL();
+  *its = j;
   return ST_OK;
 }
 
@@ -970,6 +1094,9 @@ void st_default_opts(st_solver_opts* o) {
   o->smooth_sweeps = 3;
   o->line_search = 1;
   o->exact_jacobian = 0;
+  o->krylov = 0;
+  o->krylov_rtol = 1e-2;
+  o->krylov_fallback = 10;
 }
 
 const char* st_status_str(int s) {
@@ -1174,7 +1301,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     s |= alloc_typed(h, &h->plane, Ns * sizeof(double));
     s |= alloc_typed(h, &h->plane2, Ns * sizeof(double));
     if (s != ST_OK) return fail(ST_ERR_OOM);
-    if (cudaMallocHost(&h->hscal, 8 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost(&h->hscal, kHostScalars * sizeof(double)) != cudaSuccess) {
       set_err(cudaGetLastError(), "cudaMallocHost");
       return fail(ST_ERR_CUDA);
     }
@@ -1289,6 +1416,8 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
   // iteration is halved until ||G|| drops by the factor 1 - 1e-4 alpha.
   const bool ls = h->o.line_search && h->p.reaction != ST_REACTION_NONE;
   double alpha = 0.0, prev = 0.0;
+  int cycles = 0;
+  int kry = h->o.krylov;
   for (;;) {
     TRY(fine_residual(h, Ud, h->L[0].r, h->fp64,
                       h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized), 0));
@@ -1296,7 +1425,18 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
     nrm = std::sqrt(h->hscal[0]);
     rel = nrm / ref;
     if (ls && alpha > 0.0 && !(nrm <= (1.0 - 1e-4 * alpha) * prev)) {
-      if (alpha < kMinStep) { status = ST_ERR_DIVERGED; break; }
+      if (alpha < kMinStep) {
+        if (kry == 0 && h->o.krylov_fallback > 0) {
+          // the cycle's correction is no descent direction here: continue
+          // with Newton steps on the exact Jacobian solved by FGMRES
+          kry = h->o.krylov_fallback;
+          TRY(enable_exact_jacobian(h));
+          alpha = 0.0;
+          continue;
+        }
+        status = ST_ERR_DIVERGED;
+        break;
+      }
       launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream, -0.5 * alpha);
       CKL();
       alpha *= 0.5;
@@ -1311,7 +1451,18 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
       TRY(linearize_levels(h));
       h->linearized = true;
     }
-    TRY(cycle(h, 0));
+    if (kry > 0) {
+      int lits = 0;
+      const int s = krylov_step(h, kry, &lits);
+      cycles += lits;
+      if (s != ST_OK) {
+        status = s;
+        break;
+      }
+    } else {
+      TRY(cycle(h, 0));
+      ++cycles;
+    }
     launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
     CKL();
     prev = nrm;
@@ -1321,6 +1472,7 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
   TRY(stage_out(h, U, Ud));
   CK(cudaStreamSynchronize(h->stream));
   fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
+  if (info) info->cycles = cycles;
   return status;
 }
 

@@ -357,7 +357,7 @@ struct LinParams {
   T W[MAXM][MAXM];     // dt_l*Q (forward) or dt_l*Q^T (transpose)
   StencilC<T> sc;
   const T* e;          // may be null (= 0)
-  const T* r;
+  const T* r;          // may be null (= 0)
   const T* cbar;       // may be null (= 0)
   const T* cnode;      // forward only: R'(U) per node replacing cbar in A e (exact Jacobian; may be null)
   T* out;

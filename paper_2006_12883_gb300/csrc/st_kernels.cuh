@@ -1,6 +1,7 @@
 // Launcher declarations of the CUDA kernels (one translation unit per group).
 #pragma once
 
+#include <algorithm>
 #include <utility>
 
 #include "st_internal.cuh"
@@ -51,6 +52,24 @@ struct CoarseParams {
   T* Wfrow;                // [Nt][Nc][Nc]  rows of Wf at node M
   T* Wtrow;                // [Nt][Nc][Nc]  sum over nodes of Wt
 };
+
+// Coefficients of a multi-axpy (at most 32 vectors).
+struct KrylovCoef {
+  int k;
+  double c[32];
+};
+
+// k_krylov.cu
+// number of doubles the partial-sum buffer of launch_mdot needs for n values
+long long krylov_partials(long long n);
+// out[i] = <w, V_i> for i < k (device doubles), V_i = V + i*stride
+void launch_mdot(int fp64, const void* w, const void* V, long long stride, int k, long long n, double* partial,
+                 double* out, cudaStream_t st);
+// w -= sum_i c.c[i] V_i
+void launch_maxpy(int fp64, void* w, const void* V, long long stride, const KrylovCoef& c, long long n,
+                  cudaStream_t st);
+// y = a x + b y
+void launch_axpby(int fp64, void* y, const void* x, double a, double b, long long n, cudaStream_t st);
 
 // k_fine.cu
 long long residual_blocks(const ResidParams& p);

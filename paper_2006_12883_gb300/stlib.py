@@ -40,7 +40,8 @@ class StSolverOpts(ctypes.Structure):
                 ("tol", c_double), ("max_iters", c_int), ("newton", c_int), ("use_graphs", c_int),
                 ("use_pdl", c_int), ("smooth_inner_levels", c_int),
                 ("smooth_sweeps", c_int), ("line_search", c_int),
-                ("exact_jacobian", c_int)]
+                ("exact_jacobian", c_int), ("krylov", c_int), ("krylov_rtol", c_double),
+                ("krylov_fallback", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -54,12 +55,12 @@ class StRuntime(ctypes.Structure):
 class StSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", c_int), ("status", c_int), ("rel_residual", c_double),
                 ("abs_residual", c_double), ("ref_norm", c_double), ("seconds", c_double),
-                ("history_len", c_int), ("history", c_double * MAX_HISTORY)]
+                ("history_len", c_int), ("history", c_double * MAX_HISTORY), ("cycles", c_int)]
 
     def as_dict(self):
         return dict(iterations=self.iterations, status=self.status, rel_residual=self.rel_residual,
                     abs_residual=self.abs_residual, ref_norm=self.ref_norm, seconds=self.seconds,
-                    history=list(self.history[:self.history_len]))
+                    history=list(self.history[:self.history_len]), cycles=self.cycles)
 
 
 class StLevelInfo(ctypes.Structure):

@@ -224,3 +224,42 @@ def test_monodomain_with_line_search(ej):
     assert info2["status"] != 0 or info2["iterations"] >= info["iterations"]
     S.close()
     S2.close()
+
+
+# The paper's monodomain configurations of Section 5.4 (N_x = 1024, X = 10,
+# T = 2, gamma = 5) at the (M, N_t) pairs of its SMG table.  At these time
+# steps the cycle's quasi-Newton correction from the zero guess is no descent
+# direction; the solver continues with FGMRES on the exact Jacobian.
+@pytest.mark.parametrize("M,Nt", [(3, 32), (5, 8)])
+def test_monodomain_paper_configs(M, Nt):
+    from paper_2006_12883_gb300 import stlib
+    case = Case(f"monodomain_paper_m{M}", (1025,), space.NEUMANN, 1.0, Nt, M, T=2.0, X=10.0,
+                reaction=space.CUBIC, rho=5.0, u0_kind="stimulus")
+    S = case.solver(precision=stlib.FP64, tol=1e-11, max_iters=300)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0, info
+    assert info["cycles"] > info["iterations"]  # the Krylov steps took over
+    ref = _oracle_solution(case)
+    got = U.cpu().numpy().reshape(ref.shape)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    # the same with the Krylov steps requested from the start
+    S2 = case.solver(precision=stlib.FP64, tol=1e-11, max_iters=300, krylov=10, exact_jacobian=1)
+    U2 = S2.zeros()
+    assert S2.solve(U2)["status"] == 0
+    assert np.abs(U2.cpu().numpy().reshape(ref.shape) - ref).max() <= 1e-8 * np.abs(ref).max()
+    S.close()
+    S2.close()
+
+
+def test_krylov_step_on_linear_problem():
+    """For a linear problem FGMRES with the V-cycle preconditioner solves the
+    all-at-once system in one outer iteration to the Krylov tolerance."""
+    from paper_2006_12883_gb300 import stlib
+    case = HEAT1D
+    S = case.solver(precision=stlib.FP64, tol=1e-6, krylov=20, krylov_rtol=1e-8)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0 and info["iterations"] == 1, info
+    assert info["rel_residual"] <= 1e-7
+    S.close()
