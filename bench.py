@@ -427,6 +427,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's 1D examples (Section 5.3 heat, Eq. 5.1 data; Section 5.4
+# monodomain), N_x = 1024 (1025 vertices, Neumann), at the (M, N_t) pairs of
+# its SMG tables, with the iteration counts its single-core SMG run reports.
+PAPER_PAIRS = ((1, 1024), (2, 256), (3, 32), (4, 16), (5, 8))
+PAPER_ITERS = {"heat": (2, 4, 4, 5, 5), "monodomain": (16, 16, 16, 16, 58)}
+
+
+def run_paper_tables(args):
+    """One JSON line per (example, M, coarsening): Newton iterations and
+    V-cycles to the paper's tolerance 1e-9 (true collocation residual relative
+    to ||G(0)||, all-FP64 path), wall time of the solve, and for the heat
+    equation the max error against the fully discrete closed form
+    sum_k c_k R(dt rho_k)^Nt cos(k pi x) (R the Radau IIA stability function)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2006_12883_gb300.build import build
+    build()
+    import stgen
+    from paper_2006_12883_gb300 import stlib
+    n = 1025
+    for ex in ("heat", "monodomain"):
+        X, T, rx, rho = (1.0, 1.0, stlib.NONE, 0.0) if ex == "heat" else (10.0, 2.0, stlib.CUBIC, 5.0)
+        u0 = stgen.cosine_modes(n, X) if ex == "heat" else stgen.stimulus(n, X)
+        for (M, Nt), paper_it in zip(PAPER_PAIRS, PAPER_ITERS[ex]):
+            for cname, coarsening, levels in (("SMG7", stlib.COARSEN_SPACE, 7), ("auto", stlib.COARSEN_AUTO_MU, 32)):
+                S = stlib.Solver((n,), stlib.NEUMANN, 1.0, Nt, M, u0, T=T, X=X, reaction=rx, rho=rho,
+                                 opts=stlib.make_opts(precision=stlib.FP64, tol=1e-9, max_iters=1000,
+                                                      coarsening=coarsening, max_levels=levels))
+                U = S.zeros()
+                S.solve(U, raise_on_error=False)  # warm-up (graph capture)
+                U.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = S.solve(U, raise_on_error=False)
+                torch.cuda.synchronize()
+                secs = time.perf_counter() - t0
+                line = {"mode": "paper_tables", "example": ex, "M": M, "Nt": Nt, "Nx": n - 1,
+                        "coarsening": cname, "levels": S.num_levels(), "status": info["status"],
+                        "newton_iterations": info["iterations"], "vcycles": info["cycles"],
+                        "rel_residual": info["rel_residual"], "seconds": secs,
+                        "paper_smg_iterations_1core": paper_it}
+                if ex == "heat":
+                    x = stgen.coords1d(stlib.NEUMANN, n, X)
+                    h = X / (n - 1)
+                    tau, Q = stlib.st_collocation(M)[:2]
+                    Q = np.asarray(Q).reshape(M, M)
+                    dt = T / Nt
+
+                    def R(z):
+                        return 1.0 + z * (Q[-1] @ np.linalg.solve(np.eye(M) - z * Q, np.ones(M)))
+
+                    exact = sum(a * R(dt * (2 * np.cos(k * np.pi * h) - 2) / h ** 2) ** Nt * np.cos(k * np.pi * x)
+                                for k, a in ((1, 1.0), (3, 2.0), (4, 3.0)))
+                    line["max_err_vs_discrete_closed_form"] = float(np.abs(U[-1, -1].cpu().numpy() - exact).max())
+                print(json.dumps(line), flush=True)
+                S.close()
+                del U
+                torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,7 +499,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="warm-up and timed steps only (profiling)")
     ap.add_argument("--probe", action="store_true", help="launch each hot kernel alone (profiling)")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="the paper's 1D heat and monodomain examples at its (M, Nt) pairs (JSON lines)")
     args = ap.parse_args()
+    if args.paper_tables:
+        run_paper_tables(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -305,8 +305,15 @@ struct st_handle {
   double* plane = nullptr;  // staging for one plane (gT / target / du0)
   double* plane2 = nullptr;
   std::vector<Alloc> allocs;
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // 0 fwd cycle, 1 adjoint cycle, 2 linearise
-  size_t gnodes[3] = {0, 0, 0};
+  // 0 fwd cycle, 1 adjoint cycle, 2 linearise, 3 linearise + fwd cycle
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t gnodes[4] = {0, 0, 0, 0};
+  // second capture stream and events of the linearise + cycle graph: the
+  // cbar chain and the coarse setup run beside the cycle's finest levels
+  cudaStream_t cap2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_lvl[ST_MAX_LEVELS + 1] = {};
+  bool split_lin = false;  // set while that graph's cycle is enqueued
   long long D_total = 0;
   int chunk = 1;
 };
@@ -725,6 +732,7 @@ template <typename T>
 int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   Level& Lv = h->L[l];
   const int last = (int)h->L.size() - 1;
+  if (h->split_lin) CK(cudaStreamWaitEvent(st, h->ev_lvl[l == last ? last + 1 : l], 0));
   if (l == last) return coarse_solve<T>(h, adj, Lv.r, Lv.e, st);
   const int nu1 = h->o.nu1, nu2 = h->o.nu2;
   const long long n = Lv.g.Ns * Lv.Nt * h->p.M;
@@ -738,27 +746,33 @@ int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   return ST_OK;
 }
 
-// cbar of every level and inner level from level 0's, then the coarsest
-// blocks' inverses.
+// cbar of every level and of its inner levels, restricted from level 0's,
+// then the coarsest blocks' inverses.  With `ev` (the linearise + cycle
+// graph) only the inner levels the smoothers use are restricted, ev[l] is
+// recorded once level l's coefficients are ready and ev[L] after the coarse
+// setup.
 template <typename T>
-int enqueue_linearize(st_handle* h, cudaStream_t st) {
+int enqueue_linearize(st_handle* h, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const bool rx = h->p.reaction != ST_REACTION_NONE;
-  if (rx) {
-    for (size_t l = 0; l < h->L.size(); ++l) {
-      Level& Lv = h->L[l];
-      for (size_t k = 1; k < Lv.in.size(); ++k) {
+  const size_t L = h->L.size();
+  for (size_t l = 0; l < L; ++l) {
+    Level& Lv = h->L[l];
+    if (rx) {
+      const size_t kin = ev ? (size_t)Lv.smooth_depth : Lv.in.size();
+      for (size_t k = 1; k < kin; ++k) {
         launch_restrict_space<T>(h->D, Lv.in[k - 1].g, Lv.in[k].g, Lv.Nt, (const T*)Lv.in[k - 1].cbar,
                                  (T*)Lv.in[k].cbar, st);
         CKL();
       }
-      if (l + 1 < h->L.size()) {
-        Level& Lc = h->L[l + 1];
-        if (Lv.next == 1)
-          launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
-        else
-          launch_cbar_time<T>(Lv.g, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
-        CKL();
-      }
+    }
+    if (ev) CK(cudaEventRecord(ev[l], st));
+    if (rx && l + 1 < L) {
+      Level& Lc = h->L[l + 1];
+      if (Lv.next == 1)
+        launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+      else
+        launch_cbar_time<T>(Lv.g, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+      CKL();
     }
   }
   if (rx || !h->coarse_ready) {
@@ -766,6 +780,7 @@ int enqueue_linearize(st_handle* h, cudaStream_t st) {
     launch_coarse_setup<T>(cp, st);
     CKL();
   }
+  if (ev) CK(cudaEventRecord(ev[L], st));
   return ST_OK;
 }
 
@@ -807,10 +822,35 @@ template <typename T>
 int enq_cycle_adj(st_handle* h, cudaStream_t st) { return vcycle_level<T>(h, 0, 1, st); }
 template <typename T>
 int enq_lin(st_handle* h, cudaStream_t st) { return enqueue_linearize<T>(h, st); }
+// linearise on a forked branch, cycle on the main one, joined at the end
+template <typename T>
+int enq_lin_cycle(st_handle* h, cudaStream_t st) {
+  CK(cudaEventRecord(h->ev_fork, st));
+  CK(cudaStreamWaitEvent(h->cap2, h->ev_fork, 0));
+  TRY(enqueue_linearize<T>(h, h->cap2, h->ev_lvl));
+  h->split_lin = true;
+  const int s = vcycle_level<T>(h, 0, 0, st);
+  h->split_lin = false;
+  CK(cudaEventRecord(h->ev_join, h->cap2));
+  CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  return s;
+}
 
 int cycle(st_handle* h, int adj) {
   if (h->fp64) return run_graph(h, adj, adj ? enq_cycle_adj<double> : enq_cycle_fwd<double>);
   return run_graph(h, adj, adj ? enq_cycle_adj<float> : enq_cycle_fwd<float>);
+}
+
+// relinearise and run one forward cycle as one graph
+int lin_cycle(st_handle* h) {
+  if (!h->o.use_graphs || !h->cap2) {
+    TRY(h->fp64 ? run_graph(h, 2, enq_lin<double>) : run_graph(h, 2, enq_lin<float>));
+    h->coarse_ready = true;
+    return cycle(h, 0);
+  }
+  TRY(h->fp64 ? run_graph(h, 3, enq_lin_cycle<double>) : run_graph(h, 3, enq_lin_cycle<float>));
+  h->coarse_ready = true;
+  return ST_OK;
 }
 
 int linearize_levels(st_handle* h) {
@@ -820,7 +860,7 @@ int linearize_levels(st_handle* h) {
 }
 
 void invalidate_graphs(st_handle* h) {
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if (h->gexec[i]) {
       cudaGraphExecDestroy(h->gexec[i]);
       h->gexec[i] = nullptr;
@@ -943,10 +983,11 @@ int outer_step(st_handle* h, double* Ud, bool do_cycle) {
   TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0));
   if (!do_cycle) return ST_OK;
   if (relin || !h->coarse_ready) {
-    TRY(linearize_levels(h));
+    TRY(lin_cycle(h));
     h->linearized = true;
+  } else {
+    TRY(cycle(h, 0));
   }
-  TRY(cycle(h, 0));
   launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
   CKL();
   return ST_OK;
@@ -1183,9 +1224,20 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   };
   if (colloc_setup(pin->M, &h->col) != 0) return fail(ST_ERR_UNSUPPORTED);
   build_transforms(h);
-  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking) != cudaSuccess) {
     set_err(cudaGetLastError(), "cudaStreamCreate");
     return fail(ST_ERR_CUDA);
+  }
+  {
+    bool ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l <= ST_MAX_LEVELS && ok; ++l)
+      ok = cudaEventCreateWithFlags(&h->ev_lvl[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      set_err(cudaGetLastError(), "cudaEventCreate");
+      return fail(ST_ERR_CUDA);
+    }
   }
   const int M = pin->M;
   const bool rx = pin->reaction != ST_REACTION_NONE;
@@ -1335,6 +1387,11 @@ void st_destroy(st_handle* h) {
   cudaStreamSynchronize(h->stream);
   if (h->hscal) cudaFreeHost(h->hscal);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap2) cudaStreamDestroy(h->cap2);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (int l = 0; l <= ST_MAX_LEVELS; ++l)
+    if (h->ev_lvl[l]) cudaEventDestroy(h->ev_lvl[l]);
   cudaGetLastError();
   delete h;
 }
@@ -1447,7 +1504,13 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
     if (rel <= h->o.tol) { status = ST_OK; break; }
     if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
     const bool relin = h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized);
-    if (relin || !h->coarse_ready) {
+    bool did_cycle = false;
+    if (kry == 0 && (relin || !h->coarse_ready)) {
+      TRY(lin_cycle(h));
+      h->linearized = true;
+      did_cycle = true;
+      ++cycles;
+    } else if (relin || !h->coarse_ready) {
       TRY(linearize_levels(h));
       h->linearized = true;
     }
@@ -1459,7 +1522,7 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
         status = s;
         break;
       }
-    } else {
+    } else if (!did_cycle) {
       TRY(cycle(h, 0));
       ++cycles;
     }
@@ -1875,8 +1938,12 @@ int st_stats(st_handle* h, st_stats_info* out) {
   out->cycle_graph_nodes = (int)h->gnodes[0];
   out->linearize_graph_nodes = (int)h->gnodes[2];
   const bool rx = h->p.reaction != ST_REACTION_NONE;
-  // fine residual + partial sum + update, plus the graphs
-  out->launches_per_vcycle = 3 + (int)h->gnodes[0] + ((rx && h->o.newton) ? (int)h->gnodes[2] : 0);
+  // fine residual + partial sum + update, plus the graph(s) of one st_vcycle
+  // (the linearise + cycle graph holds a few event nodes besides its kernels)
+  if (rx && h->o.newton && h->gexec[3])
+    out->launches_per_vcycle = 3 + (int)h->gnodes[3];
+  else
+    out->launches_per_vcycle = 3 + (int)h->gnodes[0] + ((rx && h->o.newton) ? (int)h->gnodes[2] : 0);
   return ST_OK;
 }
 

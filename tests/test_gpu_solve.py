@@ -263,3 +263,29 @@ def test_krylov_step_on_linear_problem():
     assert info["status"] == 0 and info["iterations"] == 1, info
     assert info["rel_residual"] <= 1e-7
     S.close()
+
+
+@pytest.mark.parametrize("M,Nt", [(1, 1024), (2, 256), (3, 32), (4, 16), (5, 8)])
+def test_heat_paper_configs_closed_form(M, Nt):
+    """The paper's heat example (Section 5.3, Eq. 5.1 data, N_x = 1024,
+    Neumann) at its (M, N_t) pairs: the cosine modes are exact eigenvectors of
+    the mirrored-ghost Laplacian with eigenvalues rho_k (Eq. 5.3), so the
+    fully discrete end value is sum_k c_k R(dt rho_k)^Nt cos(k pi x) with R the
+    Radau IIA stability function, up to rounding."""
+    from oracle import collocation as col
+    from paper_2006_12883_gb300 import stlib
+    n = 1025
+    case = Case(f"heat_paper_m{M}", (n,), space.NEUMANN, 1.0, Nt, M, u0_kind="cosine")
+    S = case.solver(precision=stlib.FP64, tol=1e-10, max_iters=200, coarsening=stlib.COARSEN_SPACE, max_levels=7)
+    U = S.zeros()
+    info = S.solve(U)
+    assert info["status"] == 0, info
+    Q = col.collocation_matrix(col.radau_right_nodes(M))
+    x = stgen.coords1d(space.NEUMANN, n)
+    h = 1.0 / (n - 1)
+    dt = 1.0 / Nt
+    exact = sum(a * col.stability_function(dt * (2 * np.cos(k * np.pi * h) - 2) / h ** 2, Q).real ** Nt
+                * np.cos(k * np.pi * x) for k, a in ((1, 1.0), (3, 2.0), (4, 3.0)))
+    # u(T) has decayed to about 5e-5 (e^{-pi^2}) of u0; compare relative to it
+    assert np.abs(U[-1, -1].cpu().numpy() - exact).max() <= 1e-5 * np.abs(exact).max()
+    S.close()
