@@ -69,7 +69,7 @@ PER2D_M5 = Case("periodic2d_m5", (16, 24), P_, 0.02, 4, 5, reaction=C_, rho=1.0)
 PER3D_M5 = Case("periodic3d_m5", (4, 8, 8), P_, 0.01, 4, 5, reaction=L_, rho=1.0)
 # 2D periodic, M = 5, runs of 4 slabs with a ragged last run (the 4-point
 # double-float residual at M = 5)
-TILED_M5 = Case("tiled2d_m5", (32, 64), P_, 0.02, 10, 5, reaction=C_, rho=1.0, u0_kind="noise", seed=9)
+TILED_M5 = Case("periodic2d_m5_runs", (32, 64), P_, 0.02, 10, 5, reaction=C_, rho=1.0, u0_kind="noise", seed=9)
 
 RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5]
 SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5]
