@@ -1935,8 +1935,9 @@ int st_stats(st_handle* h, st_stats_info* out) {
   PdlScope pdl_scope(h);
   if (!h || !out) return ST_ERR_INVALID_ARG;
   out->levels = (int)h->L.size();
-  out->cycle_graph_nodes = (int)h->gnodes[0];
-  out->linearize_graph_nodes = (int)h->gnodes[2];
+  // the relinearise + cycle graph replaces both when it has been built
+  out->cycle_graph_nodes = (int)(h->gexec[3] ? h->gnodes[3] : h->gnodes[0]);
+  out->linearize_graph_nodes = (int)(h->gexec[3] ? 0 : h->gnodes[2]);
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   // fine residual + partial sum + update, plus the graph(s) of one st_vcycle
   // (the linearise + cycle graph holds a few event nodes besides its kernels)
