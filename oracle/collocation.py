@@ -162,6 +162,23 @@ def time_restriction(tau: np.ndarray) -> np.ndarray:
     return np.linalg.solve(K, Pt.T @ np.kron(np.eye(2), K))
 
 
+def node_prolongation(tau_f: np.ndarray, tau_c: np.ndarray) -> np.ndarray:
+    """P_M (M_f x M_c): the coarse slab's nodal polynomial (Lagrange basis on
+    the M_c coarse nodes) evaluated at the M_f fine nodes -- the interpolation
+    between node sets of the M-coarsening of Section 5.2 (SMMG), same slab."""
+    ls = lagrange_basis(tau_c)
+    return np.array([[l(t) for l in ls] for t in tau_f])
+
+
+def node_restriction(tau_f: np.ndarray, tau_c: np.ndarray) -> np.ndarray:
+    """R_M (M_c x M_f) for collocation-form residuals: the DG system restricted
+    with P_M^T (Eq. 4.1), written for collocation residuals exactly as the
+    slab-bisection restriction is, R_M = K_c^{-1} P_M^T K_f."""
+    Kf, _, _ = dg_matrices(tau_f)
+    Kc, _, _ = dg_matrices(tau_c)
+    return np.linalg.solve(Kc, node_prolongation(tau_f, tau_c).T @ Kf)
+
+
 def sdc_qdelta(tau: np.ndarray, kind: str = "IE"):
     """Lower-triangular SDC preconditioners (Section 4.1).
 

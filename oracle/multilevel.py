@@ -192,6 +192,18 @@ def prolong_space(bc: int, shape, v: np.ndarray) -> np.ndarray:
     return (P @ v.reshape(-1, v.shape[-1]).T).T.reshape(*lead, P.shape[0])
 
 
+def restrict_nodes(Mf: int, Mc: int, v: np.ndarray) -> np.ndarray:
+    """M-coarsening restriction of every (slab, point): (Nt, Mf, Ns) -> (Nt, Mc, Ns)."""
+    R = col.node_restriction(col.radau_right_nodes(Mf), col.radau_right_nodes(Mc))
+    return np.einsum("cf,nfs->ncs", R, v)
+
+
+def prolong_nodes(Mf: int, Mc: int, v: np.ndarray) -> np.ndarray:
+    """(Nt, Mc, Ns) -> (Nt, Mf, Ns) with P_M."""
+    P = col.node_prolongation(col.radau_right_nodes(Mf), col.radau_right_nodes(Mc))
+    return np.einsum("fc,ncs->nfs", P, v)
+
+
 def restrict_time(M: int, v: np.ndarray) -> np.ndarray:
     """Slab bisection restriction: (Nt, M, Ns) -> (Nt/2, M, Ns) with R_t."""
     Nt, _, Ns = v.shape

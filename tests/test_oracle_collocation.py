@@ -168,3 +168,36 @@ def test_sdc_qdelta(kind, M):
         assert np.allclose(np.triu(Lm, 1), 0, atol=1e-13)
     # explicit Euler from node j to node j+1 (strictly lower; row sums tau - tau_1)
     assert np.abs(QE.sum(axis=1) - (tau - tau[0])).max() < 1e-15
+
+
+# ---------------------------------------------------------------- M-coarsening
+
+@pytest.mark.parametrize("Mf,Mc", [(2, 1), (3, 2), (4, 3), (5, 4), (5, 2), (3, 1)])
+def test_node_prolongation_interpolates_polynomials(Mf, Mc):
+    """P_M reproduces every polynomial of degree < M_c from its coarse node
+    values, and keeps the slab-end node (tau = 1 is a node of both sets)."""
+    tf, tc = col.radau_right_nodes(Mf), col.radau_right_nodes(Mc)
+    P = col.node_prolongation(tf, tc)
+    for deg in range(Mc):
+        assert np.abs(P @ tc ** deg - tf ** deg).max() < 1e-13
+    assert np.abs(P[-1] - np.eye(Mc)[-1]).max() < 1e-14
+
+
+@pytest.mark.parametrize("Mf,Mc", [(2, 1), (3, 2), (4, 3), (5, 4), (5, 2), (3, 1)])
+def test_node_restriction_is_left_inverse(Mf, Mc):
+    """The coarse polynomials are a subspace of the fine ones and the DG form
+    is integrated exactly, so P^T K_f P = K_c and R_M P_M = I."""
+    tf, tc = col.radau_right_nodes(Mf), col.radau_right_nodes(Mc)
+    P = col.node_prolongation(tf, tc)
+    Kf, _, _ = col.dg_matrices(tf)
+    Kc, _, _ = col.dg_matrices(tc)
+    assert np.abs(P.T @ Kf @ P - Kc).max() < 1e-12
+    assert np.abs(col.node_restriction(tf, tc) @ P - np.eye(Mc)).max() < 1e-12
+
+
+@pytest.mark.parametrize("Mf", [2, 3, 5])
+def test_node_restriction_to_one_node_takes_the_last_residual(Mf):
+    """M_c = 1: K_c = 1 and the column sums of K_f are l_j(1) = delta_{jM}
+    (sum_i l_i = 1), so R_M = e_M^T."""
+    R = col.node_restriction(col.radau_right_nodes(Mf), col.radau_right_nodes(1))
+    assert np.abs(R - np.eye(Mf)[-1:]).max() < 1e-12
