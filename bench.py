@@ -432,6 +432,7 @@ def run_reference(args):
 # its SMG tables, with the iteration counts its single-core SMG run reports.
 PAPER_PAIRS = ((1, 1024), (2, 256), (3, 32), (4, 16), (5, 8))
 PAPER_ITERS = {"heat": (2, 4, 4, 5, 5), "monodomain": (16, 16, 16, 16, 58)}
+PAPER_SMMG_ITERS = {"heat": (None, 12, 17, 15, 18)}
 
 
 def run_paper_tables(args):
@@ -452,7 +453,10 @@ def run_paper_tables(args):
         X, T, rx, rho = (1.0, 1.0, stlib.NONE, 0.0) if ex == "heat" else (10.0, 2.0, stlib.CUBIC, 5.0)
         u0 = stgen.cosine_modes(n, X) if ex == "heat" else stgen.stimulus(n, X)
         for (M, Nt), paper_it in zip(PAPER_PAIRS, PAPER_ITERS[ex]):
-            for cname, coarsening, levels in (("SMG7", stlib.COARSEN_SPACE, 7), ("auto", stlib.COARSEN_AUTO_MU, 32)):
+            for cname, coarsening, levels in (("SMG7", stlib.COARSEN_SPACE, 7), ("SMMG7", stlib.COARSEN_SPACE_NODES, 7),
+                                              ("auto", stlib.COARSEN_AUTO_MU, 32)):
+                if cname == "SMMG7" and M == 1:
+                    continue  # the same hierarchy as SMG7
                 S = stlib.Solver((n,), stlib.NEUMANN, 1.0, Nt, M, u0, T=T, X=X, reaction=rx, rho=rho,
                                  opts=stlib.make_opts(precision=stlib.FP64, tol=1e-9, max_iters=1000,
                                                       coarsening=coarsening, max_levels=levels))
@@ -469,6 +473,8 @@ def run_paper_tables(args):
                         "newton_iterations": info["iterations"], "vcycles": info["cycles"],
                         "rel_residual": info["rel_residual"], "seconds": secs,
                         "paper_smg_iterations_1core": paper_it}
+                if cname == "SMMG7" and ex in PAPER_SMMG_ITERS:
+                    line["paper_smmg_iterations_1core"] = PAPER_SMMG_ITERS[ex][PAPER_PAIRS.index((M, Nt))]
                 if ex == "heat":
                     x = stgen.coords1d(stlib.NEUMANN, n, X)
                     h = X / (n - 1)

@@ -65,7 +65,11 @@ enum { ST_PREC_FP64 = 0, ST_PREC_FP32_REFINE = 1 };
 /* Level hierarchy of Eq. (4.1): SPACE = SMG (space bisection only, Section
  * 5.2); AUTO_MU = per level, bisect space if mu_l = nu*dt_l/h_l^2 >= mu_crit,
  * else bisect the slabs (the mu rule of Section 4.2). */
-enum { ST_COARSEN_SPACE = 0, ST_COARSEN_AUTO_MU = 1 };
+/* SPACE: space bisection only (the paper's SMG); AUTO_MU: space bisection while
+ * mu_l = nu dt_l / h_l^2 >= mu_crit, slab bisection otherwise (STMG with the mu
+ * rule); SPACE_NODES: space bisection with one collocation node fewer per
+ * level until M = 1 (the paper's SMMG, Section 5.2). */
+enum { ST_COARSEN_SPACE = 0, ST_COARSEN_AUTO_MU = 1, ST_COARSEN_SPACE_NODES = 2 };
 /* SDC lower-triangular preconditioner: implicit Euler node to node, or the
  * LU trick (Q^T = L U, QI = U^T). */
 enum { ST_SDC_IE = 0, ST_SDC_LU = 1 };
@@ -175,9 +179,11 @@ typedef struct {
   long long Ns;       /* points per plane */
   int Nt;             /* slabs */
   double dt, h[3], mu;
-  int next_kind;      /* 0 coarsest, 1 space bisection, 2 slab bisection */
+  int next_kind;      /* 0 coarsest, 1 space bisection, 2 slab bisection,
+                         3 space bisection and one node fewer */
   double omega;       /* damping used on this level */
   int inner_levels;   /* spatial multigrid depth of the slab solves */
+  int M;              /* collocation nodes per slab on this level */
 } st_level_info;
 
 typedef struct {
@@ -283,6 +289,12 @@ int st_collocation(int M, double* tau, double* Q, double* lam, double* V, double
  * (M x 2M), row major (Eq. 4.1; the restriction acts through the DG form,
  * R_t = K^{-1} P_t^T blockdiag(K, K)). */
 int st_time_transfer(int M, double* Pt, double* Rt);
+
+/* M-coarsening transfers between the node sets of one slab (SMMG of Section
+ * 5.2): P_M (Mf x Mc) evaluates the coarse nodal polynomial at the fine
+ * nodes, R_M (Mc x Mf) = K_c^{-1} P_M^T K_f restricts collocation-form
+ * residuals; row major.  ST_ERR_INVALID_ARG unless 1 <= Mc <= Mf <= 5. */
+int st_node_transfer(int Mf, int Mc, double* P, double* R);
 
 int st_num_levels(const st_handle* h);
 int st_level_info_get(const st_handle* h, int level, st_level_info* out);

@@ -620,6 +620,43 @@ void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st
   st_launch(k_cbar_time<T>, nblk(g.Ns * Ntc, 256), 256, 0, st, g, Ntc, f, c);
 }
 
+// Node-set transfer of every (slab, point): out[n][a][s] = sum_b X[a][b] in[n][b][s]
+// (X: Mo x Mi), optionally added to out (M-coarsening of SMMG).
+template <typename T>
+struct NodeX {
+  T x[MAXM][MAXM];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_node_transfer(long long Ns, int Nt, int Mi, int Mo, NodeX<T> X,
+                                                       const T* __restrict__ in, T* __restrict__ out, int add) {
+  grid_dep_wait();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * Nt) return;
+  const long long n = idx / Ns, s = idx - n * Ns;
+  T v[MAXM];
+#pragma unroll
+  for (int b = 0; b < MAXM; ++b) v[b] = (b < Mi) ? in[(n * Mi + b) * Ns + s] : (T)0;
+#pragma unroll
+  for (int a = 0; a < MAXM; ++a) {
+    if (a < Mo) {
+      T acc = add ? out[(n * Mo + a) * Ns + s] : (T)0;
+#pragma unroll
+      for (int b = 0; b < MAXM; ++b) acc = fma(X.x[a][b], v[b], acc);
+      out[(n * Mo + a) * Ns + s] = acc;
+    }
+  }
+}
+
+template <typename T>
+void launch_node_transfer(long long Ns, int Nt, int Mi, int Mo, const double X[MAXM][MAXM], const T* in, T* out,
+                          int add, cudaStream_t st) {
+  NodeX<T> x;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) x.x[a][b] = (a < Mo && b < Mi) ? (T)X[a][b] : (T)0;
+  st_launch(k_node_transfer<T>, nblk(Ns * Nt, 256), 256, 0, st, Ns, Nt, Mi, Mo, x, in, out, add);
+}
+
 #define INST(T)                                                                                     \
   template void launch_lin_residual<T>(int, const LinParams<T>&, cudaStream_t);                    \
   template void launch_backtransform<T>(const GridP&, int, int, const T[MAXM][MAXM], T, int, const T*, \
@@ -637,7 +674,9 @@ void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st
                                         const T*, T*, cudaStream_t);                               \
   template void launch_prolong_time_add<T>(const GridP&, int, int, const double[2 * MAXM][MAXM],   \
                                            const T*, T*, cudaStream_t);                            \
-  template void launch_cbar_time<T>(const GridP&, int, const T*, T*, cudaStream_t);
+  template void launch_cbar_time<T>(const GridP&, int, const T*, T*, cudaStream_t);                \
+  template void launch_node_transfer<T>(long long, int, int, int, const double[MAXM][MAXM], const T*, T*, \
+                                        int, cudaStream_t);
 
 INST(float)
 INST(double)

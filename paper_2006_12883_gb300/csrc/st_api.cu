@@ -49,11 +49,31 @@ struct InnerLev {
   void* cbar = nullptr;
 };
 
+// The collocation data of one node count: Q and its eigenbasis, the real
+// forward / back transforms of the Q-diagonalised slab solve (forward and
+// adjoint), the shift groups, and the slab-bisection transfers.
+struct NodeSet {
+  int M = 0;
+  Colloc col;
+  int ngroups = 0;
+  int gplane[MAXM], gcplx[MAXM];
+  std::complex<double> glam[MAXM];
+  double Ff[MAXM][MAXM], Bf[MAXM][MAXM], Fa[MAXM][MAXM], Ba[MAXM][MAXM];
+  double RtT[MAXM][2 * MAXM];  // P_t^T (adjoint restriction)
+  double PtT[2 * MAXM][MAXM];  // R_t^T (adjoint prolongation)
+};
+
 struct Level {
   GridP g;
   int Nt = 0;
+  int M = 1;                    // collocation nodes per slab on this level
+  const NodeSet* ns = nullptr;  // their collocation data
   double dt = 0, mu = 0, omega = 1;
-  int next = 0;  // 0 coarsest, 1 space, 2 slabs
+  int next = 0;  // 0 coarsest, 1 space, 2 slabs, 3 space and nodes (M -> M-1)
+  // next == 3: node-set transfers to the coarser level (P: M x Mc, R: Mc x M)
+  // and their transposes (adjoint), and a buffer of M planes on the coarse grid
+  double Pn[MAXM][MAXM], Rn[MAXM][MAXM], PnT[MAXM][MAXM], RnT[MAXM][MAXM];
+  void* tmp = nullptr;
   int bottom_sweeps = 2;
   // depth of the inner multigrid the block-Jacobi smoother uses, and the
   // Jacobi sweeps at its bottom
@@ -112,6 +132,7 @@ const int kCoarseKMax = 96;        // largest dense slab block M*Nc
 struct PlanLevel {
   GridP g;
   int Nt;
+  int M;
   double dt, mu, omega;
   int next;
   std::vector<GridP> inner;
@@ -174,7 +195,9 @@ int validate(const st_problem* p, const st_solver_opts* o) {
   }
   if (o) {
     if (o->precision != ST_PREC_FP64 && o->precision != ST_PREC_FP32_REFINE) return ST_ERR_INVALID_ARG;
-    if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU) return ST_ERR_INVALID_ARG;
+    if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU &&
+        o->coarsening != ST_COARSEN_SPACE_NODES)
+      return ST_ERR_INVALID_ARG;
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) return ST_ERR_INVALID_ARG;
     if (o->inner_cycles < 1 || o->inner_smooth < 1 || o->inner_coarse_iters < 1) return ST_ERR_INVALID_ARG;
     if (o->smooth_inner_levels < 0 || o->smooth_sweeps < 2) return ST_ERR_INVALID_ARG;
@@ -193,6 +216,7 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
   PlanLevel L0;
   L0.g = make_grid(d, p->n, p->bc, p->X);
   L0.Nt = p->Nt;
+  L0.M = p->M;
   L0.dt = p->T / p->Nt;
   out.push_back(L0);
   const int maxl = std::min(o.max_levels, ST_MAX_LEVELS);
@@ -209,6 +233,8 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     int kind = 0;
     if (o.coarsening == ST_COARSEN_SPACE) {
       if (cs && cur.g.Ns > o.coarse_max_points) kind = 1;
+    } else if (o.coarsening == ST_COARSEN_SPACE_NODES) {
+      if (cs && cur.g.Ns > o.coarse_max_points) kind = cur.M > 1 ? 3 : 1;
     } else {
       const bool small_s = cur.g.Ns <= o.coarse_max_points;
       const bool small_t = cur.Nt <= o.coarse_max_slabs;
@@ -221,7 +247,8 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     PlanLevel nx;
     nx.Nt = cur.Nt;
     nx.dt = cur.dt;
-    if (kind == 1) {
+    nx.M = kind == 3 ? cur.M - 1 : cur.M;
+    if (kind == 1 || kind == 3) {
       nx.g = coarsen(d, cur.g, p->X);
     } else {
       nx.g = cur.g;
@@ -232,9 +259,9 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     out.push_back(nx);
   }
   out.back().next = 0;
-  const double lmax = max_shift(p->M);
   const double wj = d == 1 ? 2.0 / 3.0 : (d == 2 ? 0.8 : 6.0 / 7.0);
   for (auto& L : out) {
+    const double lmax = max_shift(L.M);
     L.mu = p->nu * L.dt * L.g.ih2[0];
     L.omega = default_omega(o, L.mu);
     L.inner.clear();
@@ -247,7 +274,7 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     const double rho = std::max(1e-3, 1.0 - wj / (1.0 + sig));
     L.bottom_sweeps = std::max(2, std::min(o.inner_coarse_iters, (int)std::ceil(std::log(0.05) / std::log(rho))));
   }
-  if (out.back().g.Ns * p->M > kCoarseKMax) return ST_ERR_UNSUPPORTED;
+  if (out.back().g.Ns * out.back().M > kCoarseKMax) return ST_ERR_UNSUPPORTED;
   return ST_OK;
 }
 
@@ -269,14 +296,9 @@ struct st_handle {
   cudaStream_t cap = nullptr;
   int D = 1, fp64 = 0;
   size_t esz = 4;
-  Colloc col;
-  // shift groups of the Q-eigenbasis (real planes / complex pairs)
-  int ngroups = 0;
-  int gplane[MAXM], gcplx[MAXM];
-  std::complex<double> glam[MAXM];
-  double Ff[MAXM][MAXM], Bf[MAXM][MAXM], Fa[MAXM][MAXM], Ba[MAXM][MAXM];
-  double RtT[MAXM][2 * MAXM];  // P_t^T (adjoint restriction)
-  double PtT[2 * MAXM][MAXM];  // R_t^T (adjoint prolongation)
+  // collocation data per node count (index M); the finest level's is `fine`
+  NodeSet ns[MAXM + 1];
+  const NodeSet* fine = nullptr;
   std::vector<Level> L;
   // coarsest level
   int Nc = 0, K = 0;
@@ -366,71 +388,71 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-void build_transforms(st_handle* h) {
-  const int M = h->p.M;
-  const Colloc& c = h->col;
+void build_nodeset(NodeSet& s, int M) {
+  s.M = M;
+  const Colloc& c = s.col;
   // groups
-  h->ngroups = 0;
+  s.ngroups = 0;
   for (int q = 0; q < M;) {
-    h->gplane[h->ngroups] = q;
-    h->glam[h->ngroups] = c.lam[q];
+    s.gplane[s.ngroups] = q;
+    s.glam[s.ngroups] = c.lam[q];
     if (c.lam[q].imag() == 0.0) {
-      h->gcplx[h->ngroups] = 0;
+      s.gcplx[s.ngroups] = 0;
       ++q;
     } else {
-      h->gcplx[h->ngroups] = 1;
+      s.gcplx[s.ngroups] = 1;
       q += 2;
     }
-    ++h->ngroups;
+    ++s.ngroups;
   }
   // forward (Q = V L V^-1): y = Vinv res, e += Re(V z);
   // adjoint (Q^T = W L W^-1 with W = V^{-T}, W^{-1} = V^T)
   for (int a = 0; a < MAXM; ++a)
-    for (int b = 0; b < MAXM; ++b) h->Ff[a][b] = h->Bf[a][b] = h->Fa[a][b] = h->Ba[a][b] = 0;
-  for (int gq = 0; gq < h->ngroups; ++gq) {
-    const int p = h->gplane[gq];
+    for (int b = 0; b < MAXM; ++b) s.Ff[a][b] = s.Bf[a][b] = s.Fa[a][b] = s.Ba[a][b] = 0;
+  for (int gq = 0; gq < s.ngroups; ++gq) {
+    const int p = s.gplane[gq];
     for (int j = 0; j < M; ++j) {
       const std::complex<double> fi = c.Vinv[p][j];   // forward row p of V^-1
       const std::complex<double> ai = c.V[j][p];      // adjoint row p of V^T
       const std::complex<double> fb = c.V[j][p];      // forward back-transform
       const std::complex<double> ab = c.Vinv[p][j];   // adjoint back: (V^{-T})[j][p] = Vinv[p][j]
-      if (!h->gcplx[gq]) {
-        h->Ff[p][j] = fi.real();
-        h->Fa[p][j] = ai.real();
-        h->Bf[j][p] = fb.real();
-        h->Ba[j][p] = ab.real();
+      if (!s.gcplx[gq]) {
+        s.Ff[p][j] = fi.real();
+        s.Fa[p][j] = ai.real();
+        s.Bf[j][p] = fb.real();
+        s.Ba[j][p] = ab.real();
       } else {
-        h->Ff[p][j] = fi.real();
-        h->Ff[p + 1][j] = fi.imag();
-        h->Fa[p][j] = ai.real();
-        h->Fa[p + 1][j] = ai.imag();
-        h->Bf[j][p] = 2 * fb.real();
-        h->Bf[j][p + 1] = -2 * fb.imag();
-        h->Ba[j][p] = 2 * ab.real();
-        h->Ba[j][p + 1] = -2 * ab.imag();
+        s.Ff[p][j] = fi.real();
+        s.Ff[p + 1][j] = fi.imag();
+        s.Fa[p][j] = ai.real();
+        s.Fa[p + 1][j] = ai.imag();
+        s.Bf[j][p] = 2 * fb.real();
+        s.Bf[j][p + 1] = -2 * fb.imag();
+        s.Ba[j][p] = 2 * ab.real();
+        s.Ba[j][p + 1] = -2 * ab.imag();
       }
     }
   }
   for (int m = 0; m < MAXM; ++m)
     for (int kk = 0; kk < 2 * MAXM; ++kk) {
-      h->RtT[m][kk] = (m < M && kk < 2 * M) ? c.Pt[kk][m] : 0.0;
-      h->PtT[kk][m] = (m < M && kk < 2 * M) ? c.Rt[m][kk] : 0.0;
+      s.RtT[m][kk] = (m < M && kk < 2 * M) ? c.Pt[kk][m] : 0.0;
+      s.PtT[kk][m] = (m < M && kk < 2 * M) ? c.Rt[m][kk] : 0.0;
     }
 }
 
 template <typename T>
-Shifts<T> level_shifts(const st_handle* h, double dt) {
+Shifts<T> level_shifts(const NodeSet& h, double dt) {
   Shifts<T> s;
   for (int p = 0; p < MAXM; ++p) {
     s.kind[p] = SH_NONE;
     s.sr[p] = s.si[p] = (T)0;
   }
-  for (int q = 0; q < h->ngroups; ++q) {
-    const int p = h->gplane[q];
-    s.kind[p] = h->gcplx[q] ? SH_RE : SH_REAL;
-    if (h->gcplx[q]) s.kind[p + 1] = SH_IM;
-    s.sr[p] = (T)(dt * h->glam[q].real());
-    s.si[p] = (T)(dt * h->glam[q].imag());
+  for (int q = 0; q < h.ngroups; ++q) {
+    const int p = h.gplane[q];
+    s.kind[p] = h.gcplx[q] ? SH_RE : SH_REAL;
+    if (h.gcplx[q]) s.kind[p + 1] = SH_IM;
+    s.sr[p] = (T)(dt * h.glam[q].real());
+    s.si[p] = (T)(dt * h.glam[q].imag());
   }
   return s;
 }
@@ -603,19 +625,19 @@ LinParams<T> lin_params(st_handle* h, const Level& Lv, int adj) {
   LinParams<T> lp;
   lp.g = Lv.g;
   lp.Nt = Lv.Nt;
-  lp.M = h->p.M;
+  lp.M = Lv.M;
   lp.chunk = (Lv.g.Ns >= 4096 && Lv.Nt >= 8) ? 4 : 1;
   lp.transpose = adj;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) {
-      const double q = (a < h->p.M && b < h->p.M) ? (adj ? h->col.Q[b][a] : h->col.Q[a][b]) : 0.0;
+      const double q = (a < Lv.M && b < Lv.M) ? (adj ? Lv.ns->col.Q[b][a] : Lv.ns->col.Q[a][b]) : 0.0;
       lp.W[a][b] = (T)(Lv.dt * q);
-      lp.F[a][b] = (T)(adj ? h->Fa[a][b] : h->Ff[a][b]);
+      lp.F[a][b] = (T)(adj ? Lv.ns->Fa[a][b] : Lv.ns->Ff[a][b]);
     }
   lp.sc = stencil_of<T>(Lv.g, h->p.nu);
   lp.nchunks = (Lv.Nt + lp.chunk - 1) / lp.chunk;
   lp.zout = nullptr;
-  lp.sh = level_shifts<T>(h, Lv.dt);
+  lp.sh = level_shifts<T>(*Lv.ns, Lv.dt);
   lp.omega_j = (T)jacobi_weight(h->D);
   lp.e = nullptr;
   lp.r = nullptr;
@@ -644,7 +666,7 @@ int level_residual(st_handle* h, int l, int adj, const void* e, const void* r, v
 template <typename T>
 int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   Level& Lv = h->L[l];
-  const int M = h->p.M;
+  const int M = Lv.M;
   const bool multi = !(Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit);
   {
     // residual + Q-eigenbasis transform (+ zero-start Jacobi of the slab systems)
@@ -664,8 +686,8 @@ int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   f.omega = (T)Lv.omega;
   f.e = (T*)Lv.e;
   for (int a = 0; a < MAXM; ++a)
-    for (int b = 0; b < MAXM; ++b) f.B[a][b] = (T)(adj ? h->Ba[a][b] : h->Bf[a][b]);
-  TRY(inner_solve<T>(h, Lv, Lv.smooth_depth, Lv.smooth_sweeps, M, level_shifts<T>(h, Lv.dt), use_cbar,
+    for (int b = 0; b < MAXM; ++b) f.B[a][b] = (T)(adj ? Lv.ns->Ba[a][b] : Lv.ns->Bf[a][b]);
+  TRY(inner_solve<T>(h, Lv, Lv.smooth_depth, Lv.smooth_sweeps, M, level_shifts<T>(*Lv.ns, Lv.dt), use_cbar,
                      h->o.inner_cycles, multi, &f, st));
   return ST_OK;
 }
@@ -674,11 +696,16 @@ template <typename T>
 int restrict_level(st_handle* h, int l, int adj, const void* fine, void* coarse, cudaStream_t st) {
   Level& Lv = h->L[l];
   Level& Lc = h->L[l + 1];
-  const int M = h->p.M;
+  const int M = Lv.M;
   if (Lv.next == 1) {
     launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)coarse, st);
+  } else if (Lv.next == 3) {
+    // full weighting of every node plane, then the node-set restriction
+    launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)Lv.tmp, st);
+    CKL();
+    launch_node_transfer<T>(Lc.g.Ns, Lc.Nt, M, Lc.M, adj ? Lv.PnT : Lv.Rn, (const T*)Lv.tmp, (T*)coarse, 0, st);
   } else {
-    launch_restrict_time<T>(Lv.g, Lc.Nt, M, adj ? h->RtT : h->col.Rt, (const T*)fine, (T*)coarse, st);
+    launch_restrict_time<T>(Lv.g, Lc.Nt, M, adj ? Lv.ns->RtT : Lv.ns->col.Rt, (const T*)fine, (T*)coarse, st);
   }
   CKL();
   return ST_OK;
@@ -688,11 +715,16 @@ template <typename T>
 int prolong_level(st_handle* h, int l, int adj, const void* coarse, void* fine, cudaStream_t st) {
   Level& Lv = h->L[l];
   Level& Lc = h->L[l + 1];
-  const int M = h->p.M;
+  const int M = Lv.M;
   if (Lv.next == 1) {
     launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)coarse, (T*)fine, st);
+  } else if (Lv.next == 3) {
+    // node-set interpolation on the coarse grid, then linear interpolation
+    launch_node_transfer<T>(Lc.g.Ns, Lc.Nt, Lc.M, M, adj ? Lv.RnT : Lv.Pn, (const T*)coarse, (T*)Lv.tmp, 0, st);
+    CKL();
+    launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)Lv.tmp, (T*)fine, st);
   } else {
-    launch_prolong_time_add<T>(Lv.g, Lc.Nt, M, adj ? h->PtT : h->col.Pt, (const T*)coarse, (T*)fine, st);
+    launch_prolong_time_add<T>(Lv.g, Lc.Nt, M, adj ? Lv.ns->PtT : Lv.ns->col.Pt, (const T*)coarse, (T*)fine, st);
   }
   CKL();
   return ST_OK;
@@ -703,12 +735,12 @@ CoarseParams<T> coarse_params(st_handle* h) {
   Level& Lv = h->L.back();
   CoarseParams<T> cp;
   cp.Nt = Lv.Nt;
-  cp.M = h->p.M;
+  cp.M = Lv.M;
   cp.Nc = h->Nc;
   cp.K = h->K;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b)
-      cp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? Lv.dt * h->col.Q[a][b] : 0.0;
+      cp.dtq[a][b] = (a < Lv.M && b < Lv.M) ? Lv.dt * Lv.ns->col.Q[a][b] : 0.0;
   cp.nu = h->p.nu;
   cp.Lc = h->Lc;
   cp.cbar = (h->p.reaction != ST_REACTION_NONE) ? (const T*)Lv.cbar : nullptr;
@@ -735,7 +767,7 @@ int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   if (h->split_lin) CK(cudaStreamWaitEvent(st, h->ev_lvl[l == last ? last + 1 : l], 0));
   if (l == last) return coarse_solve<T>(h, adj, Lv.r, Lv.e, st);
   const int nu1 = h->o.nu1, nu2 = h->o.nu2;
-  const long long n = Lv.g.Ns * Lv.Nt * h->p.M;
+  const long long n = Lv.g.Ns * Lv.Nt * Lv.M;
   if (nu1 == 0) CK(cudaMemsetAsync(Lv.e, 0, n * h->esz, st));
   for (int i = 0; i < nu1; ++i) TRY(smooth<T>(h, l, adj, i == 0, st));
   TRY(level_residual<T>(h, l, adj, Lv.e, Lv.r, Lv.in[0].y, 0, st));
@@ -768,7 +800,7 @@ int enqueue_linearize(st_handle* h, cudaStream_t st, cudaEvent_t* ev = nullptr) 
     if (ev) CK(cudaEventRecord(ev[l], st));
     if (rx && l + 1 < L) {
       Level& Lc = h->L[l + 1];
-      if (Lv.next == 1)
+      if (Lv.next == 1 || Lv.next == 3)
         launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
       else
         launch_cbar_time<T>(Lv.g, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
@@ -879,7 +911,7 @@ ResidParams fine_params(st_handle* h, const double* U, int adj) {
   rp.chunk = h->chunk;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b)
-      rp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? L0.dt * (adj ? h->col.Q[b][a] : h->col.Q[a][b]) : 0.0;
+      rp.dtq[a][b] = (a < h->p.M && b < h->p.M) ? L0.dt * (adj ? h->fine->col.Q[b][a] : h->fine->col.Q[a][b]) : 0.0;
   rp.nu = h->p.nu;
   rp.sc = stencil_of<double>(L0.g, h->p.nu);
   rp.nchunks = (rp.Nt + rp.chunk - 1) / rp.chunk;
@@ -1181,15 +1213,16 @@ int st_plan(const st_problem* p, const st_solver_opts* oin, st_plan_info* out) {
     li.next_kind = L.next;
     li.omega = L.omega;
     li.inner_levels = (int)L.inner.size();
-    const size_t D = (size_t)L.g.Ns * L.Nt * p->M;
+    li.M = L.M;
+    const size_t D = (size_t)L.g.Ns * L.Nt * L.M;
     bytes += 5 * round_up(D * esz) + (rx ? round_up((size_t)L.g.Ns * L.Nt * esz) : 0);
     for (size_t k = 1; k < L.inner.size(); ++k) {
-      const size_t Dk = (size_t)L.inner[k].Ns * L.Nt * p->M;
+      const size_t Dk = (size_t)L.inner[k].Ns * L.Nt * L.M;
       bytes += 3 * round_up(Dk * esz) + (rx ? round_up((size_t)L.inner[k].Ns * L.Nt * esz) : 0);
     }
   }
   const PlanLevel& C = pl.back();
-  const size_t Kc = (size_t)C.g.Ns * p->M;
+  const size_t Kc = (size_t)C.g.Ns * C.M;
   bytes += round_up(C.Nt * Kc * Kc * esz) + 2 * round_up(C.Nt * Kc * C.g.Ns * esz) +
            2 * round_up(C.Nt * C.g.Ns * C.g.Ns * esz) + round_up(C.Nt * C.g.Ns * esz);
   if (rx && o.exact_jacobian) bytes += round_up((size_t)pl[0].g.Ns * p->Nt * p->M * esz);
@@ -1222,8 +1255,11 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     st_destroy(h);
     return s;
   };
-  if (colloc_setup(pin->M, &h->col) != 0) return fail(ST_ERR_UNSUPPORTED);
-  build_transforms(h);
+  for (int m = 1; m <= pin->M; ++m) {
+    if (colloc_setup(m, &h->ns[m].col) != 0) return fail(ST_ERR_UNSUPPORTED);
+    build_nodeset(h->ns[m], m);
+  }
+  h->fine = &h->ns[pin->M];
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking) != cudaSuccess) {
     set_err(cudaGetLastError(), "cudaStreamCreate");
@@ -1251,22 +1287,38 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     Lv.mu = pl[l].mu;
     Lv.omega = pl[l].omega;
     Lv.next = pl[l].next;
+    Lv.M = pl[l].M;
+    Lv.ns = &h->ns[Lv.M];
     Lv.bottom_sweeps = pl[l].bottom_sweeps;
     {
       // While some coarser level of the hierarchy is coarser in space, the
       // smooth spatial error is left to it, so the slab solves need only damp
       // the oscillatory part; below the last space bisection (only slab
       // bisection or the coarsest level follows) they keep the full spatial
-      // multigrid.
+      // multigrid.  So does a level whose next coarser one has fewer nodes:
+      // the error modes of its time polynomial that the coarse node set does
+      // not represent are left to the smoother at every spatial frequency.
       bool space_below = false;
-      for (size_t q = l; q < pl.size(); ++q) space_below = space_below || pl[q].next == 1;
+      for (size_t q = l; q < pl.size(); ++q) space_below = space_below || pl[q].next == 1 || pl[q].next == 3;
       const int full = (int)pl[l].inner.size();
       const int cap = h->o.smooth_inner_levels;
-      Lv.smooth_depth = (cap > 0 && cap < full && space_below) ? cap : full;
+      Lv.smooth_depth = (cap > 0 && cap < full && space_below && pl[l].next != 3) ? cap : full;
       Lv.smooth_sweeps = Lv.smooth_depth < full ? h->o.smooth_sweeps : Lv.bottom_sweeps;
     }
-    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
+    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * Lv.M;
     int s = ST_OK;
+    if (Lv.next == 3) {
+      double P[MAXM][MAXM], R[MAXM][MAXM];
+      if (node_transfer_setup(Lv.M, pl[l + 1].M, P, R) != 0) return fail(ST_ERR_UNSUPPORTED);
+      for (int i = 0; i < MAXM; ++i)
+        for (int j = 0; j < MAXM; ++j) {
+          Lv.Pn[i][j] = P[i][j];
+          Lv.Rn[i][j] = R[i][j];
+          Lv.PnT[i][j] = P[j][i];
+          Lv.RnT[i][j] = R[j][i];
+        }
+      s |= alloc_into(h, &Lv.tmp, (size_t)pl[l + 1].g.Ns * Lv.Nt * Lv.M * h->esz);
+    }
     s |= alloc_into(h, &Lv.e, D * h->esz);
     s |= alloc_into(h, &Lv.r, D * h->esz);
     if (rx) s |= alloc_into(h, &Lv.cbar, (size_t)Lv.g.Ns * Lv.Nt * h->esz);
@@ -1274,7 +1326,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     for (size_t k = 0; k < Lv.in.size(); ++k) {
       InnerLev& I = Lv.in[k];
       I.g = pl[l].inner[k];
-      const size_t Dk = (size_t)I.g.Ns * Lv.Nt * M;
+      const size_t Dk = (size_t)I.g.Ns * Lv.Nt * Lv.M;
       s |= alloc_into(h, &I.y, Dk * h->esz);
       s |= alloc_into(h, &I.z, Dk * h->esz);
       s |= alloc_into(h, &I.t, Dk * h->esz);
@@ -1292,7 +1344,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   {
     Level& C = h->L.back();
     h->Nc = (int)C.g.Ns;
-    h->K = h->Nc * M;
+    h->K = h->Nc * C.M;
     // dense Laplacian of the coarsest grid by applying the stencil to unit vectors
     std::vector<double> Lc((size_t)h->Nc * h->Nc, 0.0);
     const int nn[3] = {C.g.n0, C.g.n1, C.g.n2};
@@ -1362,8 +1414,12 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   if (s != ST_OK) return fail(s);
   // zero the cycle buffers once (cbar stays 0 for linear problems)
   for (auto& Lv : h->L) {
-    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * M;
-    if (cudaMemsetAsync(Lv.e, 0, D * h->esz, h->stream) != cudaSuccess) return fail(ST_ERR_CUDA);
+    const size_t D = (size_t)Lv.g.Ns * Lv.Nt * Lv.M;
+    const cudaError_t e = cudaMemsetAsync(Lv.e, 0, D * h->esz, h->stream);
+    if (e != cudaSuccess) {
+      set_err(e, "cudaMemsetAsync");
+      return fail(ST_ERR_CUDA);
+    }
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
     set_err(cudaGetLastError(), "st_create sync");
@@ -1546,14 +1602,14 @@ int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out) {
   TRY(stage_in(h, U, &Ud, true));
   Level& L0 = h->L[0];
   const int M = h->p.M;
-  const double(*QI)[MAXM] = (h->o.sdc_qdelta == ST_SDC_LU) ? h->col.QI_lu : h->col.QI_ie;
+  const double(*QI)[MAXM] = (h->o.sdc_qdelta == ST_SDC_LU) ? h->fine->col.QI_lu : h->fine->col.QI_ie;
   for (int sw = 0; sw < nsweeps; ++sw) {
     TRY(fine_residual(h, Ud, L0.r, h->fp64, false, 0));
     for (int m = 0; m < M; ++m) {
       SdcCoef cf;
       for (int q = 0; q < MAXM; ++q) {
         cf.qi[q] = (q < m) ? L0.dt * QI[m][q] : 0.0;
-        cf.qe[q] = (q < m) ? L0.dt * h->col.QE[m][q] : 0.0;
+        cf.qe[q] = (q < m) ? L0.dt * h->fine->col.QE[m][q] : 0.0;
       }
       launch_sdc_rhs(h->D, h->fp64, L0.g, L0.Nt, M, m, h->p.nu, h->p.reaction, h->p.rho, cf, L0.r, L0.e, Ud,
                      L0.in[0].y, h->stream);
@@ -1685,6 +1741,17 @@ int st_collocation(int M, double* tau, double* Q, double* lam, double* V, double
   return ST_OK;
 }
 
+int st_node_transfer(int Mf, int Mc, double* P, double* R) {
+  double Pm[MAXM][MAXM], Rm[MAXM][MAXM];
+  if (node_transfer_setup(Mf, Mc, Pm, Rm) != 0) return ST_ERR_INVALID_ARG;
+  for (int j = 0; j < Mf; ++j)
+    for (int m = 0; m < Mc; ++m) {
+      if (P) P[j * Mc + m] = Pm[j][m];
+      if (R) R[m * Mf + j] = Rm[m][j];
+    }
+  return ST_OK;
+}
+
 int st_time_transfer(int M, double* Pt, double* Rt) {
   Colloc c;
   if (colloc_setup(M, &c) != 0) return ST_ERR_INVALID_ARG;
@@ -1711,6 +1778,7 @@ int st_level_info_get(const st_handle* h, int level, st_level_info* out) {
   out->next_kind = Lv.next;
   out->omega = Lv.omega;
   out->inner_levels = (int)Lv.in.size();
+  out->M = Lv.M;
   return ST_OK;
 }
 
@@ -1727,7 +1795,7 @@ int st_linearize(st_handle* h, const double* U) {
 }
 
 static size_t level_elems(const st_handle* h, int l) {
-  return (size_t)h->L[l].g.Ns * h->L[l].Nt * h->p.M;
+  return (size_t)h->L[l].g.Ns * h->L[l].Nt * h->L[l].M;
 }
 
 int st_level_cbar(st_handle* h, int level, void* out) {
@@ -1837,14 +1905,14 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         // back-transform and the damped block-Jacobi update of e
         auto go = [&](auto tag) -> int {
           using TT = decltype(tag);
-          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(h, L0.dt), rx);
+          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(*L0.ns, L0.dt), rx);
           BtFuse<TT> f;
           f.on = true;
           f.e_zero = 0;
           f.omega = (TT)L0.omega;
           f.e = (TT*)L0.e;
           for (int a2 = 0; a2 < MAXM; ++a2)
-            for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (TT)h->Bf[a2][b];
+            for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (TT)h->fine->Bf[a2][b];
           apply_fuse(ip, f);
           launch_inner_jacobi<TT>(h->D, 0, ip, st);
           CKL();
@@ -1856,13 +1924,13 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         if (h->fp64) {
           double B[MAXM][MAXM];
           for (int a2 = 0; a2 < MAXM; ++a2)
-            for (int b = 0; b < MAXM; ++b) B[a2][b] = h->Bf[a2][b];
+            for (int b = 0; b < MAXM; ++b) B[a2][b] = h->fine->Bf[a2][b];
           launch_backtransform<double>(L0.g, L0.Nt, h->p.M, B, L0.omega, 0, (const double*)L0.in[0].z,
                                        (double*)L0.e, st);
         } else {
           float B[MAXM][MAXM];
           for (int a2 = 0; a2 < MAXM; ++a2)
-            for (int b = 0; b < MAXM; ++b) B[a2][b] = (float)h->Bf[a2][b];
+            for (int b = 0; b < MAXM; ++b) B[a2][b] = (float)h->fine->Bf[a2][b];
           launch_backtransform<float>(L0.g, L0.Nt, h->p.M, B, (float)L0.omega, 0, (const float*)L0.in[0].z,
                                       (float*)L0.e, st);
         }
@@ -1874,7 +1942,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
       case ST_KERNEL_PROLONG: {
         auto go = [&](auto tag) -> int {
           using TT = decltype(tag);
-          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(h, L0.dt), rx);
+          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(*L0.ns, L0.dt), rx);
           if (which == ST_KERNEL_SHIFTED_RESIDUAL) launch_shifted_residual<TT>(h->D, ip, st);
           else if (which == ST_KERNEL_INNER_RESTRICT) launch_inner_restrict<TT>(h->D, ip, st);
           else

@@ -113,6 +113,10 @@ template <typename T>
 void launch_prolong_time_add(const GridP& g, int Ntc, int M, const double P[2 * MAXM][MAXM], const T* c, T* f,
                              cudaStream_t st);
 template <typename T> void launch_cbar_time(const GridP& g, int Ntc, const T* f, T* c, cudaStream_t st);
+// out[n][a][s] (+)= sum_b X[a][b] in[n][b][s], X Mo x Mi (node-set transfer)
+template <typename T>
+void launch_node_transfer(long long Ns, int Nt, int Mi, int Mo, const double X[MAXM][MAXM], const T* in, T* out,
+                          int add, cudaStream_t st);
 
 // k_level4.cu: float4 variants (return false when they do not apply)
 bool launch_lin_residual4(int D, const LinParams<float>& p, cudaStream_t st);

@@ -322,4 +322,35 @@ int colloc_setup(int M, Colloc* out) {
   return 0;
 }
 
+int node_transfer_setup(int Mf, int Mc, double P[MAXM][MAXM], double R[MAXM][MAXM]) {
+  if (Mf < 1 || Mc < 1 || Mf > MAXM || Mc > Mf) return -1;
+  Colloc cf, cc;
+  if (colloc_setup(Mf, &cf) != 0 || colloc_setup(Mc, &cc) != 0) return -2;
+  LD tc[MAXM];
+  for (int m = 0; m < Mc; ++m) tc[m] = cc.tau[m];
+  LD Pl[MAXM][MAXM];
+  for (int j = 0; j < Mf; ++j)
+    for (int m = 0; m < Mc; ++m) Pl[j][m] = lagrange(tc, Mc, m, (LD)cf.tau[j]);
+  LD Kc[2 * MAXM][2 * MAXM], Kci[2 * MAXM][2 * MAXM];
+  for (int a = 0; a < Mc; ++a)
+    for (int b = 0; b < Mc; ++b) Kc[a][b] = cc.K[a][b];
+  if (!invert(Mc, Kc, Kci)) return -3;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) P[a][b] = R[a][b] = 0.0;
+  for (int j = 0; j < Mf; ++j)
+    for (int m = 0; m < Mc; ++m) P[j][m] = (double)Pl[j][m];
+  // R = Kc^{-1} (P^T Kf)
+  for (int m = 0; m < Mc; ++m)
+    for (int j = 0; j < Mf; ++j) {
+      LD acc = 0;
+      for (int i = 0; i < Mc; ++i) {
+        LD t = 0;
+        for (int l = 0; l < Mf; ++l) t += Pl[l][i] * (LD)cf.K[l][j];
+        acc += Kci[m][i] * t;
+      }
+      R[m][j] = (double)acc;
+    }
+  return 0;
+}
+
 }  // namespace st

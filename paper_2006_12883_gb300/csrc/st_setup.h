@@ -27,4 +27,10 @@ struct Colloc {
 // 0 on success, negative on failure.
 int colloc_setup(int M, Colloc* out);
 
+// M-coarsening between the Radau node sets of one slab (Section 5.2, SMMG):
+// P (Mf x Mc) evaluates the coarse nodal polynomial at the fine nodes,
+// R (Mc x Mf) = Kc^{-1} P^T Kf restricts collocation-form residuals.
+// 0 on success, negative on failure.
+int node_transfer_setup(int Mf, int Mc, double P[MAXM][MAXM], double R[MAXM][MAXM]);
+
 }  // namespace st

@@ -21,7 +21,7 @@ ST_ERR_NOT_CONVERGED, ST_ERR_DIVERGED, ST_ERR_TIMEOUT, ST_ERR_UNSUPPORTED = 4, 5
 DIRICHLET, PERIODIC, NEUMANN = 0, 1, 2
 NONE, LOGISTIC, CUBIC = 0, 1, 2
 FP64, FP32_REFINE = 0, 1
-COARSEN_SPACE, COARSEN_AUTO_MU = 0, 1
+COARSEN_SPACE, COARSEN_AUTO_MU, COARSEN_SPACE_NODES = 0, 1, 2
 SDC_IE, SDC_LU = 0, 1
 MAX_M, MAX_LEVELS, MAX_HISTORY = 5, 32, 64
 
@@ -65,11 +65,12 @@ class StSolveInfo(ctypes.Structure):
 
 class StLevelInfo(ctypes.Structure):
     _fields_ = [("n", c_int * 3), ("Ns", c_longlong), ("Nt", c_int), ("dt", c_double), ("h", c_double * 3),
-                ("mu", c_double), ("next_kind", c_int), ("omega", c_double), ("inner_levels", c_int)]
+                ("mu", c_double), ("next_kind", c_int), ("omega", c_double), ("inner_levels", c_int),
+                ("M", c_int)]
 
     def as_dict(self):
         return dict(n=list(self.n), Ns=self.Ns, Nt=self.Nt, dt=self.dt, h=list(self.h), mu=self.mu,
-                    next_kind=self.next_kind, omega=self.omega, inner_levels=self.inner_levels)
+                    next_kind=self.next_kind, omega=self.omega, inner_levels=self.inner_levels, M=self.M)
 
 
 class StStatsInfo(ctypes.Structure):
@@ -104,6 +105,7 @@ _SIGS = {
     "st_last_error": (ctypes.c_char_p, []),
     "st_collocation": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_time_transfer": (c_int, [c_int, c_void_p, c_void_p]),
+    "st_node_transfer": (c_int, [c_int, c_int, c_void_p, c_void_p]),
     "st_num_levels": (c_int, [c_void_p]),
     "st_level_info_get": (c_int, [c_void_p, c_int, POINTER(StLevelInfo)]),
     "st_linearize": (c_int, [c_void_p, c_void_p]),
@@ -154,6 +156,9 @@ class StError(RuntimeError):
 
 def check(status: int, where: str):
     if status != ST_OK:
+        if status == ST_ERR_CUDA:
+            detail = lib().st_last_error()
+            where = f"{where} [{detail.decode() if detail else ''}]"
         raise StError(status, where)
     return status
 
@@ -185,6 +190,15 @@ def st_collocation(M: int):
                                Vi.ctypes.data), "st_collocation")
     c = lambda a: (a[0::2] + 1j * a[1::2])
     return tau, Q.reshape(M, M), c(lam), c(V).reshape(M, M), c(Vi).reshape(M, M)
+
+
+def st_node_transfer(Mf: int, Mc: int):
+    """(P_M[Mf][Mc], R_M[Mc][Mf]) from the library's setup."""
+    import numpy as np
+    P = np.zeros(Mf * Mc)
+    R = np.zeros(Mc * Mf)
+    check(lib().st_node_transfer(Mf, Mc, P.ctypes.data, R.ctypes.data), "st_node_transfer")
+    return P.reshape(Mf, Mc), R.reshape(Mc, Mf)
 
 
 def st_time_transfer(M: int):
@@ -378,7 +392,7 @@ class Solver:
     def level_shape(self, l):
         li = self.level_info(l)
         d = len(self.grid_shape)
-        return (li["Nt"], self.M) + tuple(li["n"][:d][::-1])
+        return (li["Nt"], li["M"]) + tuple(li["n"][:d][::-1])
 
     def linearize(self, U):
         check(lib().st_linearize(self.h, self._ptr(U)), "st_linearize")

@@ -45,7 +45,7 @@ class Case:
 
     def solver(self, **opts):
         from paper_2006_12883_gb300 import stlib
-        o = stlib.make_opts(**opts)
+        o = stlib.make_opts(**{**self.extra, **opts})
         return stlib.Solver(self.shape, self.bc, self.nu, self.Nt, self.M, self.u0(), T=self.T, X=self.X,
                             reaction=self.reaction, rho=self.rho, opts=o)
 
@@ -71,8 +71,13 @@ PER3D_M5 = Case("periodic3d_m5", (4, 8, 8), P_, 0.01, 4, 5, reaction=L_, rho=1.0
 # double-float residual at M = 5)
 TILED_M5 = Case("periodic2d_m5_runs", (32, 64), P_, 0.02, 10, 5, reaction=C_, rho=1.0, u0_kind="noise", seed=9)
 
+# space bisection with one collocation node fewer per level (SMMG)
+SMMG2D = Case("smmg2d", (32, 32), P_, 1e-2, 8, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=12884,
+              extra=dict(coarsening=2))
+SMMG1D = Case("smmg1d_m5", (65,), N_, 1.0, 8, 5, u0_kind="cosine", extra=dict(coarsening=2))
+
 RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5]
-SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5]
+SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D]
 
 
 def residual_scale(p: system.Problem, U: np.ndarray) -> float:

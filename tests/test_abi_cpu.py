@@ -78,6 +78,18 @@ def test_plan_auto_mu_rule(stlib):
     assert info.level[info.levels - 1].Ns <= 16
 
 
+def test_plan_space_nodes_rule(stlib):
+    """SPACE_NODES (SMMG of Section 5.2) bisects space on every level and drops
+    one collocation node per level until M = 1: M_l = max(M - l + 1, 1)."""
+    p = stlib.make_problem((1025,), stlib.NEUMANN, 1.0, 8, 5)
+    info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE_NODES, max_levels=7))
+    lv = [info.level[l] for l in range(info.levels)]
+    assert [l.M for l in lv] == [max(5 - l, 1) for l in range(len(lv))]
+    assert [l.n[0] for l in lv] == [1025, 513, 257, 129, 65, 33, 17]
+    assert all(l.Nt == 8 for l in lv)
+    assert [l.next_kind for l in lv] == [3, 3, 3, 3, 1, 1, 0]
+
+
 def test_plan_dirichlet_and_neumann_sizes(stlib):
     p = stlib.make_problem((63,), stlib.DIRICHLET, 1.0, 16, 2)
     info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE))
@@ -102,3 +114,12 @@ def test_invalid_arguments_rejected(stlib):
         with pytest.raises(stlib.StError) as ei:
             stlib.st_plan(p)
         assert ei.value.status == stlib.ST_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("Mf,Mc", [(2, 1), (3, 2), (5, 4), (5, 1), (4, 2)])
+def test_host_node_transfer_matches_oracle(Mf, Mc):
+    from paper_2006_12883_gb300 import stlib
+    P, R = stlib.st_node_transfer(Mf, Mc)
+    tf, tc = col.radau_right_nodes(Mf), col.radau_right_nodes(Mc)
+    assert np.abs(P - col.node_prolongation(tf, tc)).max() < 1e-13
+    assert np.abs(R - col.node_restriction(tf, tc)).max() < 1e-12

@@ -8,7 +8,7 @@ import pytest
 import stgen
 from oracle import multilevel as ml
 from oracle import space, system
-from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, Case
+from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, SMMG1D, SMMG2D, Case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -17,12 +17,12 @@ P_ = space.PERIODIC
 # a case whose hierarchy mixes space and slab bisection (AUTO_MU) and one
 # with space bisection only (SPACE)
 MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise", seed=5)
-LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5]
+LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D]
 
 
 def _oracle_level(S, case, l, cbar, U=None):
     """The oracle's level l; with U (the linearisation point) level 0 carries
-    R'(U) per node, as the library's finest level does by default."""
+    R'(U) per node, as the library's finest level does with exact_jacobian."""
     li = S.level_info(l)
     d = len(case.shape)
     shape = tuple(li["n"][:d][::-1])
@@ -30,7 +30,7 @@ def _oracle_level(S, case, l, cbar, U=None):
     if U is not None and l == 0 and case.reaction != space.NONE:
         p = case.problem()
         cnode = p.dR(np.asarray(U).reshape(p.Nt, p.M, p.Ns))
-    return ml.Level(shape=shape, bc=case.bc, Nt=li["Nt"], M=case.M, dt=li["dt"], nu=case.nu, X=case.X,
+    return ml.Level(shape=shape, bc=case.bc, Nt=li["Nt"], M=li["M"], dt=li["dt"], nu=case.nu, X=case.X,
                     cbar=cbar, cnode=cnode)
 
 
@@ -60,7 +60,7 @@ def test_cbar_hierarchy(case, prec):
         if l + 1 < S.num_levels():
             li = S.level_info(l)
             lev = _oracle_level(S, case, l, cb)
-            if li["next_kind"] == 1:
+            if li["next_kind"] in (1, 3):
                 cb = ml.restrict_space(case.bc, lev.shape, cb)
             else:
                 cb = ml.restrict_cbar_time(cb)
@@ -84,10 +84,11 @@ def test_level_residual_and_transfers(case, prec, ej):
         et = torch.tensor(e, dtype=dt, device="cuda")
         rt = torch.tensor(r, dtype=dt, device="cuda")
         e_, r_ = et.double().cpu().numpy(), rt.double().cpu().numpy()
+        M = lev.M
         for tr in (False, True):
             if tr and case.bc == space.NEUMANN:
                 continue
-            got = S.level_residual(l, et, rt, transpose=tr).double().cpu().numpy().reshape(lev.Nt, p.M, -1)
+            got = S.level_residual(l, et, rt, transpose=tr).double().cpu().numpy().reshape(lev.Nt, M, -1)
             ref = ml.linear_residual_T(lev, e_, r_) if tr else ml.linear_residual(lev_fwd, e_, r_)
             if l == 0 and not tr and ej:
                 # the finest level's operator is minus the exact Jacobian of G
@@ -96,37 +97,44 @@ def test_level_residual_and_transfers(case, prec, ej):
             scale = np.abs(e_).max() * (1 + lev.dt * case.nu * 4 * len(case.shape) / min(S.level_info(l)["h"][:len(case.shape)]) ** 2) + np.abs(r_).max()
             assert np.abs(got - ref).max() <= _tol(prec) * scale, (l, tr)
         if l + 1 < S.num_levels():
+            from oracle import collocation as col
             li = S.level_info(l)
+            Mc = S.level_info(l + 1)["M"]
+            kind = li["next_kind"]
+            tf, tc = col.radau_right_nodes(M), col.radau_right_nodes(Mc)
             for tr in (False, True):
                 c = S.level_restrict(l, rt, transpose=tr).double().cpu().numpy()
-                if li["next_kind"] == 1:
-                    ref = ml.restrict_space(case.bc, lev.shape, r_.reshape(lev.Nt, p.M, -1))
+                rr = r_.reshape(lev.Nt, M, -1)
+                if kind == 1:
+                    ref = ml.restrict_space(case.bc, lev.shape, rr)
+                elif kind == 3:
+                    X = col.node_prolongation(tf, tc).T if tr else col.node_restriction(tf, tc)
+                    ref = np.einsum("cf,nfs->ncs", X, ml.restrict_space(case.bc, lev.shape, rr))
+                elif tr:
+                    Pt = col.time_prolongation(tf)
+                    ref = np.einsum("km,nks->nms", Pt, r_.reshape(lev.Nt // 2, 2 * M, -1))
                 else:
-                    if tr:
-                        from oracle import collocation as col
-                        Pt = col.time_prolongation(col.radau_right_nodes(p.M))
-                        ref = np.einsum("km,nks->nms", Pt, r_.reshape(lev.Nt // 2, 2 * p.M, -1))
-                    else:
-                        ref = ml.restrict_time(p.M, r_.reshape(lev.Nt, p.M, -1))
+                    ref = ml.restrict_time(M, rr)
                 assert np.abs(c.reshape(ref.shape) - ref).max() <= _tol(prec) * 4 * np.abs(r_).max(), (l, tr)
                 cshape = S.level_shape(l + 1)
                 cv = stgen.random_field(cshape, 300 + l)
                 ct = torch.tensor(cv, dtype=dt, device="cuda")
-                cv_ = ct.double().cpu().numpy().reshape(cshape[0], p.M, -1)
+                cv_ = ct.double().cpu().numpy().reshape(cshape[0], Mc, -1)
                 fine = et.clone()
                 S.level_prolong(l, ct, fine, transpose=tr)
-                if li["next_kind"] == 1:
+                if kind == 1:
                     add = ml.prolong_space(case.bc, lev.shape, cv_)
+                elif kind == 3:
+                    X = col.node_restriction(tf, tc).T if tr else col.node_prolongation(tf, tc)
+                    add = ml.prolong_space(case.bc, lev.shape, np.einsum("fc,ncs->nfs", X, cv_))
+                elif tr:
+                    Rt = col.time_restriction(tf)
+                    add = np.einsum("mk,nms->nks", Rt, cv_).reshape(lev.Nt, M, -1)
                 else:
-                    if tr:
-                        from oracle import collocation as col
-                        Rt = col.time_restriction(col.radau_right_nodes(p.M))
-                        add = np.einsum("mk,nms->nks", Rt, cv_).reshape(lev.Nt, p.M, -1)
-                    else:
-                        add = ml.prolong_time(p.M, cv_)
+                    add = ml.prolong_time(M, cv_)
                 ref = e_.reshape(add.shape) + add
                 assert np.abs(fine.double().cpu().numpy().reshape(ref.shape) - ref).max() <= \
-                    _tol(prec) * 4 * (np.abs(e_).max() + np.abs(cv_).max()), (l, tr)
+                    _tol(prec) * 8 * (np.abs(e_).max() + np.abs(cv_).max()), (l, tr)
     S.close()
 
 
@@ -139,8 +147,8 @@ def test_coarse_solve_exact(case, transpose):
     lev = _oracle_level(S, case, L, cb.reshape(cb.shape[0], -1))
     shp = S.level_shape(L)
     r = stgen.random_field(shp, 400)
-    e = S.coarse_solve(torch.tensor(r, device="cuda"), transpose=transpose).cpu().numpy().reshape(lev.Nt, p.M, -1)
-    ref = (ml.coarse_solve_exact_T if transpose else ml.coarse_solve_exact)(lev, r.reshape(lev.Nt, p.M, -1))
+    e = S.coarse_solve(torch.tensor(r, device="cuda"), transpose=transpose).cpu().numpy().reshape(lev.Nt, lev.M, -1)
+    ref = (ml.coarse_solve_exact_T if transpose else ml.coarse_solve_exact)(lev, r.reshape(lev.Nt, lev.M, -1))
     assert np.abs(e - ref).max() <= 1e-10 * max(1, np.abs(ref).max())
     S.close()
 
