@@ -148,6 +148,11 @@ typedef struct {
                            decrease along a cycle's correction, st_solve
                            continues with the exact Jacobian and FGMRES of
                            this many steps (default 10; 0 = report DIVERGED) */
+  int pfasst_levels;    /* st_pfasst: levels of the hierarchy (default 3; the
+                           handle must coarsen in space only, ST_COARSEN_SPACE) */
+  int pfasst_coarse_M;  /* st_pfasst: nodes per slab on the levels above the
+                           finest (default 1) */
+  int pfasst_sweeps;    /* st_pfasst: SDC sweeps per level and visit (default 1) */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -240,6 +245,26 @@ int st_vcycle(st_handle* h, double* U, double* norm_out);
  * top of the FP64 residual: slab n starts from the previous iterate's last
  * node of slab n-1.  norm_out receives ||G(U)|| before the last sweep. */
 int st_sdc_sweep(st_handle* h, double* U, int nsweeps, double* norm_out);
+
+/* PFASST (Section 4.1; Emmett and Minion 2012): iterate on U (Nt*M*Ns
+ * doubles in the layout of st_solve, host or device; its content is the
+ * start iterate, e.g. u0 spread over every node) until the collocation
+ * residual ||G(U)|| / ||G(0)|| <= o.tol or o.max_iters iterations.  One
+ * iteration: IMEX SDC sweeps on all slabs at once on each level from the
+ * finest down (each slab starting from the last node of the slab before),
+ * the restriction of the iterate with the FAS correction
+ * tau_{l+1} = R(dt Q F(U_l) + tau_l) - dt Q F(R U_l), serial sweeps slab
+ * after slab on the coarsest level, then the interpolated coarse corrections
+ * back up with sweeps on the levels in between.  Level l is the handle's
+ * l-th space-bisected level with o.pfasst_coarse_M nodes (l >= 1); transfers
+ * are full weighting / linear interpolation in space and nodal-polynomial
+ * evaluation between node sets; spatial solves use the level's inner
+ * multigrid (o.sdc_inner_cycles cycles).  The state of the levels above the
+ * finest is FP64; sweep corrections use the cycle precision.
+ * Errors: ST_ERR_UNSUPPORTED unless the first o.pfasst_levels - 1 levels
+ * bisect space only; otherwise as st_solve (info->history: residual per
+ * iteration). */
+int st_pfasst(st_handle* h, double* U, st_solve_info* info);
 
 /* Solve G(U) = 0 from the given U (zero initial guess in the paper, Section
  * 5.2) by V-cycles inside FP64 defect correction (Newton with the averaged

@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
 #pragma unroll
           for (int q = 0; q < MAXM; ++q)
             if (q < M) g = fma(p.dtq[m][q], F[q], g);
+          if (p.tau) g += p.tau[base + (long long)m * Ns];
           sq = fma(g, g, sq);
           if (R) R[base + (long long)m * Ns] = (TR)g;
         }
@@ -639,6 +640,24 @@ void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0
 
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st) {
   st_launch(k_sum_partials, 1, 1024, 0, st, part, n, out);
+}
+
+// W[n][m][s] += U[n][m][s] - prev_n(s), prev_n = u0 (n = 0) or U[n-1][M-1]:
+// turns a residual G(U) (with its tau) into dt Q F(U) + tau.
+__global__ void __launch_bounds__(256) k_add_state(double* __restrict__ W, const double* __restrict__ U,
+                                                   const double* __restrict__ u0, long long Ns, int Nt, int M) {
+  grid_dep_wait();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * Nt * M) return;
+  const long long s = idx % Ns;
+  const long long nm = idx / Ns;
+  const long long n = nm / M;
+  const double prev = (n == 0) ? u0[s] : U[((n - 1) * M + (M - 1)) * Ns + s];
+  W[idx] += U[idx] - prev;
+}
+
+void launch_add_state(double* W, const double* U, const double* u0, long long Ns, int Nt, int M, cudaStream_t st) {
+  st_launch(k_add_state, blocks_for(Ns * Nt * M, 256), 256, 0, st, W, U, u0, Ns, Nt, M);
 }
 
 void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha) {

@@ -90,6 +90,21 @@ struct Alloc {
   size_t bytes;
 };
 
+// One PFASST level above the finest (FP64 state; the grid and the inner
+// spatial multigrid are those of the space-bisected cycle level of the same
+// index).
+struct PfLevel {
+  int M = 1;
+  double* U = nullptr;     // iterate [Nt][M][Ns]
+  double* Ubar = nullptr;  // the restricted iterate before the coarse sweeps
+  double* tau = nullptr;   // FAS correction
+  double* W = nullptr;     // work: dt Q F(U) + tau
+  double* tmp = nullptr;   // transfers: the finer level's node count on this grid
+  double* u0 = nullptr;    // restricted initial value
+  double Rv[MAXM][MAXM];   // node values, finer -> this (M x M_finer)
+  double Pv[MAXM][MAXM];   // node values, this -> finer (M_finer x M)
+};
+
 template <typename T>
 StencilC<T> stencil_of(const GridP& g, double nu) {
   StencilC<T> c;
@@ -203,6 +218,7 @@ int validate(const st_problem* p, const st_solver_opts* o) {
     if (o->smooth_inner_levels < 0 || o->smooth_sweeps < 2) return ST_ERR_INVALID_ARG;
     if (o->krylov < 0 || o->krylov > 30 || !(o->krylov_rtol > 0.0)) return ST_ERR_INVALID_ARG;
     if (o->krylov_fallback < 0 || o->krylov_fallback > 30) return ST_ERR_INVALID_ARG;
+    if (o->pfasst_levels < 1 || o->pfasst_coarse_M < 1 || o->pfasst_sweeps < 1) return ST_ERR_INVALID_ARG;
     if (o->sdc_inner_cycles < 1 || o->max_iters < 0 || !(o->tol >= 0)) return ST_ERR_INVALID_ARG;
     if (o->max_levels < 1 || o->coarse_max_points < 1 || o->coarse_max_slabs < 1) return ST_ERR_INVALID_ARG;
     if (o->sdc_qdelta != ST_SDC_IE && o->sdc_qdelta != ST_SDC_LU) return ST_ERR_INVALID_ARG;
@@ -336,6 +352,9 @@ struct st_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_lvl[ST_MAX_LEVELS + 1] = {};
   bool split_lin = false;  // set while that graph's cycle is enqueued
+  int nt_override = 0;     // > 0: inner solves act on this many slabs from the first
+  std::vector<PfLevel> pf;  // PFASST levels 1.. (allocated at first use)
+  double* pfW0 = nullptr;   // PFASST work on the finest level
   long long D_total = 0;
   int chunk = 1;
 };
@@ -480,7 +499,7 @@ InnerParams<T> inner_params(st_handle* h, Level& Lv, int k, int P, const Shifts<
   InnerLev& I = Lv.in[k];
   ip.g = I.g;
   ip.gc = (k + 1 < (int)Lv.in.size()) ? Lv.in[k + 1].g : I.g;
-  ip.Nt = Lv.Nt;
+  ip.Nt = h->nt_override > 0 ? h->nt_override : Lv.Nt;
   ip.P = P;
   ip.sh = sh;
   ip.sc = stencil_of<T>(I.g, h->p.nu);
@@ -574,7 +593,8 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int depth, int sweeps, int P, c
     CKL();
   }
   TRY(inner_vcycle<T>(h, Lv, k + 1, depth, sweeps, P, sh, use_cbar, true, nullptr, st));
-  launch_prolong_space_add<T>(h->D, I.g, Lv.in[k + 1].g, (long long)Lv.Nt * P, (const T*)Lv.in[k + 1].z,
+  const int nt_in = h->nt_override > 0 ? h->nt_override : Lv.Nt;
+  launch_prolong_space_add<T>(h->D, I.g, Lv.in[k + 1].g, (long long)nt_in * P, (const T*)Lv.in[k + 1].z,
                               (T*)I.z, st);
   CKL();
   for (int it = 0; it < ns; ++it) {
@@ -924,6 +944,7 @@ ResidParams fine_params(st_handle* h, const double* U, int adj) {
   rp.R = nullptr;
   rp.cbar = nullptr;
   rp.cnode = nullptr;
+  rp.tau = nullptr;
   rp.partial = h->partial;
   return rp;
 }
@@ -1135,6 +1156,183 @@ int krylov_step(st_handle* h, int m, int* its) {
   return ST_OK;
 }
 
+// ---------------------------------------------------------------------------
+// PFASST (Section 4.1): IMEX SDC sweeps on a hierarchy of space-bisected
+// levels with fewer nodes, FAS corrections, serial sweeps on the coarsest.
+// ---------------------------------------------------------------------------
+// Residual parameters of nt slabs of PFASST level data (FP64 arithmetic).
+ResidParams pf_params(st_handle* h, const Level& Lv, int M, const double* U, const double* u0, const double* tau,
+                      int nt) {
+  ResidParams rp = fine_params(h, U, 0);
+  rp.g = Lv.g;
+  rp.Nt = nt;
+  rp.M = M;
+  rp.chunk = 1;
+  rp.nchunks = nt;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) rp.dtq[a][b] = (a < M && b < M) ? Lv.dt * h->ns[M].col.Q[a][b] : 0.0;
+  rp.sc = stencil_of<double>(Lv.g, h->p.nu);
+  rp.u0 = u0;
+  rp.tau = tau;
+  rp.partial = nullptr;
+  return rp;
+}
+
+// One IMEX SDC sweep (correction form) of slabs [n0, n0 + nt) of level l
+// with M nodes; slab n0 starts from u0 if n0 == 0, else from the current
+// last node of slab n0 - 1.  Spatial solves: the level's inner multigrid.
+int pf_sweep(st_handle* h, int l, int M, double* U, const double* u0, const double* tau, int n0, int nt) {
+  Level& Lv = h->L[l];
+  const long long Ns = Lv.g.Ns;
+  double* Un = U + (long long)n0 * M * Ns;
+  const double* prev = n0 == 0 ? u0 : U + ((long long)(n0 - 1) * M + (M - 1)) * Ns;
+  ResidParams rp = pf_params(h, Lv, M, Un, prev, tau ? tau + (long long)n0 * M * Ns : nullptr, nt);
+  rp.R = Lv.r;
+  launch_residual(h->D, h->fp64, h->fp64, rp, h->stream);
+  CKL();
+  const Colloc& c = h->ns[M].col;
+  const double(*QI)[MAXM] = (h->o.sdc_qdelta == ST_SDC_LU) ? c.QI_lu : c.QI_ie;
+  h->nt_override = nt;
+  int s = ST_OK;
+  for (int m = 0; m < M && s == ST_OK; ++m) {
+    SdcCoef cf;
+    for (int q = 0; q < MAXM; ++q) {
+      cf.qi[q] = (q < m) ? Lv.dt * QI[m][q] : 0.0;
+      cf.qe[q] = (q < m) ? Lv.dt * c.QE[m][q] : 0.0;
+    }
+    launch_sdc_rhs(h->D, h->fp64, Lv.g, nt, M, m, h->p.nu, h->p.reaction, h->p.rho, cf, Lv.r, Lv.e, Un,
+                   Lv.in[0].y, h->stream);
+    if (cudaGetLastError() != cudaSuccess) { s = ST_ERR_CUDA; break; }
+    if (h->fp64)
+      s = inner_solve<double>(h, Lv, (int)Lv.in.size(), Lv.bottom_sweeps, 1, real_shift<double>(Lv.dt * QI[m][m]),
+                              false, h->o.sdc_inner_cycles, false, nullptr, h->stream);
+    else
+      s = inner_solve<float>(h, Lv, (int)Lv.in.size(), Lv.bottom_sweeps, 1,
+                             real_shift<float>((float)(Lv.dt * QI[m][m])), false, h->o.sdc_inner_cycles, false,
+                             nullptr, h->stream);
+    if (s != ST_OK) break;
+    launch_scatter_plane(h->fp64, Lv.in[0].z, Lv.e, Ns, nt, M, m, h->stream);
+  }
+  h->nt_override = 0;
+  TRY(s);
+  CKL();
+  launch_update(h->fp64, Un, Lv.e, (long long)nt * M * Ns, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+// W = dt Q F(U) + tau on every slab of level l (M nodes)
+int pf_integrals(st_handle* h, int l, int M, const double* U, const double* u0, const double* tau, double* W) {
+  Level& Lv = h->L[l];
+  ResidParams rp = pf_params(h, Lv, M, U, u0, tau, Lv.Nt);
+  rp.R = W;
+  launch_residual(h->D, 1, h->fp64, rp, h->stream);
+  CKL();
+  launch_add_state(W, U, u0, Lv.g.Ns, Lv.Nt, M, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+// out (level l + 1) = value restriction of in (level l, Mf nodes)
+int pf_restrict(st_handle* h, int l, int Mf, const double* in, double* out) {
+  Level& Lf = h->L[l];
+  Level& Lc = h->L[l + 1];
+  PfLevel& P = h->pf[l + 1];
+  launch_restrict_space<double>(h->D, Lf.g, Lc.g, (long long)Lf.Nt * Mf, in, P.tmp, h->stream);
+  CKL();
+  launch_node_transfer<double>(Lc.g.Ns, Lc.Nt, Mf, P.M, P.Rv, P.tmp, out, 0, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+// fine (level l, Mf nodes) += interpolation of d (level l + 1)
+int pf_prolong_add(st_handle* h, int l, int Mf, const double* d, double* fine) {
+  Level& Lf = h->L[l];
+  Level& Lc = h->L[l + 1];
+  PfLevel& P = h->pf[l + 1];
+  launch_node_transfer<double>(Lc.g.Ns, Lc.Nt, P.M, Mf, P.Pv, d, P.tmp, 0, h->stream);
+  CKL();
+  launch_prolong_space_add<double>(h->D, Lf.g, Lc.g, (long long)Lf.Nt * Mf, P.tmp, fine, h->stream);
+  CKL();
+  return ST_OK;
+}
+
+int pf_setup(st_handle* h, int nl) {
+  if ((int)h->pf.size() == nl) {
+    for (int l = 1; l < nl; ++l) {  // the initial value may have changed
+      const double* src = l == 1 ? h->u0 : h->pf[l - 1].u0;
+      launch_restrict_space<double>(h->D, h->L[l - 1].g, h->L[l].g, 1, src, h->pf[l].u0, h->stream);
+      CKL();
+    }
+    return ST_OK;
+  }
+  if (!h->pf.empty()) return ST_ERR_INVALID_ARG;  // the hierarchy is fixed per handle
+  h->pf.resize(nl);
+  TRY(alloc_typed(h, &h->pfW0, (size_t)h->D_total * sizeof(double)));
+  for (int l = 1; l < nl; ++l) {
+    PfLevel& P = h->pf[l];
+    const int Mf = l == 1 ? h->p.M : h->pf[l - 1].M;
+    P.M = std::min(h->o.pfasst_coarse_M, Mf);
+    const Level& Lv = h->L[l];
+    const size_t n = (size_t)Lv.g.Ns * Lv.Nt * P.M;
+    TRY(alloc_typed(h, &P.U, n * sizeof(double)));
+    TRY(alloc_typed(h, &P.Ubar, n * sizeof(double)));
+    TRY(alloc_typed(h, &P.tau, n * sizeof(double)));
+    TRY(alloc_typed(h, &P.W, n * sizeof(double)));
+    TRY(alloc_typed(h, &P.tmp, (size_t)Lv.g.Ns * Lv.Nt * Mf * sizeof(double)));
+    TRY(alloc_typed(h, &P.u0, (size_t)Lv.g.Ns * sizeof(double)));
+    if (node_eval_setup(Mf, P.M, P.Rv) != 0 || node_eval_setup(P.M, Mf, P.Pv) != 0) return ST_ERR_UNSUPPORTED;
+    // the restricted initial value
+    const double* src = l == 1 ? h->u0 : h->pf[l - 1].u0;
+    launch_restrict_space<double>(h->D, h->L[l - 1].g, Lv.g, 1, src, P.u0, h->stream);
+    CKL();
+  }
+  return ST_OK;
+}
+
+// One PFASST iteration on the finest iterate Ud.
+int pf_iteration(st_handle* h, double* Ud) {
+  const int nl = (int)h->pf.size();
+  const int ns = h->o.pfasst_sweeps;
+  const int Nt = h->p.Nt;
+  auto lvU = [&](int l) { return l == 0 ? Ud : h->pf[l].U; };
+  auto lvM = [&](int l) { return l == 0 ? h->p.M : h->pf[l].M; };
+  auto lvu0 = [&](int l) { return l == 0 ? (const double*)h->u0 : (const double*)h->pf[l].u0; };
+  auto lvtau = [&](int l) { return l == 0 ? (const double*)nullptr : (const double*)h->pf[l].tau; };
+  auto lvW = [&](int l) { return l == 0 ? h->pfW0 : h->pf[l].W; };
+  if (nl == 1) {
+    for (int s = 0; s < ns; ++s) TRY(pf_sweep(h, 0, lvM(0), Ud, lvu0(0), nullptr, 0, Nt));
+    return ST_OK;
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    for (int s = 0; s < ns; ++s) TRY(pf_sweep(h, l, lvM(l), lvU(l), lvu0(l), lvtau(l), 0, Nt));
+    PfLevel& C = h->pf[l + 1];
+    // tau_{l+1} = R(dt Q F(U_l) + tau_l) - dt Q F(R U_l)
+    TRY(pf_integrals(h, l, lvM(l), lvU(l), lvu0(l), lvtau(l), lvW(l)));
+    TRY(pf_restrict(h, l, lvM(l), lvW(l), C.tau));
+    TRY(pf_restrict(h, l, lvM(l), lvU(l), C.U));
+    TRY(pf_integrals(h, l + 1, C.M, C.U, C.u0, nullptr, C.W));
+    launch_axpby(1, C.tau, C.W, -1.0, 1.0, (long long)h->L[l + 1].g.Ns * Nt * C.M, h->stream);
+    CKL();
+    CK(cudaMemcpyAsync(C.Ubar, C.U, (size_t)h->L[l + 1].g.Ns * Nt * C.M * sizeof(double),
+                       cudaMemcpyDeviceToDevice, h->stream));
+  }
+  // the coarsest level, slab after slab
+  const int c = nl - 1;
+  for (int n = 0; n < Nt; ++n)
+    for (int s = 0; s < ns; ++s) TRY(pf_sweep(h, c, lvM(c), lvU(c), lvu0(c), lvtau(c), n, 1));
+  // back up: U_l += P(U_{l+1} - Ubar_{l+1}), sweeps on the levels in between
+  for (int l = nl - 2; l >= 0; --l) {
+    PfLevel& C = h->pf[l + 1];
+    launch_axpby(1, C.Ubar, C.U, 1.0, -1.0, (long long)h->L[l + 1].g.Ns * Nt * C.M, h->stream);
+    CKL();
+    TRY(pf_prolong_add(h, l, lvM(l), C.Ubar, lvU(l)));
+    if (l > 0)
+      for (int s = 0; s < ns; ++s) TRY(pf_sweep(h, l, lvM(l), lvU(l), lvu0(l), lvtau(l), 0, Nt));
+  }
+  return ST_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1170,6 +1368,9 @@ void st_default_opts(st_solver_opts* o) {
   o->krylov = 0;
   o->krylov_rtol = 1e-2;
   o->krylov_fallback = 10;
+  o->pfasst_levels = 3;
+  o->pfasst_coarse_M = 1;
+  o->pfasst_sweeps = 1;
 }
 
 const char* st_status_str(int s) {
@@ -1592,6 +1793,39 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
   CK(cudaStreamSynchronize(h->stream));
   fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
   if (info) info->cycles = cycles;
+  return status;
+}
+
+int st_pfasst(st_handle* h, double* U, st_solve_info* info) {
+  PdlScope pdl_scope(h);
+  if (!h || !U) return ST_ERR_INVALID_ARG;
+  for (size_t l = 0; l + 1 < h->L.size(); ++l)
+    if ((int)l + 1 < h->o.pfasst_levels && h->L[l].next != 1) return ST_ERR_UNSUPPORTED;
+  const int nl = std::min(h->o.pfasst_levels, (int)h->L.size());
+  const double t0 = now_s();
+  double* Ud = nullptr;
+  TRY(stage_in(h, U, &Ud, true));
+  TRY(pf_setup(h, nl));
+  const double ref = ref_norm(h);
+  std::vector<double> hist;
+  int status = ST_ERR_NOT_CONVERGED;
+  double rel = 0, nrm = 0;
+  int it = 0;
+  for (;;) {
+    TRY(fine_residual(h, Ud, nullptr, 1, false, 0));
+    TRY(read_scalars(h, 1));
+    nrm = std::sqrt(h->hscal[0]);
+    rel = nrm / ref;
+    hist.push_back(rel);
+    if (!std::isfinite(rel) || rel > 1e8) { status = ST_ERR_DIVERGED; break; }
+    if (rel <= h->o.tol) { status = ST_OK; break; }
+    if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
+    TRY(pf_iteration(h, Ud));
+    ++it;
+  }
+  TRY(stage_out(h, U, Ud));
+  CK(cudaStreamSynchronize(h->stream));
+  fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
   return status;
 }
 

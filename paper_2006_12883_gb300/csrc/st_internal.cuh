@@ -333,6 +333,8 @@ struct ResidParams {
   void* R;             // output residual (float or double, may be null)
   void* cbar;          // output mean_m R'(U) (may be null)
   void* cnode;         // output R'(U) at every node, layout of U (may be null)
+  const double* tau;   // added to G (FAS correction of a coarse PFASST level; may be null;
+                       // honoured by the FP64-arithmetic kernel only)
   double* partial;     // per-block sums of squares (may be null)
 };
 

@@ -82,6 +82,8 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st);
 void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st);
 void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st);
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st);
+// W += U - prev (the slab's initial value on every node): G(U) -> dt Q F(U) + tau
+void launch_add_state(double* W, const double* U, const double* u0, long long Ns, int Nt, int M, cudaStream_t st);
 // U += alpha * e (n values)
 void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha = 1.0);
 void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,

@@ -104,6 +104,7 @@ extern "C" int st_residual_noalloc(const st_problem* p, const double* U, double*
   rp.R = R;
   rp.cbar = nullptr;
   rp.cnode = nullptr;
+  rp.tau = nullptr;
   double* scratch = nullptr;
   int s = scratch_address(&scratch);
   if (s != ST_OK) return s;

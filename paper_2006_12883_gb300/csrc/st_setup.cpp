@@ -353,4 +353,17 @@ int node_transfer_setup(int Mf, int Mc, double P[MAXM][MAXM], double R[MAXM][MAX
   return 0;
 }
 
+int node_eval_setup(int Mfrom, int Mto, double X[MAXM][MAXM]) {
+  if (Mfrom < 1 || Mto < 1 || Mfrom > MAXM || Mto > MAXM) return -1;
+  Colloc cf, ct;
+  if (colloc_setup(Mfrom, &cf) != 0 || colloc_setup(Mto, &ct) != 0) return -2;
+  LD tf[MAXM];
+  for (int m = 0; m < Mfrom; ++m) tf[m] = cf.tau[m];
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) X[a][b] = 0.0;
+  for (int i = 0; i < Mto; ++i)
+    for (int j = 0; j < Mfrom; ++j) X[i][j] = (double)lagrange(tf, Mfrom, j, (LD)ct.tau[i]);
+  return 0;
+}
+
 }  // namespace st

@@ -33,4 +33,9 @@ int colloc_setup(int M, Colloc* out);
 // 0 on success, negative on failure.
 int node_transfer_setup(int Mf, int Mc, double P[MAXM][MAXM], double R[MAXM][MAXM]);
 
+// X (Mto x Mfrom): the nodal polynomial on the Mfrom Radau nodes evaluated
+// at the Mto Radau nodes (value restriction / interpolation between node
+// sets).  0 on success.
+int node_eval_setup(int Mfrom, int Mto, double X[MAXM][MAXM]);
+
 }  // namespace st

@@ -41,7 +41,8 @@ class StSolverOpts(ctypes.Structure):
                 ("use_pdl", c_int), ("smooth_inner_levels", c_int),
                 ("smooth_sweeps", c_int), ("line_search", c_int),
                 ("exact_jacobian", c_int), ("krylov", c_int), ("krylov_rtol", c_double),
-                ("krylov_fallback", c_int)]
+                ("krylov_fallback", c_int), ("pfasst_levels", c_int), ("pfasst_coarse_M", c_int),
+                ("pfasst_sweeps", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -106,6 +107,7 @@ _SIGS = {
     "st_collocation": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "st_time_transfer": (c_int, [c_int, c_void_p, c_void_p]),
     "st_node_transfer": (c_int, [c_int, c_int, c_void_p, c_void_p]),
+    "st_pfasst": (c_int, [c_void_p, c_void_p, c_void_p]),
     "st_num_levels": (c_int, [c_void_p]),
     "st_level_info_get": (c_int, [c_void_p, c_int, POINTER(StLevelInfo)]),
     "st_linearize": (c_int, [c_void_p, c_void_p]),
@@ -344,6 +346,16 @@ class Solver:
         s = lib().st_solve(self.h, self._ptr(U), ctypes.byref(info))
         if raise_on_error and s not in (ST_OK,):
             raise StError(s, "st_solve")
+        d = info.as_dict()
+        d["status"] = s
+        return d
+
+    def pfasst(self, U, raise_on_error=True):
+        """PFASST iterations on U (start iterate in, solution out)."""
+        info = StSolveInfo()
+        s = lib().st_pfasst(self.h, self._ptr(U), ctypes.byref(info))
+        if raise_on_error and s != ST_OK:
+            raise StError(s, "st_pfasst")
         d = info.as_dict()
         d["status"] = s
         return d
