@@ -543,8 +543,10 @@ void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], 
 
 template <typename T>
 void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value)
+  if constexpr (std::is_same<T, float>::value) {
+    if (!zero && tl_tma && launch_jacobi_tma(D, p, st)) return;
     if (!zero && launch_inner4(D, 1, p, st)) return;
+  }
   const unsigned nb = nblk(p.g.Ns * p.Nt, 256);
   if (zero) st_launch(k_inner_jacobi_zero<T>, nb, 256, 0, st, p);
   else DISPATCH_D(D, (st_launch(k_inner_jacobi<DD, T>, nb, 256, 0, st, p)));

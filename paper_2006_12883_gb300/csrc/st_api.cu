@@ -16,6 +16,7 @@ using namespace st;
 
 namespace st {
 thread_local int tl_pdl = 1;
+thread_local int tl_tma = 0;
 }
 
 namespace {
@@ -300,6 +301,7 @@ size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
 // Krylov dot products
 const int kHostScalars = 80;
 const int kHostKrylov = 16;
+const int kHostFlag = 8;  // an int: the TMA wait flag
 
 }  // namespace
 
@@ -353,6 +355,7 @@ struct st_handle {
   cudaEvent_t ev_lvl[ST_MAX_LEVELS + 1] = {};
   bool split_lin = false;  // set while that graph's cycle is enqueued
   int nt_override = 0;     // > 0: inner solves act on this many slabs from the first
+  int* tma_err = nullptr;   // device flag of the TMA-staged kernels (this device's copy)
   std::vector<PfLevel> pf;  // PFASST levels 1.. (allocated at first use)
   double* pfW0 = nullptr;   // PFASST work on the finest level
   long long D_total = 0;
@@ -363,9 +366,17 @@ namespace {
 
 // Launch mode of the calling thread for the duration of one API call.
 struct PdlScope {
-  int saved;
-  explicit PdlScope(const st_handle* h) : saved(tl_pdl) { if (h) tl_pdl = h->o.use_pdl ? 1 : 0; }
-  ~PdlScope() { tl_pdl = saved; }
+  int saved, saved_tma;
+  explicit PdlScope(const st_handle* h) : saved(tl_pdl), saved_tma(tl_tma) {
+    if (h) {
+      tl_pdl = h->o.use_pdl ? 1 : 0;
+      tl_tma = h->o.use_tma ? 1 : 0;
+    }
+  }
+  ~PdlScope() {
+    tl_pdl = saved;
+    tl_tma = saved_tma;
+  }
 };
 
 void* dev_alloc(st_handle* h, size_t bytes) {
@@ -970,7 +981,14 @@ int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_
 
 int read_scalars(st_handle* h, int n) {
   CK(cudaMemcpyAsync(h->hscal, h->scal, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  int* hflag = reinterpret_cast<int*>(h->hscal + kHostFlag);
+  *hflag = 0;
+  if (h->tma_err) CK(cudaMemcpyAsync(hflag, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (*hflag) {  // a TMA-staged kernel gave up waiting for its copies
+    CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
+    return ST_ERR_TIMEOUT;
+  }
   return ST_OK;
 }
 
@@ -1371,6 +1389,7 @@ void st_default_opts(st_solver_opts* o) {
   o->pfasst_levels = 3;
   o->pfasst_coarse_M = 1;
   o->pfasst_sweeps = 1;
+  o->use_tma = 0;
 }
 
 const char* st_status_str(int s) {
@@ -1611,6 +1630,8 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
       return fail(ST_ERR_CUDA);
     }
   }
+  h->tma_err = tma_error_flag();
+  tma_prepare();
   int s = st_set_u0(h, pin->u0);
   if (s != ST_OK) return fail(s);
   // zero the cycle buffers once (cbar stays 0 for linear problems)

@@ -59,6 +59,17 @@ struct KrylovCoef {
   double c[32];
 };
 
+// k_tma.cu: the Jacobi sweep with TMA-staged tiles (2D periodic, x % 64, y % 16,
+// M = 3 or 5, FP32); false when the shape does not qualify (nothing launched)
+extern thread_local int tl_tma;
+bool jacobi_tma_ok(int D, const InnerParams<float>& p);
+bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st);
+// device address of the flag a TMA-staged kernel sets when a wait expires
+int* tma_error_flag();
+// once per handle, outside any stream capture: the tensor-map encoder and the
+// kernels' shared-memory limits and residency
+void tma_prepare();
+
 // k_krylov.cu
 // number of doubles the partial-sum buffer of launch_mdot needs for n values
 long long krylov_partials(long long n);

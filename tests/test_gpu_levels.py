@@ -8,7 +8,8 @@ import pytest
 import stgen
 from oracle import multilevel as ml
 from oracle import space, system
-from tests.gpu_cases import CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, SMMG1D, SMMG2D, Case
+from tests.gpu_cases import (CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, RAGGED, SMMG1D, SMMG2D, TILED_M5,
+                             Case)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -177,28 +178,33 @@ def test_smoothing_step_converged_inner(case, ej):
     S.close()
 
 
-@pytest.mark.parametrize("case", [HEAT1D, LOG2D, DIR2D_M5, PER2D_M5], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [HEAT1D, LOG2D, DIR2D_M5, PER2D_M5, RAGGED, TILED_M5], ids=lambda c: c.name)
 @pytest.mark.parametrize("sweeps", [2, 3, 5])
-def test_smoothing_step_jacobi_slab_solves(case, sweeps):
+@pytest.mark.parametrize("tma", [0, 1], ids=["direct", "tma"])
+def test_smoothing_step_jacobi_slab_solves(case, sweeps, tma):
     """On a level that coarsens in space next, the default smoother replaces
     each slab solve by a few weighted-Jacobi sweeps on the eigen-decoupled
     shifted systems (no inner multigrid): compared with the oracle's
     complex-arithmetic version of exactly that step."""
-    p, S, U = _setup(case, "fp64", smooth_inner_levels=1, smooth_sweeps=sweeps, exact_jacobian=sweeps % 2)
+    if tma and case not in (RAGGED, TILED_M5):
+        pytest.skip("the TMA-staged sweep takes 2D periodic grids in whole 64 x 16 tiles")
+    p, S, U = _setup(case, "fp32" if tma else "fp64", smooth_inner_levels=1, smooth_sweeps=sweeps,
+                     exact_jacobian=sweeps % 2, use_tma=tma)
     info = S.level_info(0)
     assert info["next_kind"] == 1
     cb = S.level_cbar(0).cpu().numpy()
     lev = _oracle_level(S, case, 0, cb.reshape(cb.shape[0], -1), U if sweeps % 2 else None)
     shp = S.level_shape(0)
-    e = stgen.random_field(shp, 510)
-    r = stgen.random_field(shp, 511)
-    et = torch.tensor(e, device="cuda")
-    S.level_smooth(0, et, torch.tensor(r, device="cuda"))
+    et = torch.tensor(stgen.random_field(shp, 510), dtype=S.cycle_dtype, device="cuda")
+    rt = torch.tensor(stgen.random_field(shp, 511), dtype=S.cycle_dtype, device="cuda")
+    e, r = et.double().cpu().numpy(), rt.double().cpu().numpy()
+    S.level_smooth(0, et, rt)
     omega_j = {1: 2.0 / 3.0, 2: 0.8, 3: 6.0 / 7.0}[len(case.shape)]
     ref = ml.smoothing_step_jacobi(lev, e.reshape(lev.Nt, p.M, -1), r.reshape(lev.Nt, p.M, -1), info["omega"],
                                    sweeps, omega_j)
-    err = np.abs(et.cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max()
-    assert err < 1e-12, err
+    err = np.abs(et.double().cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max()
+    # FP32: a few ulps times the conditioning of the eigenbasis (M = 5) and the sweeps
+    assert err < (5e-5 if tma else 1e-12), err
     S.close()
 
 
@@ -216,3 +222,18 @@ def test_level_vcycle_contracts(case, transpose):
     ratio = float(res.norm() / r.norm())
     assert ratio < 0.6, ratio
     S.close()
+
+
+@pytest.mark.parametrize("case", [RAGGED, TILED_M5], ids=lambda c: c.name)
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_tma_staged_sweeps_equal_direct_loads(case, prec):
+    """With use_tma, Jacobi sweeps on 2D periodic grids in whole 64 x 16 tiles
+    stage their operands through TMA copies; the arithmetic is the same as
+    the direct-load kernel's, so a V-cycle gives identical results either way."""
+    outs = []
+    for tma in (1, 0):
+        p, S, U = _setup(case, prec, use_tma=tma)
+        r = torch.tensor(stgen.random_field(S.level_shape(0), 700), dtype=S.cycle_dtype, device="cuda")
+        outs.append(S.level_vcycle(r).cpu())
+        S.close()
+    assert torch.equal(outs[0], outs[1])
