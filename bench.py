@@ -154,8 +154,8 @@ class ClockSampler:
 # `python bench.py --probe` (profiles/); valid only for the kernel source it
 # was taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # profiles/hot_kernels_logistic2d_256_Nt256_M3.md: 671.1 MB read + 177.4 MB written
-    "k_inner4": {"file": "k_level4.cu", "sha256": "df772311479d6f0e557c52278e475f7b0b2c30e15cb4552ffc0cf85cefcdbaa8", "dram_bytes": 848482560},
+    # filled from the ncu capture summarised in profiles/hot_kernels_logistic2d_256_Nt256_M3.md
+    "k_jacobi_tma": {"file": "k_tma.cu", "sha256": "", "dram_bytes": 0},
 }
 
 
@@ -322,9 +322,10 @@ def run_ours(args):
     # list): the fine-level Jacobi sweep of the shifted slab systems, fused with
     # the back-transform and the block-Jacobi update; HBM bound
     k = kernels["slab_jacobi"]
-    roofline = {"bound": "hbm", "kernel": "k_inner4<2,3,1>: fine-level Jacobi sweep + back-transform + update",
+    roofline = {"bound": "hbm", "kernel": "k_jacobi_tma<3>: fine-level Jacobi sweep + back-transform + update of e "
+                                          "(TMA-staged tiles)",
                 "achieved": k["GBps"], "peak": hbm, "unit": "GB/s", "frac": k["GBps"] / hbm,
-                "traffic": ncu_traffic("k_inner4", D),
+                "traffic": ncu_traffic("k_jacobi_tma", D),
                 "peak_source": f"{src} copy bandwidth (burst; kernel timed alone)",
                 "bytes_per_dof": k["bytes"] / D}
     kf = kernels["fine_residual_fp64"]

@@ -153,12 +153,12 @@ typedef struct {
   int pfasst_coarse_M;  /* st_pfasst: nodes per slab on the levels above the
                            finest (default 1) */
   int pfasst_sweeps;    /* st_pfasst: SDC sweeps per level and visit (default 1) */
-  int use_tma;          /* 1: Jacobi sweeps on 2D periodic grids with x % 64 == 0,
-                           y % 16 == 0 and M = 3 or 5 stage their tiles through
-                           TMA copies (persistent, two stages); a wait that
-                           expires makes the call report ST_ERR_TIMEOUT.
-                           0 (default): direct float4 loads, which measure as
-                           fast inside the cycle graph. */
+  int use_tma;          /* 1 (default): the Jacobi sweep that also updates e
+                           (the last of a slab solve) on 2D periodic grids with
+                           x % 64 == 0, y % 16 == 0 and M = 3 or 5 stages its
+                           tiles through TMA copies (persistent, two stages); a
+                           wait that expires makes the call report
+                           ST_ERR_TIMEOUT.  0: direct float4 loads. */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must

@@ -525,8 +525,10 @@ __global__ void __launch_bounds__(256) k_cbar_time(GridP g, int Ntc, const T* __
 
 template <typename T>
 void launch_lin_residual(int D, const LinParams<T>& p, cudaStream_t st) {
-  if constexpr (std::is_same<T, float>::value)
+  if constexpr (std::is_same<T, float>::value) {
+    if (tl_tma && launch_linres_tma(D, p, st)) return;
     if (launch_lin_residual4(D, p, st)) return;
+  }
   const unsigned nb = nblk((long long)p.g.Ns * p.nchunks, 256);
   DISPATCH_D(D, (st_launch(k_lin_residual<DD, T>, nb, 256, 0, st, p)));
 }

@@ -1,5 +1,6 @@
 // TMA-staged Jacobi sweep of the Q-diagonalised slab systems on 2D periodic
-// grids (x size a multiple of 64, y size a multiple of 16, M = 3 or 5, FP32):
+// grids (x size a multiple of 64, y size a multiple of 16, M = 3 or 5, FP32),
+// used for the sweep that also updates e (the last of a slab solve):
 // the same arithmetic as k_inner4<2, M, 1> in k_level4.cu, with the operands
 // of a 64 x 16 tile (z, y, e of every plane and cbar) brought into shared
 // memory by cp.async.bulk.tensor copies and the one-point halo of z by plain
@@ -275,8 +276,215 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
   }
 }
 
+// ---------------------------------------------------------------------------
+// The level residual r - A e + C e (forward) with the Q-eigenbasis transform
+// and the optional zero-start Jacobi iterate (or without the transform), as
+// k_lin_residual4<2, M> computes it, with e, r, cbar and the previous slab's
+// last node plane of e staged by TMA copies and the halo of e prefetched.
+// ---------------------------------------------------------------------------
+struct LinMaps {
+  CUtensorMap e, r, cb, out;
+};
+
+template <int M>
+struct LinSmem {
+  float e[kStages][M][kTH][kTW];
+  float r[kStages][M][kTH][kTW];
+  float ep[kStages][kTH][kTW];     // last node of the previous slab (coupling)
+  float cb[kStages][kTH][kTW];
+  float erow[kStages][M][2][kTW];
+  float ecol[kStages][M][kTH][2];
+  unsigned long long bar[kStages];
+};
+
+template <int M>
+__global__ void __launch_bounds__(256, 2) k_linres_tma(const __grid_constant__ LinMaps maps, LinParams<float> p) {
+  grid_dep_wait();
+  extern __shared__ __align__(128) unsigned char smraw[];
+  LinSmem<M>& S = *reinterpret_cast<LinSmem<M>*>(smraw);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int n0 = p.g.n0, n1 = p.g.n1;
+  const long long Ns = p.g.Ns;
+  const int ntx = n0 / kTW, nty = n1 / kTH;
+  const int per_slab = ntx * nty;
+  const int ntiles = per_slab * p.Nt;
+  const bool has_cb = p.cbar != nullptr;
+  auto tile_bytes = [&](int n) {
+    return (unsigned)(kTH * kTW * 4) * (2 * M + (n > 0 ? 1 : 0) + (has_cb ? 1 : 0));
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&S.bar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int t, int s) {
+    const int n = t / per_slab, r = t - n * per_slab;
+    const int j0 = (r / ntx) * kTH, i0 = (r % ntx) * kTW;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect(&S.bar[s], tile_bytes(n));
+    for (int pl = 0; pl < M; ++pl) {
+      const int row = (n * M + pl) * n1 + j0;
+      tma_2d(&S.e[s][pl][0][0], &maps.e, i0, row, &S.bar[s]);
+      tma_2d(&S.r[s][pl][0][0], &maps.r, i0, row, &S.bar[s]);
+    }
+    if (n > 0) tma_2d(&S.ep[s][0][0], &maps.e, i0, ((n - 1) * M + (M - 1)) * n1 + j0, &S.bar[s]);
+    if (has_cb) tma_2d(&S.cb[s][0][0], &maps.cb, i0, n * n1 + j0, &S.bar[s]);
+  };
+  constexpr int kHaloRow = M * 2 * kTW, kHalo = kHaloRow + M * kTH * 2;
+  constexpr int kPer = (kHalo + 255) / 256;
+  auto halo_load = [&](int t, float v[kPer]) {
+    const int n = t / per_slab, r = t - n * per_slab;
+    const int j0 = (r / ntx) * kTH, i0 = (r % ntx) * kTW;
+    const int jn = (j0 == 0 ? n1 : j0) - 1, js = (j0 + kTH == n1) ? 0 : j0 + kTH;
+    const int il = (i0 == 0 ? n0 : i0) - 1, ir = (i0 + kTW == n0) ? 0 : i0 + kTW;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = threadIdx.x + 256 * u;
+      if (q < kHaloRow) {
+        const int pl = q / (2 * kTW), side = (q / kTW) & 1, x = q % kTW;
+        v[u] = p.e[((long long)n * M + pl) * Ns + (long long)(side ? js : jn) * n0 + i0 + x];
+      } else if (q < kHalo) {
+        const int qq = q - kHaloRow;
+        const int pl = qq / (2 * kTH), row = (qq >> 1) % kTH, side = qq & 1;
+        v[u] = p.e[((long long)n * M + pl) * Ns + (long long)(j0 + row) * n0 + (side ? ir : il)];
+      }
+    }
+  };
+  auto halo_store = [&](int s, const float v[kPer]) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = threadIdx.x + 256 * u;
+      if (q < kHaloRow) {
+        const int pl = q / (2 * kTW), side = (q / kTW) & 1, x = q % kTW;
+        S.erow[s][pl][side][x] = v[u];
+      } else if (q < kHalo) {
+        const int qq = q - kHaloRow;
+        const int pl = qq / (2 * kTH), row = (qq >> 1) % kTH, side = qq & 1;
+        S.ecol[s][pl][row][side] = v[u];
+      }
+    }
+  };
+  float hv[kPer];
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  if ((int)blockIdx.x < ntiles) {
+    halo_load(blockIdx.x, hv);
+    halo_store(0, hv);
+  }
+  bool failed = false;
+  int it = 0;
+  int t = blockIdx.x;
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int tn = t + gridDim.x;
+    if (threadIdx.x == 0 && tn < ntiles) issue(tn, s ^ 1);
+    if (tn < ntiles) halo_load(tn, hv);
+    const int n = t / per_slab, r = t - n * per_slab;
+    const int j0 = (r / ntx) * kTH, i0 = (r % ntx) * kTW;
+    if (!mbar_wait(&S.bar[s], (unsigned)((it >> 1) & 1))) {
+      failed = true;
+      if (threadIdx.x == 0) atomicExch(&g_tma_error, 1);
+    }
+    __syncthreads();
+    if (__syncthreads_or(failed)) break;
+    const int c0 = 4 * tx;
+    auto ld = [](const float* a, float v[4]) {
+      const float4 x = *reinterpret_cast<const float4*>(a);
+      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    };
+    float cb[4] = {0.f, 0.f, 0.f, 0.f}, carry[4] = {0.f, 0.f, 0.f, 0.f};
+    if (has_cb) ld(&S.cb[s][ty][c0], cb);
+    if (n > 0) ld(&S.ep[s][ty][c0], carry);
+    float ev[M][4], Fe[M][4];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      ld(&S.e[s][b][ty][c0], ev[b]);
+      const float xl = tx == 0 ? S.ecol[s][b][ty][0] : S.e[s][b][ty][c0 - 1];
+      const float xr = tx == 15 ? S.ecol[s][b][ty][1] : S.e[s][b][ty][c0 + 4];
+      const float v[6] = {xl, ev[b][0], ev[b][1], ev[b][2], ev[b][3], xr};
+      float lo[4], hi[4];
+      ld(ty == 0 ? &S.erow[s][b][0][c0] : &S.e[s][b][ty - 1][c0], lo);
+      ld(ty == kTH - 1 ? &S.erow[s][b][1][c0] : &S.e[s][b][ty + 1][c0], hi);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Fe[b][q] = cb[q] * ev[b][q];
+        Fe[b][q] = fmaf(p.sc.k2, ev[b][q], Fe[b][q]);
+        Fe[b][q] = fmaf(p.sc.cx, v[q] + v[q + 2], Fe[b][q]);
+        Fe[b][q] = fmaf(p.sc.cy, lo[q] + hi[q], Fe[b][q]);
+      }
+    }
+    float res[M][4];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      float r4[4];
+      ld(&S.r[s][a][ty][c0], r4);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float acc = r4[q] - ev[a][q];
+#pragma unroll
+        for (int b = 0; b < M; ++b) acc = fmaf(p.W[a][b], Fe[b][q], acc);
+        res[a][q] = acc + carry[q];
+      }
+    }
+    const long long base = (long long)n * M * Ns + (long long)(j0 + ty) * n0 + i0 + c0;
+    if (p.transform) {
+      float y[M][4];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int b = 0; b < M; ++b) acc = fmaf(p.F[a][b], res[b][q], acc);
+          y[a][q] = acc;
+        }
+        *reinterpret_cast<float4*>(p.out + base + (long long)a * Ns) = make_float4(y[a][0], y[a][1], y[a][2], y[a][3]);
+      }
+      if (p.zout) {
+#pragma unroll
+        for (int pl = 0; pl < M; ++pl) {
+          const int kd = p.sh.kind[pl];
+          if (kd == SH_REAL || kd == SH_RE) {
+            const int pi = pl + 1 < M ? pl + 1 : pl;
+            float zr[4], zi[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float dprime = p.sc.k2 + cb[q];
+              const float sr = p.sh.sr[pl], si = p.sh.si[pl];
+              if (kd == SH_REAL) {
+                zr[q] = p.omega_j * y[pl][q] / (1.f - sr * dprime);
+                zi[q] = 0.f;
+              } else {
+                const float dr = 1.f - sr * dprime, di = -si * dprime;
+                const float inv = p.omega_j / (dr * dr + di * di);
+                zr[q] = (y[pl][q] * dr + y[pi][q] * di) * inv;
+                zi[q] = (y[pi][q] * dr - y[pl][q] * di) * inv;
+              }
+            }
+            *reinterpret_cast<float4*>(p.zout + base + (long long)pl * Ns) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+            if (kd == SH_RE && pl + 1 < M)
+              *reinterpret_cast<float4*>(p.zout + base + (long long)pi * Ns) =
+                  make_float4(zi[0], zi[1], zi[2], zi[3]);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+        *reinterpret_cast<float4*>(p.out + base + (long long)a * Ns) =
+            make_float4(res[a][0], res[a][1], res[a][2], res[a][3]);
+    }
+    if (tn < ntiles) halo_store(s ^ 1, hv);
+    __syncthreads();
+  }
+  if (failed && threadIdx.x == 0) {
+    mbar_wait(&S.bar[it & 1], (unsigned)((it >> 1) & 1));
+    if (t + (int)gridDim.x < ntiles) mbar_wait(&S.bar[(it + 1) & 1], (unsigned)(((it + 1) >> 1) & 1));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int g_resident[2] = {0, 0};  // resident blocks on the device (M = 3, M = 5)
+int g_resident_lin[2] = {0, 0};
 std::mutex g_prepare_mu;
 
 bool encode(CUtensorMap* map, const float* base, int n0, long long rows) {
@@ -302,6 +510,9 @@ bool jacobi_tma_ok(int D, const InnerParams<float>& p) {
 
 bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st) {
   if (!jacobi_tma_ok(D, p)) return false;
+  // measured: staging pays for the sweep that also reads and updates e (ten
+  // tiles per stage); with seven the direct float4 loads are as fast
+  if (!(p.fuse_bt && !p.e_zero)) return false;
   TmaMaps m;
   memset(&m, 0, sizeof(m));
   const long long rows = (long long)p.Nt * p.P * p.g.n1;
@@ -316,6 +527,27 @@ bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st) {
   const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident[p.P == 3 ? 0 : 1]);
   if (p.P == 3) st_launch(k_jacobi_tma<3>, grid, 256, sizeof(TileSmem<3>), st, m, p);
   else st_launch(k_jacobi_tma<5>, grid, 256, sizeof(TileSmem<5>), st, m, p);
+  return true;
+}
+
+bool launch_linres_tma(int D, const LinParams<float>& p, cudaStream_t st) {
+  // forward operator with e (the stencil variants), node-averaged cbar only
+  if (!(D == 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 % kTW == 0 && p.g.n1 % kTH == 0 &&
+        p.e && !p.transpose && !p.cnode && aligned16(p.e) && aligned16(p.r) && aligned16(p.out) &&
+        (!p.zout || aligned16(p.zout)) && (!p.cbar || aligned16(p.cbar))))
+    return false;
+  const int slot = p.M == 3 ? 0 : 1;
+  if (g_resident_lin[slot] < 1) return false;
+  const long long ntiles = (long long)(p.g.n0 / kTW) * (p.g.n1 / kTH) * p.Nt;
+  if (ntiles < (long long)kMinTilesPerBlock * g_resident_lin[slot]) return false;
+  LinMaps m;
+  memset(&m, 0, sizeof(m));
+  const long long rows = (long long)p.Nt * p.M * p.g.n1;
+  if (!encode(&m.e, p.e, p.g.n0, rows) || !encode(&m.r, p.r, p.g.n0, rows)) return false;
+  if (p.cbar && !encode(&m.cb, p.cbar, p.g.n0, (long long)p.Nt * p.g.n1)) return false;
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident_lin[slot]);
+  if (p.M == 3) st_launch(k_linres_tma<3>, grid, 256, sizeof(LinSmem<3>), st, m, p);
+  else st_launch(k_linres_tma<5>, grid, 256, sizeof(LinSmem<5>), st, m, p);
   return true;
 }
 
@@ -341,6 +573,8 @@ void tma_prepare() {
   };
   g_resident[0] = setup(k_jacobi_tma<3>, sizeof(TileSmem<3>));
   g_resident[1] = setup(k_jacobi_tma<5>, sizeof(TileSmem<5>));
+  g_resident_lin[0] = setup(k_linres_tma<3>, sizeof(LinSmem<3>));
+  g_resident_lin[1] = setup(k_linres_tma<5>, sizeof(LinSmem<5>));
   cudaGetLastError();  // a failed query leaves the TMA path off, not an error
 }
 

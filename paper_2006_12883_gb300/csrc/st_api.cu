@@ -16,7 +16,7 @@ using namespace st;
 
 namespace st {
 thread_local int tl_pdl = 1;
-thread_local int tl_tma = 0;
+thread_local int tl_tma = 1;
 }
 
 namespace {
@@ -1389,7 +1389,7 @@ void st_default_opts(st_solver_opts* o) {
   o->pfasst_levels = 3;
   o->pfasst_coarse_M = 1;
   o->pfasst_sweeps = 1;
-  o->use_tma = 0;
+  o->use_tma = 1;
 }
 
 const char* st_status_str(int s) {

@@ -64,6 +64,8 @@ struct KrylovCoef {
 extern thread_local int tl_tma;
 bool jacobi_tma_ok(int D, const InnerParams<float>& p);
 bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st);
+// the level residual with e (forward, node-averaged cbar), same shapes
+bool launch_linres_tma(int D, const LinParams<float>& p, cudaStream_t st);
 // device address of the flag a TMA-staged kernel sets when a wait expires
 int* tma_error_flag();
 // once per handle, outside any stream capture: the tensor-map encoder and the

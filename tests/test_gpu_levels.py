@@ -18,7 +18,7 @@ P_ = space.PERIODIC
 # a case whose hierarchy mixes space and slab bisection (AUTO_MU) and one
 # with space bisection only (SPACE)
 MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise", seed=5)
-LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D]
+LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, RAGGED, TILED_M5]
 
 
 def _oracle_level(S, case, l, cbar, U=None):
