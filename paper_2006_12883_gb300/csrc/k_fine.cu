@@ -7,6 +7,7 @@
 // register from one slab to the next; consecutive threads own consecutive
 // points (coalesced along x).  The per-block partial sums depend only on this
 // fixed mapping, so norms are bitwise reproducible.
+#include "ff_arith.cuh"
 #include "st_kernels.cuh"
 
 namespace st {
@@ -78,81 +79,9 @@ __global__ void __launch_bounds__(256) k_residual(ResidParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// The same residual in double-float arithmetic on the FP32 pipes, for the
-// FP32 cycle (output rounded to float).  A value is an unevaluated sum
-// hi + lo of two floats (about 48 significant bits).  Error-free
-// transformations: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based
-// exact product error (Dekker 1971); additions use the "sloppy" double-float
-// add whose error is bounded by a few 2^-48 times the operands' magnitudes,
-// which is the scale the residual tolerance is stated in.
+// The same residual in double-float arithmetic (ff_arith.cuh) for the FP32
+// cycle, output rounded to float.
 // ---------------------------------------------------------------------------
-struct ff {
-  float hi, lo;
-};
-
-__device__ __forceinline__ ff two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const ff s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-// a * c with c = chi + clo
-__device__ __forceinline__ ff ff_mul_c(ff a, float chi, float clo) {
-  const float p = a.hi * chi;
-  float e = fmaf(a.hi, chi, -p);
-  e = fmaf(a.hi, clo, e);
-  e = fmaf(a.lo, chi, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) { return ff_mul_c(a, b.hi, b.lo); }
-// acc + a * c
-__device__ __forceinline__ ff ff_madd_c(ff acc, ff a, float chi, float clo) {
-  const float p = a.hi * chi;
-  float e = fmaf(a.hi, chi, -p);
-  e = fmaf(a.hi, clo, e);
-  e = fmaf(a.lo, chi, e);
-  const ff s = two_sum(acc.hi, p);
-  return fast_two_sum(s.hi, s.lo + (acc.lo + e));
-}
-
-// Split a double into hi + lo floats with integer operations only: hi keeps
-// the leading 24 significant bits (truncated), lo the next 29 bits rounded to
-// 24.  Magnitudes below 2^-126 become 0 and lo is dropped below 2^-74; both
-// are far below the residual's rounding level for O(1) data; infinities and
-// NaNs stay infinities and NaNs.
-__device__ __forceinline__ ff split_double(double u) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
-  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
-  const int e = (int)((hw >> 20) & 0x7ffu);
-  const unsigned sign = hw & 0x80000000u;
-  const unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
-  float hi = (e >= 897) ? __uint_as_float(hb) : 0.0f;
-  if (e > 1150) {  // beyond the float range: infinity, or NaN for a NaN input
-    const bool nan = (e == 2047) && (((hw & 0xfffffu) | lw) != 0u);
-    return {__uint_as_float(nan ? 0x7fc00000u : (sign | 0x7f800000u)), 0.0f};
-  }
-  const float scale = __uint_as_float((unsigned)max(e - 948, 0) << 23);  // 2^(e-1075), 0 if subnormal
-  float lo = __uint2float_rn(lw & 0x1fffffffu) * scale;
-  lo = (e >= 949) ? lo : 0.0f;
-  return {hi, sign ? -lo : lo};
-}
-
-struct FFC {
-  float hi, lo;
-};
-struct ResidFF {
-  FFC cx, cy, cz, k2, rho, w[MAXM][MAXM];
-  float rho32;
-};
-
 __device__ __forceinline__ ff nb_ff(const double* __restrict__ p, long long s, long long o, bool valid) {
   return valid ? split_double(p[s + o]) : ff{0.0f, 0.0f};
 }
@@ -357,11 +286,16 @@ static FFC split_const(double v) {
   return c;
 }
 
+static bool al16(const void* q) { return ((unsigned long long)(size_t)q & 15ull) == 0; }
+
 static bool ff4_ok(int D, const ResidParams& p) {
-  return D >= 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 >= 4 && p.g.n0 % 4 == 0;
+  return D >= 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 >= 4 && p.g.n0 % 4 == 0 &&
+         al16(p.U) && al16(p.u0) && al16(p.R) && al16(p.cbar) && al16(p.cnode);
 }
 
 long long residual_ff_blocks(int D, const ResidParams& p) {
+  const long long nt = residual_tile_blocks(D, p);
+  if (nt > 0) return nt;
   return ff4_ok(D, p) ? residual_blocks4(p) : residual_blocks(p);
 }
 
@@ -375,6 +309,7 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
   c.rho32 = (float)p.rho;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) c.w[a][b] = split_const(p.dtq[a][b]);
+  if (launch_residual_tile(D, p, c, st)) return;
   if (ff4_ok(D, p)) {
     const FastDiv fG((unsigned)(p.g.Ns >> 2));
     const unsigned nb4 = (unsigned)residual_blocks4(p);
