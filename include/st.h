@@ -51,7 +51,7 @@ typedef enum {
   ST_ERR_CUDA = 3,          /* a CUDA runtime error (see st_last_error) */
   ST_ERR_NOT_CONVERGED = 4, /* max_iters reached ("n.c." of Section 5.2) */
   ST_ERR_DIVERGED = 5,      /* non-finite or growing residual ("n.c.") */
-  ST_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait expired */
+  ST_ERR_TIMEOUT = 6,       /* a bounded device wait (TMA-staged kernels) expired */
   ST_ERR_UNSUPPORTED = 7    /* valid input the library does not handle */
 } st_status;
 
@@ -243,7 +243,13 @@ int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* n
  * Jacobi in time with Q-diagonalised spatial multigrid slab solves, space /
  * slab bisection transfers, exact forward substitution on the coarsest
  * level; Section 4.2), then U += e.  norm_out receives ||G(U)|| before the
- * update. */
+ * update.  With a device U the call returns as soon as that norm is known:
+ * the linearisation, the cycle and the update of U stay queued on the
+ * handle's stream, so work queued on that stream afterwards (or following a
+ * synchronisation of it) sees the updated U, and back-to-back calls keep the
+ * device busy.  An expired wait of a TMA-staged kernel in that cycle is
+ * reported (ST_ERR_TIMEOUT) by the next call that synchronises.  With a host
+ * U the call returns after U has been copied back. */
 int st_vcycle(st_handle* h, double* U, double* norm_out);
 
 /* nsweeps IMEX SDC sweeps on all slabs at once (Section 4.1; reaction

@@ -64,7 +64,7 @@ __device__ __forceinline__ float tprod(float a, float chi, float clo, float& e) 
 }
 
 template <int M>
-__global__ void __launch_bounds__(256, 2) k_residual_tile(ResidParams p, ResidFF c) {
+__global__ void __launch_bounds__(256, M == 3 ? 3 : 2) k_residual_tile(ResidParams p, ResidFF c) {
   grid_dep_wait();
   __shared__ __align__(16) RSmem S;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;

@@ -19,11 +19,11 @@ static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1
 template <typename T>
 __device__ __forceinline__ void zero_jacobi(T yr, T yi, int cplx, T sr, T si, T dprime, T omega, T& zr, T& zi) {
   if (!cplx) {
-    zr = omega * yr / ((T)1 - sr * dprime);
+    zr = jdiv(omega * yr, (T)1 - sr * dprime);
     zi = (T)0;
   } else {
     const T dr = (T)1 - sr * dprime, di = -si * dprime;
-    const T inv = omega / (dr * dr + di * di);
+    const T inv = jdiv(omega, dr * dr + di * di);
     zr = (yr * dr + yi * di) * inv;
     zi = (yi * dr - yr * di) * inv;
   }
@@ -196,7 +196,7 @@ __device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int
       const long long o = base + (long long)pl * Ns;
       if (kd == SH_REAL) {
         const T dg = (T)1 - sr * dprime;
-        zn[pl] = zr + p.omega * (p.y[o] - (zr - sr * Lr)) / dg;
+        zn[pl] = zr + jdiv(p.omega * (p.y[o] - (zr - sr * Lr)), dg);
       } else if (pl + 1 < MAXM) {
         const T* zpi = zpr + Ns;
         const T zi = zpi[s];
@@ -204,7 +204,7 @@ __device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int
         const T rr = p.y[o] - (zr - sr * Lr + si * Li);
         const T ri = p.y[o + Ns] - (zi - sr * Li - si * Lr);
         const T dr = (T)1 - sr * dprime, di = -si * dprime;
-        const T inv = p.omega / (dr * dr + di * di);
+        const T inv = jdiv(p.omega, dr * dr + di * di);
         zn[pl] = zr + (rr * dr + ri * di) * inv;
         zn[pl + 1 < MAXM ? pl + 1 : pl] = zi + (ri * dr - rr * di) * inv;
       }

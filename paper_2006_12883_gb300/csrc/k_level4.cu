@@ -78,11 +78,11 @@ __device__ __forceinline__ void split4(unsigned idx, const GridP& g, const FastD
 __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float sr, float si, float dprime,
                                             float omega, float& zr, float& zi) {
   if (!cplx) {
-    zr = omega * yr / (1.f - sr * dprime);
+    zr = jdiv(omega * yr, 1.f - sr * dprime);
     zi = 0.f;
   } else {
     const float dr = 1.f - sr * dprime, di = -si * dprime;
-    const float inv = omega / (dr * dr + di * di);
+    const float inv = jdiv(omega, dr * dr + di * di);
     zr = (yr * dr + yi * di) * inv;
     zi = (yi * dr - yr * di) * inv;
   }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(Inner
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float r = yr[q] - (zr[q] - sr * Lr[q]);
-          out[pl][q] = (MODE == 0) ? r : zr[q] + p.omega * r / (1.f - sr * (p.sc.k2 + cb[q]));
+          out[pl][q] = (MODE == 0) ? r : zr[q] + jdiv(p.omega * r, 1.f - sr * (p.sc.k2 + cb[q]));
         }
       } else if (pl + 1 < M) {
         const float* zip = zrp + Ns;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256, inner4_min_blocks<D, M>()) k_inner4(Inner
           } else {
             const float dprime = p.sc.k2 + cb[q];
             const float dr = 1.f - sr * dprime, di = -si * dprime;
-            const float inv = p.omega / (dr * dr + di * di);
+            const float inv = jdiv(p.omega, dr * dr + di * di);
             out[pl][q] = zr[q] + (rr * dr + ri * di) * inv;
             out[pl + 1 < M ? pl + 1 : pl][q] = zi[q] + (ri * dr - rr * di) * inv;
           }

@@ -18,7 +18,7 @@
 
 namespace st {
 
-__device__ int g_tma_error = 0;
+__device__ int g_tma_error = 0;  // count of expired waits (never reset)
 
 namespace {
 
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
     const int j0 = (r / ntx) * kTH, i0 = (r % ntx) * kTW;
     if (!mbar_wait(&S.bar[s], (unsigned)((it >> 1) & 1))) {
       failed = true;
-      if (threadIdx.x == 0) atomicExch(&g_tma_error, 1);
+      if (threadIdx.x == 0) atomicAdd(&g_tma_error, 1);
     }
     __syncthreads();
     if (__syncthreads_or(failed)) break;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const float rres = yr[q] - (zr[q] - sr * Lr[q]);
-            out[pl][q] = zr[q] + p.omega * rres / (1.f - sr * (p.sc.k2 + cb[q]));
+            out[pl][q] = zr[q] + jdiv(p.omega * rres, 1.f - sr * (p.sc.k2 + cb[q]));
           }
         } else if (pl + 1 < M) {
           const int pi = pl + 1 < M ? pl + 1 : pl;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
             const float ri = yi[q] - (zi[q] - sr * Li[q] - si * Lr[q]);
             const float dprime = p.sc.k2 + cb[q];
             const float dr = 1.f - sr * dprime, di = -si * dprime;
-            const float inv = p.omega / (dr * dr + di * di);
+            const float inv = jdiv(p.omega, dr * dr + di * di);
             out[pl][q] = zr[q] + (rr * dr + ri * di) * inv;
             out[pi][q] = zi[q] + (ri * dr - rr * di) * inv;
           }
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256, 2) k_linres_tma(const __grid_constant__ L
     const int j0 = (r / ntx) * kTH, i0 = (r % ntx) * kTW;
     if (!mbar_wait(&S.bar[s], (unsigned)((it >> 1) & 1))) {
       failed = true;
-      if (threadIdx.x == 0) atomicExch(&g_tma_error, 1);
+      if (threadIdx.x == 0) atomicAdd(&g_tma_error, 1);
     }
     __syncthreads();
     if (__syncthreads_or(failed)) break;
@@ -451,11 +451,11 @@ __global__ void __launch_bounds__(256, 2) k_linres_tma(const __grid_constant__ L
               const float dprime = p.sc.k2 + cb[q];
               const float sr = p.sh.sr[pl], si = p.sh.si[pl];
               if (kd == SH_REAL) {
-                zr[q] = p.omega_j * y[pl][q] / (1.f - sr * dprime);
+                zr[q] = jdiv(p.omega_j * y[pl][q], 1.f - sr * dprime);
                 zi[q] = 0.f;
               } else {
                 const float dr = 1.f - sr * dprime, di = -si * dprime;
-                const float inv = p.omega_j / (dr * dr + di * di);
+                const float inv = jdiv(p.omega_j, dr * dr + di * di);
                 zr[q] = (y[pl][q] * dr + y[pi][q] * di) * inv;
                 zi[q] = (y[pi][q] * dr - y[pl][q] * di) * inv;
               }

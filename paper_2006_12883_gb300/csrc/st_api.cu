@@ -301,7 +301,8 @@ size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
 // Krylov dot products
 const int kHostScalars = 80;
 const int kHostKrylov = 16;
-const int kHostFlag = 8;  // an int: the TMA wait flag
+const int kHostFlag = 8;          // an int: the count of expired TMA waits, read synchronously
+const int kHostFlagDeferred = 9;  // an int: the same count, copied behind an asynchronous cycle
 
 }  // namespace
 
@@ -355,7 +356,9 @@ struct st_handle {
   cudaEvent_t ev_lvl[ST_MAX_LEVELS + 1] = {};
   bool split_lin = false;  // set while that graph's cycle is enqueued
   int nt_override = 0;     // > 0: inner solves act on this many slabs from the first
-  int* tma_err = nullptr;   // device flag of the TMA-staged kernels (this device's copy)
+  int* tma_err = nullptr;   // device count of expired TMA waits (this device's copy)
+  int tma_seen = 0;         // the count this handle has reported
+  cudaEvent_t ev_norm = nullptr;  // the residual norm of an asynchronous st_vcycle is on the host
   std::vector<PfLevel> pf;  // PFASST levels 1.. (allocated at first use)
   double* pfW0 = nullptr;   // PFASST work on the finest level
   long long D_total = 0;
@@ -979,17 +982,23 @@ int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_
   return ST_OK;
 }
 
+// A TMA-staged kernel gave up waiting for its copies since this handle last
+// looked: report it once.
+int tma_report(st_handle* h, int count) {
+  if (count > h->tma_seen) {
+    h->tma_seen = count;
+    return ST_ERR_TIMEOUT;
+  }
+  return ST_OK;
+}
+
 int read_scalars(st_handle* h, int n) {
   CK(cudaMemcpyAsync(h->hscal, h->scal, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   int* hflag = reinterpret_cast<int*>(h->hscal + kHostFlag);
   *hflag = 0;
   if (h->tma_err) CK(cudaMemcpyAsync(hflag, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (*hflag) {  // a TMA-staged kernel gave up waiting for its copies
-    CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
-    return ST_ERR_TIMEOUT;
-  }
-  return ST_OK;
+  return tma_report(h, *hflag);
 }
 
 int stage_in(st_handle* h, const double* U, double** Ud, bool copy) {
@@ -1062,6 +1071,37 @@ int outer_step(st_handle* h, double* Ud, bool do_cycle) {
   launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
   CKL();
   return ST_OK;
+}
+
+// One outer iteration on a device iterate that returns as soon as ||G(U)||
+// is known: the norm is copied to the host behind the residual and the call
+// waits for that copy only, while the linearisation, the cycle and the
+// update of U stay queued on the stream (stream order covers every later use
+// of U).  Repeated calls thus keep the device busy: the next residual is
+// queued while this cycle runs.  An expired TMA wait inside the cycle is
+// reported by the next call that synchronises.
+int outer_step_async(st_handle* h, double* Ud, double* norm) {
+  const bool rx = h->p.reaction != ST_REACTION_NONE;
+  const bool relin = rx && (h->o.newton || !h->linearized);
+  int* deferred = reinterpret_cast<int*>(h->hscal + kHostFlagDeferred);
+  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0));
+  CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaEventRecord(h->ev_norm, h->stream));
+  if (relin || !h->coarse_ready) {
+    TRY(lin_cycle(h));
+    h->linearized = true;
+  } else {
+    TRY(cycle(h, 0));
+  }
+  launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
+  CKL();
+  CK(cudaEventSynchronize(h->ev_norm));
+  *norm = std::sqrt(h->hscal[0]);
+  // the count copied behind the previous call's cycle has landed (it precedes
+  // this call's residual on the stream); the next copy goes behind this cycle
+  const int seen = *deferred;
+  if (h->tma_err) CK(cudaMemcpyAsync(deferred, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  return tma_report(h, seen);
 }
 
 // Switch the finest level's operator to the exact Jacobian (allocates R'
@@ -1487,7 +1527,8 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   }
   {
     bool ok = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) == cudaSuccess;
     for (int l = 0; l <= ST_MAX_LEVELS && ok; ++l)
       ok = cudaEventCreateWithFlags(&h->ev_lvl[l], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -1629,8 +1670,13 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
       set_err(cudaGetLastError(), "cudaMallocHost");
       return fail(ST_ERR_CUDA);
     }
+    std::memset(h->hscal, 0, kHostScalars * sizeof(double));
   }
   h->tma_err = tma_error_flag();
+  if (h->tma_err) {  // expiries before this handle existed are not its own
+    int c = 0;
+    if (cudaMemcpy(&c, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) h->tma_seen = c;
+  }
   tma_prepare();
   int s = st_set_u0(h, pin->u0);
   if (s != ST_OK) return fail(s);
@@ -1667,6 +1713,7 @@ void st_destroy(st_handle* h) {
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap2) cudaStreamDestroy(h->cap2);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_norm) cudaEventDestroy(h->ev_norm);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int l = 0; l <= ST_MAX_LEVELS; ++l)
     if (h->ev_lvl[l]) cudaEventDestroy(h->ev_lvl[l]);
@@ -1727,6 +1774,12 @@ int st_residual(st_handle* h, const double* U, void* R, int R_is_fp64, double* n
 int st_vcycle(st_handle* h, double* U, double* norm_out) {
   PdlScope pdl_scope(h);
   if (!h || !U) return ST_ERR_INVALID_ARG;
+  if (is_device_ptr(U)) {
+    double nrm = 0.0;
+    TRY(outer_step_async(h, U, &nrm));
+    if (norm_out) *norm_out = nrm;
+    return ST_OK;
+  }
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
   TRY(outer_step(h, Ud, true));

@@ -319,6 +319,19 @@ struct StencilC {
 };
 
 // Fine FP64 residual (*) and its adjoint; also the SDC right-hand side.
+// Quotient by the diagonal of a shifted slab system in the Jacobi updates:
+// the fast reciprocal-based division in FP32 (error about 2 ulp; a damped
+// Jacobi smoother needs the diagonal inverse only approximately, and every
+// FP32 smoothing kernel uses this same form), the IEEE one in FP64.
+template <typename T>
+__device__ __forceinline__ T jdiv(T a, T b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float jdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
 struct ResidParams {
   GridP g;
   int Nt, M, chunk, nchunks;

@@ -237,3 +237,22 @@ def test_tma_staged_sweeps_equal_direct_loads(case, prec):
         outs.append(S.level_vcycle(r).cpu())
         S.close()
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("case", [RAGGED, TILED_M5], ids=lambda c: c.name)
+def test_staged_whole_cycles_same_bits(case):
+    """Whole FP32 V-cycles (graph replay, with the FP64-accurate residual and
+    the update of U) with and without the TMA-staged kernels give the same
+    iterate to the bit."""
+    from paper_2006_12883_gb300 import stlib
+    outs = []
+    for tma in (1, 0):
+        p = case.problem()
+        S = case.solver(precision=stlib.FP32_REFINE, use_tma=tma)
+        U = torch.tensor(stgen.random_field((p.Nt, p.M, p.Ns), 11, 0.3) + 0.4, device="cuda")
+        U = U.reshape(S.field_shape)
+        S.vcycle(U)
+        S.vcycle(U)
+        outs.append(U.cpu())
+        S.close()
+    assert torch.equal(outs[0], outs[1])
