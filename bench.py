@@ -71,7 +71,7 @@ def make_solver(stlib, w, u0, **opts):
 FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor) per the pool's hardware notes
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
-                 ("prolong_add", 7), ("vcycle_graph", 4))
+                 ("prolong_add", 7), ("slab_jacobi_plain", 8), ("vcycle_graph", 4))
 
 
 def reduce_max(x, dist, device):
@@ -155,8 +155,8 @@ class ClockSampler:
 # was taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
     # filled from the ncu capture summarised in profiles/hot_kernels_logistic2d_256_Nt256_M3.md
-    # 671.2 MB read + 174.2 MB written
-    "k_jacobi_tma": {"file": "k_tma.cu", "sha256": "8a729e011072fe4a4790e601d6f5865ba476581a00d2f13c7d98e8b3a1204148", "dram_bytes": 845362944},
+    # (level-0 launch): 469.8 MB read + 175.2 MB written
+    "k_inner4<2, 3, 1>": {"file": "k_level4.cu", "sha256": "ad356b750a6e4a30675e6c4ce0fdcc037bb9c683ed8301a0e857dd307581c943", "dram_bytes": 644968448},
 }
 
 
@@ -319,23 +319,24 @@ def run_ours(args):
         kms, kb = S.time_kernel(which, U, iters=max(5, args.steps // 2))
         kernels[name] = {"ms": kms, "bytes": kb, "GBps": (kb / (kms / 1e3) / 1e9) if kb else None}
     hbm, src = measured_peaks()
-    # dominant kernel (largest share of the cycle's time in the ncu launch
-    # list): the fine-level Jacobi sweep of the shifted slab systems, fused with
-    # the back-transform and the block-Jacobi update; HBM bound
-    k = kernels["slab_jacobi"]
-    roofline = {"bound": "hbm", "kernel": "k_jacobi_tma<3>: fine-level Jacobi sweep + back-transform + update of e "
-                                          "(TMA-staged tiles)",
+    # dominant kernel (largest share of the step's time in the ncu launch
+    # list): the Jacobi sweep of the shifted slab systems that updates z
+    # (k_inner4<2, 3, 1>, every sweep but a slab solve's last), timed here at
+    # level 0 where it moves the most bytes; HBM bound
+    k = kernels["slab_jacobi_plain"]
+    roofline = {"bound": "hbm", "kernel": "k_inner4<2,3,1>: level-0 Jacobi sweep of the shifted slab systems "
+                                          "(z, y, cbar in, z out; direct float4 loads)",
                 "achieved": k["GBps"], "peak": hbm, "unit": "GB/s", "frac": k["GBps"] / hbm,
-                "traffic": ncu_traffic("k_jacobi_tma", D),
+                "traffic": ncu_traffic("k_inner4<2, 3, 1>", D),
                 "peak_source": f"{src} copy bandwidth (burst; kernel timed alone)",
                 "bytes_per_dof": k["bytes"] / D}
     kf = kernels["fine_residual_fp64"]
-    fine_residual = {"kernel": "k_residual_ff: FP64-accurate residual in double-float arithmetic",
+    fine_residual = {"kernel": "k_residual_tile<3>: FP64-accurate residual on the FP32 pipes (tiles split once)",
                      "ms": kf["ms"], "GBps": kf["GBps"], "frac_of_hbm": kf["GBps"] / hbm,
-                     "note": "issue bound on the FP32/integer pipes (double-float emulation of FP64)"}
+                     "note": "issue bound on the FP32/integer pipes (compensated double-float arithmetic)"}
     fp32_kernels = {n: {"GBps": kernels[n]["GBps"], "frac_of_" + src + "_hbm": kernels[n]["GBps"] / hbm}
-                    for n in ("level_residual_transform", "slab_jacobi", "shifted_residual", "inner_restrict",
-                              "prolong_add")}
+                    for n in ("level_residual_transform", "slab_jacobi", "slab_jacobi_plain", "shifted_residual",
+                              "inner_restrict", "prolong_add")}
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:

@@ -377,7 +377,9 @@ enum {
   ST_KERNEL_VCYCLE = 4,        /* one whole V-cycle (graph replay), not a single kernel */
   ST_KERNEL_SHIFTED_RESIDUAL = 5, /* residual of the level-0 shifted slab systems */
   ST_KERNEL_INNER_RESTRICT = 6,   /* full weighting of that residual to the next inner grid */
-  ST_KERNEL_PROLONG = 7           /* linear interpolation + correction, inner grid 1 -> 0 */
+  ST_KERNEL_PROLONG = 7,          /* linear interpolation + correction, inner grid 1 -> 0 */
+  ST_KERNEL_JACOBI_PLAIN = 8      /* level-0 Jacobi sweep of the shifted slab systems that only
+                                     updates z (the sweeps before the cycle's last) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream

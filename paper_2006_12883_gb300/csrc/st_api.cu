@@ -2183,8 +2183,9 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
   PdlScope pdl_scope(h);
-  if (!h || iters < 1 || which < 0 || which > 7) return ST_ERR_INVALID_ARG;
-  if (which >= ST_KERNEL_SHIFTED_RESIDUAL && h->L[0].in.size() < 2) return ST_ERR_UNSUPPORTED;
+  if (!h || iters < 1 || which < 0 || which > 8) return ST_ERR_INVALID_ARG;
+  if (which >= ST_KERNEL_SHIFTED_RESIDUAL && which <= ST_KERNEL_PROLONG && h->L[0].in.size() < 2)
+    return ST_ERR_UNSUPPORTED;
   if (which == ST_KERNEL_FINE_RESIDUAL && (!U || !is_device_ptr(U))) return ST_ERR_INVALID_ARG;
   Level& L0 = h->L[0];
   const bool rx = h->p.reaction != ST_REACTION_NONE;
@@ -2222,6 +2223,16 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
           for (int a2 = 0; a2 < MAXM; ++a2)
             for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (TT)h->fine->Bf[a2][b];
           apply_fuse(ip, f);
+          launch_inner_jacobi<TT>(h->D, 0, ip, st);
+          CKL();
+          return ST_OK;
+        };
+        return h->fp64 ? go(double(0)) : go(float(0));
+      }
+      case ST_KERNEL_JACOBI_PLAIN: {  // z -> t with the level-0 shifts
+        auto go = [&](auto tag) -> int {
+          using TT = decltype(tag);
+          InnerParams<TT> ip = inner_params<TT>(h, L0, 0, h->p.M, level_shifts<TT>(*L0.ns, L0.dt), rx);
           launch_inner_jacobi<TT>(h->D, 0, ip, st);
           CKL();
           return ST_OK;
@@ -2269,6 +2280,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_FINE_RESIDUAL: bytes = D * (8 + es) + (rx ? planes * es : 0); break;
     case ST_KERNEL_LEVEL_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_JACOBI: bytes = D * 4 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_JACOBI_PLAIN: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
     case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_INNER_RESTRICT: {

@@ -124,7 +124,7 @@ _SIGS = {
 }
 
 KERNEL_FINE_RESIDUAL, KERNEL_LEVEL_RESIDUAL, KERNEL_JACOBI, KERNEL_BACKTRANSFORM, KERNEL_VCYCLE = 0, 1, 2, 3, 4
-KERNEL_SHIFTED_RESIDUAL, KERNEL_INNER_RESTRICT, KERNEL_PROLONG = 5, 6, 7
+KERNEL_SHIFTED_RESIDUAL, KERNEL_INNER_RESTRICT, KERNEL_PROLONG, KERNEL_JACOBI_PLAIN = 5, 6, 7, 8
 
 
 def lib_path() -> str:
