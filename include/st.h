@@ -391,6 +391,14 @@ enum {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch);
 
+/* Self-check of the bounded device waits: launches, on the handle's stream,
+ * one block that waits on an mbarrier nothing will complete, with the limit
+ * the TMA-staged kernels use (about a second).  The wait expires, the block
+ * counts the expiry and returns, and the following synchronisation reports
+ * it: the call returns ST_ERR_TIMEOUT when that chain works (and leaves the
+ * handle usable, the expiry reported once), ST_ERR_CUDA on a CUDA error. */
+int st_wait_selftest(st_handle* h);
+
 typedef struct {
   int levels;
   int cycle_graph_nodes;        /* kernel + memset nodes of one V-cycle */

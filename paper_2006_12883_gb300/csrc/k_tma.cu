@@ -578,6 +578,21 @@ void tma_prepare() {
   cudaGetLastError();  // a failed query leaves the TMA path off, not an error
 }
 
+// One block waiting on an mbarrier that no copy and no thread will complete:
+// the bounded wait of the staged kernels expires, the expiry is counted as
+// theirs are, and the block returns (nothing is in flight).
+__global__ void k_wait_expiry() {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u)) atomicAdd(&g_tma_error, 1);
+}
+
+void launch_wait_expiry(cudaStream_t st) { k_wait_expiry<<<1, 32, 0, st>>>(); }
+
 int* tma_error_flag() {
   void* a = nullptr;
   if (cudaGetSymbolAddress(&a, g_tma_error) != cudaSuccess) return nullptr;

@@ -2319,6 +2319,16 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
   return ST_OK;
 }
 
+int st_wait_selftest(st_handle* h) {
+  if (!h) return ST_ERR_INVALID_ARG;
+  if (!h->tma_err) return ST_ERR_UNSUPPORTED;
+  const int s0 = read_scalars(h, 1);  // earlier expiries are not this call's
+  if (s0 != ST_OK && s0 != ST_ERR_TIMEOUT) return s0;
+  launch_wait_expiry(h->stream);
+  CKL();
+  return read_scalars(h, 1);
+}
+
 int st_stats(st_handle* h, st_stats_info* out) {
   PdlScope pdl_scope(h);
   if (!h || !out) return ST_ERR_INVALID_ARG;

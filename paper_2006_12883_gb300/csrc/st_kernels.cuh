@@ -66,8 +66,11 @@ bool jacobi_tma_ok(int D, const InnerParams<float>& p);
 bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st);
 // the level residual with e (forward, node-averaged cbar), same shapes
 bool launch_linres_tma(int D, const LinParams<float>& p, cudaStream_t st);
-// device address of the flag a TMA-staged kernel sets when a wait expires
+// device address of the count of expired waits of the TMA-staged kernels
 int* tma_error_flag();
+// one block whose bounded mbarrier wait expires (nothing completes it); the
+// expiry is counted like a staged kernel's
+void launch_wait_expiry(cudaStream_t st);
 // once per handle, outside any stream capture: the tensor-map encoder and the
 // kernels' shared-memory limits and residency
 void tma_prepare();

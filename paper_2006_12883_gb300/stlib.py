@@ -120,6 +120,7 @@ _SIGS = {
     "st_level_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "st_time_kernel": (c_int, [c_void_p, c_int, c_void_p, c_int, POINTER(c_double), POINTER(c_double)]),
     "st_stats": (c_int, [c_void_p, POINTER(StStatsInfo)]),
+    "st_wait_selftest": (c_int, [c_void_p]),
     "st_residual_noalloc": (c_int, [POINTER(StProblem), c_void_p, c_void_p, POINTER(c_double), c_void_p]),
 }
 
@@ -386,6 +387,11 @@ class Solver:
         check(lib().st_stats(self.h, ctypes.byref(st)), "st_stats")
         return dict(levels=st.levels, cycle_graph_nodes=st.cycle_graph_nodes,
                     linearize_graph_nodes=st.linearize_graph_nodes, launches_per_vcycle=st.launches_per_vcycle)
+
+    def wait_selftest(self):
+        """Status of st_wait_selftest (ST_ERR_TIMEOUT when a bounded device wait
+        expires, is counted and is reported as it should)."""
+        return lib().st_wait_selftest(self.h)
 
     def adjoint_lambda(self, out=None):
         out = self.zeros() if out is None else out

@@ -182,6 +182,25 @@ def test_error_statuses():
     S.close()
 
 
+def test_bounded_wait_expiry_is_reported_once_and_handle_survives():
+    """Failure detection on the GPU without a fault: one block waits on an
+    mbarrier that nothing completes, with the bounded wait of the TMA-staged
+    kernels.  The wait expires, the block counts it and returns; the host
+    reports ST_ERR_TIMEOUT once, and the handle keeps working (residuals and
+    asynchronous V-cycles give the same numbers as before, no stale report)."""
+    from paper_2006_12883_gb300 import stlib
+    p = LOG2D.problem()
+    S = LOG2D.solver(precision=stlib.FP32_REFINE)
+    U = torch.tensor(stgen.random_field((p.Nt, p.M, p.Ns), 5, 0.3) + 0.4, device="cuda").reshape(S.field_shape)
+    n0 = S.residual(U)
+    assert S.wait_selftest() == stlib.ST_ERR_TIMEOUT
+    assert S.residual(U) == n0
+    V = U.clone()
+    a = [S.vcycle(V) for _ in range(3)]
+    assert S.residual(V) < a[0]
+    S.close()
+
+
 def test_allocator_failure_is_oom():
     from paper_2006_12883_gb300 import stlib
     import ctypes
