@@ -492,7 +492,17 @@ __global__ void __launch_bounds__(256) k_update4(double* __restrict__ U, const T
 // SDC right-hand side for node m (correction form):
 //   y = g_m + sum_{j<m} [ dt*QI_mj*nu*Lap delta_j + dt*QE_mj*(R(U_j + delta_j) - R(U_j)) ]
 // g is G(U^k) (cycle precision), delta holds the corrections of nodes < m.
+// Arithmetic in the cycle precision T; the reaction difference is taken in
+// closed form, rho d (1 - 2u - d) (logistic) or rho d (1 - 3u^2 - 3ud - d^2)
+// (cubic), so a small correction d loses no digits to cancellation.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T react_diff(int reaction, T rho, T u, T d) {
+  if (reaction == ST_REACTION_LOGISTIC) return rho * d * ((T)1 - (T)2 * u - d);
+  if (reaction == ST_REACTION_CUBIC) return rho * d * ((T)1 - (T)3 * u * u - (T)3 * u * d - d * d);
+  return (T)0;
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, double nu, int reaction,
                                                  double rho, SdcCoef cf,
@@ -504,18 +514,17 @@ __global__ void __launch_bounds__(256) k_sdc_rhs(GridP g, int Nt, int M, int m, 
   if (idx >= (unsigned)Nt * (unsigned)g.Ns) return;
   int n, s, i, j, k;
   split_index(idx, g, n, s, i, j, k);
-  const double ihx = g.ih2[0], ihy = g.ih2[1], ihz = g.ih2[2];
-  double acc = (double)G[((long long)n * M + m) * Ns + s];
+  const T ihx = (T)g.ih2[0], ihy = (T)g.ih2[1], ihz = (T)g.ih2[2];
+  const T nuT = (T)nu, rhoT = (T)rho;
+  T acc = G[((long long)n * M + m) * Ns + s];
   for (int q = 0; q < m; ++q) {
     const T* pl = delta + ((long long)n * M + q) * Ns;
-    const double dq = (double)pl[s];
-    acc += cf.qi[q] * nu * lap_at<D, T, double>(pl, s, i, j, k, g, dq, ihx, ihy, ihz);
-    if (reaction != ST_REACTION_NONE) {
-      const double uq = U[((long long)n * M + q) * Ns + s];
-      acc += cf.qe[q] * (react<double>(reaction, rho, uq + dq) - react<double>(reaction, rho, uq));
-    }
+    const T dq = pl[s];
+    acc += (T)cf.qi[q] * nuT * lap_at<D, T, T>(pl, s, i, j, k, g, dq, ihx, ihy, ihz);
+    if (reaction != ST_REACTION_NONE)
+      acc += (T)cf.qe[q] * react_diff<T>(reaction, rhoT, (T)U[((long long)n * M + q) * Ns + s], dq);
   }
-  y[(long long)n * Ns + s] = (T)acc;
+  y[(long long)n * Ns + s] = acc;
 }
 
 // Copy a [Nt][Ns] field into plane m of a [Nt][M][Ns] field.

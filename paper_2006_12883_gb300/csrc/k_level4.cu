@@ -91,10 +91,11 @@ __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// 2D, M = 3 fits 64 registers (4 blocks of 256 per SM); larger instances
-// keep their registers rather than spill.
+// 2D, M = 3 fits 64 registers (4 blocks of 256 per SM), as does one plane
+// (the SDC node solves); larger instances keep their registers rather than
+// spill.
 template <int D, int M>
-constexpr int inner4_min_blocks() { return (D == 2 && M == 3) ? 4 : 1; }
+constexpr int inner4_min_blocks() { return ((D == 2 && M == 3) || M == 1) ? 4 : 1; }
 
 // The level residual keeps M planes of e and their stencil sums live: at most
 // 128 registers (2 blocks per SM) except 2D, M = 3 (64, 4 blocks).
@@ -439,8 +440,14 @@ bool launch_lin_residual4(int D, const LinParams<float>& p, cudaStream_t st) {
   return true;
 }
 
+// the shifted systems of the slab solves (P = M planes) and of the SDC node
+// solves (P = 1)
+static bool inner4_ok(const GridP& g, int D, int P) {
+  return D >= 2 && (P == 1 || P == 3 || P == 5) && g.n0 >= 4 && (g.n0 % 4) == 0 && g.bc == BC_PER;
+}
+
 bool launch_inner4(int D, int mode, const InnerParams<float>& p, cudaStream_t st) {
-  if (!vec4_ok(p.g, D, p.P)) return false;
+  if (!inner4_ok(p.g, D, p.P)) return false;
   const FastDiv fG((unsigned)(p.g.Ns >> 2));
   const unsigned nb = nblk4((p.g.Ns >> 2) * p.Nt);
 #define K4(DD, MM)                                                         \
@@ -450,8 +457,10 @@ bool launch_inner4(int D, int mode, const InnerParams<float>& p, cudaStream_t st
   } while (0)
   if (D == 2 && p.P == 3) K4(2, 3);
   else if (D == 2 && p.P == 5) K4(2, 5);
-  else if (D == 3 && p.P == 3) K4(3, 3);
-  else K4(3, 5);
+  else if (D == 2) K4(2, 1);
+  else if (p.P == 3) K4(3, 3);
+  else if (p.P == 5) K4(3, 5);
+  else K4(3, 1);
 #undef K4
   return true;
 }
@@ -471,13 +480,15 @@ bool launch_restrict4(int D, const GridP& gf, const GridP& gc, long long planes,
 }
 
 bool launch_inner_restrict4(int D, const InnerParams<float>& p, cudaStream_t st) {
-  if (!restrict4_ok(D, p.g, p.gc) || !(p.P == 3 || p.P == 5)) return false;
+  if (!restrict4_ok(D, p.g, p.gc) || !(p.P == 1 || p.P == 3 || p.P == 5)) return false;
   const FastDiv fG((unsigned)(p.gc.Ns >> 2));
   const unsigned nb = nblk4((p.gc.Ns >> 2) * p.Nt);
   if (D == 2 && p.P == 3) st_launch(k_inner_restrict4<2, 3>, nb, 256, 0, st, p, fG);
-  else if (D == 2) st_launch(k_inner_restrict4<2, 5>, nb, 256, 0, st, p, fG);
+  else if (D == 2 && p.P == 5) st_launch(k_inner_restrict4<2, 5>, nb, 256, 0, st, p, fG);
+  else if (D == 2) st_launch(k_inner_restrict4<2, 1>, nb, 256, 0, st, p, fG);
   else if (p.P == 3) st_launch(k_inner_restrict4<3, 3>, nb, 256, 0, st, p, fG);
-  else st_launch(k_inner_restrict4<3, 5>, nb, 256, 0, st, p, fG);
+  else if (p.P == 5) st_launch(k_inner_restrict4<3, 5>, nb, 256, 0, st, p, fG);
+  else st_launch(k_inner_restrict4<3, 1>, nb, 256, 0, st, p, fG);
   return true;
 }
 

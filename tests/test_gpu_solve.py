@@ -9,7 +9,7 @@ import pytest
 import stgen
 from oracle import sdc as osdc
 from oracle import space, system
-from tests.gpu_cases import HEAT1D, LOG2D, MONO, SOLVE_CASES, Case
+from tests.gpu_cases import HEAT1D, LOG2D, MONO, SOLVE_CASES, TILED_M5, Case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -130,6 +130,22 @@ def test_sdc_one_sweep_matches_oracle(case, kind):
     S.sdc_sweep(U, 1)
     ref = osdc.sdc_sweep(p, U0, case.u0(), "IE" if kind == 0 else "LU")
     assert _rel(U.cpu().numpy().reshape(ref.shape), ref) < 1e-9
+    S.close()
+
+
+@pytest.mark.parametrize("case", [LOG2D, TILED_M5], ids=lambda c: c.name)
+def test_sdc_fp32_sweep_matches_oracle(case):
+    """The same sweep with the FP32 node solves (one-plane float4 spatial
+    multigrid on periodic 2D grids) inside the FP64 sweep: equal to the
+    oracle's exact-solve sweep to FP32 accuracy."""
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    S = case.solver(precision=stlib.FP32_REFINE, sdc_inner_cycles=30, inner_coarse_iters=60)
+    U0 = stgen.random_field((p.Nt, p.M, p.Ns), 23, 0.2) + np.tile(case.u0(), (p.Nt, p.M, 1))
+    U = torch.tensor(U0, device="cuda").reshape(S.field_shape)
+    S.sdc_sweep(U, 1)
+    ref = osdc.sdc_sweep(p, U0, case.u0(), "IE")
+    assert _rel(U.cpu().numpy().reshape(ref.shape), ref) < 2e-6
     S.close()
 
 
