@@ -347,8 +347,9 @@ struct st_handle {
   double* plane2 = nullptr;
   std::vector<Alloc> allocs;
   // 0 fwd cycle, 1 adjoint cycle, 2 linearise, 3 linearise + fwd cycle
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-  size_t gnodes[4] = {0, 0, 0, 0};
+  // graphs: 0 forward cycle, 1 adjoint cycle, 2 linearisation, 3 linearisation + cycle, 4 PFASST iteration
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t gnodes[5] = {0, 0, 0, 0, 0};
   // second capture stream and events of the linearise + cycle graph: the
   // cbar chain and the coarse setup run beside the cycle's finest levels
   cudaStream_t cap2 = nullptr;
@@ -361,6 +362,7 @@ struct st_handle {
   cudaEvent_t ev_norm = nullptr;  // the residual norm of an asynchronous st_vcycle is on the host
   std::vector<PfLevel> pf;  // PFASST levels 1.. (allocated at first use)
   double* pfW0 = nullptr;   // PFASST work on the finest level
+  double* pfU = nullptr;    // PFASST: the finest iterate (fixed address for the iteration graph)
   long long D_total = 0;
   int chunk = 1;
 };
@@ -926,7 +928,7 @@ int linearize_levels(st_handle* h) {
 }
 
 void invalidate_graphs(st_handle* h) {
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 5; ++i)
     if (h->gexec[i]) {
       cudaGraphExecDestroy(h->gexec[i]);
       h->gexec[i] = nullptr;
@@ -1327,6 +1329,7 @@ int pf_setup(st_handle* h, int nl) {
   if (!h->pf.empty()) return ST_ERR_INVALID_ARG;  // the hierarchy is fixed per handle
   h->pf.resize(nl);
   TRY(alloc_typed(h, &h->pfW0, (size_t)h->D_total * sizeof(double)));
+  TRY(alloc_typed(h, &h->pfU, (size_t)h->D_total * sizeof(double)));
   for (int l = 1; l < nl; ++l) {
     PfLevel& P = h->pf[l];
     const int Mf = l == 1 ? h->p.M : h->pf[l - 1].M;
@@ -1389,6 +1392,17 @@ int pf_iteration(st_handle* h, double* Ud) {
       for (int s = 0; s < ns; ++s) TRY(pf_sweep(h, l, lvM(l), lvU(l), lvu0(l), lvtau(l), 0, Nt));
   }
   return ST_OK;
+}
+
+// The PFASST iteration on the handle's copy of the iterate, captured once as
+// a graph (its launch sequence is fixed by the hierarchy: the serial coarsest
+// sweep alone is N_t slab sweeps of some twenty launches each).
+int enq_pf_iteration(st_handle* h, cudaStream_t st) {
+  const cudaStream_t saved = h->stream;
+  h->stream = st;
+  const int s = pf_iteration(h, h->pfU);
+  h->stream = saved;
+  return s;
 }
 
 }  // namespace
@@ -1880,13 +1894,14 @@ int st_pfasst(st_handle* h, double* U, st_solve_info* info) {
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
   TRY(pf_setup(h, nl));
+  CK(cudaMemcpyAsync(h->pfU, Ud, (size_t)h->D_total * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   const double ref = ref_norm(h);
   std::vector<double> hist;
   int status = ST_ERR_NOT_CONVERGED;
   double rel = 0, nrm = 0;
   int it = 0;
   for (;;) {
-    TRY(fine_residual(h, Ud, nullptr, 1, false, 0));
+    TRY(fine_residual(h, h->pfU, nullptr, 1, false, 0));
     TRY(read_scalars(h, 1));
     nrm = std::sqrt(h->hscal[0]);
     rel = nrm / ref;
@@ -1894,9 +1909,10 @@ int st_pfasst(st_handle* h, double* U, st_solve_info* info) {
     if (!std::isfinite(rel) || rel > 1e8) { status = ST_ERR_DIVERGED; break; }
     if (rel <= h->o.tol) { status = ST_OK; break; }
     if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
-    TRY(pf_iteration(h, Ud));
+    TRY(run_graph(h, 4, enq_pf_iteration));
     ++it;
   }
+  CK(cudaMemcpyAsync(Ud, h->pfU, (size_t)h->D_total * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   TRY(stage_out(h, U, Ud));
   CK(cudaStreamSynchronize(h->stream));
   fill_info(info, it, status, rel, nrm, ref, now_s() - t0, hist);
