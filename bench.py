@@ -465,6 +465,8 @@ def run_reference(args):
 PAPER_PAIRS = ((1, 1024), (2, 256), (3, 32), (4, 16), (5, 8))
 PAPER_ITERS = {"heat": (2, 4, 4, 5, 5), "monodomain": (16, 16, 16, 16, 58)}
 PAPER_SMMG_ITERS = {"heat": (None, 12, 17, 15, 18)}
+# its STMG_3^5 (space and slab bisection on every level, 5 levels), single core
+PAPER_STMG_ITERS = {"heat": (6, 18, 30, 30, 30)}
 # its PFASST_1^3 with one slab per core (Cores = N_t); "n.c." = not converged
 PAPER_PFASST_ITERS = {"heat": (7, 30, 35, 29, 22), "monodomain": (6, 8, "n.c.", "n.c.", "n.c.")}
 
@@ -488,12 +490,24 @@ def run_paper_tables(args):
         u0 = stgen.cosine_modes(n, X) if ex == "heat" else stgen.stimulus(n, X)
         for (M, Nt), paper_it in zip(PAPER_PAIRS, PAPER_ITERS[ex]):
             for cname, coarsening, levels in (("SMG7", stlib.COARSEN_SPACE, 7), ("SMMG7", stlib.COARSEN_SPACE_NODES, 7),
+                                              ("STMG7", stlib.COARSEN_SPACE_TIME, 7),
                                               ("auto", stlib.COARSEN_AUTO_MU, 32)):
                 if cname == "SMMG7" and M == 1:
                     continue  # the same hierarchy as SMG7
-                S = stlib.Solver((n,), stlib.NEUMANN, 1.0, Nt, M, u0, T=T, X=X, reaction=rx, rho=rho,
-                                 opts=stlib.make_opts(precision=stlib.FP64, tol=1e-9, max_iters=1000,
-                                                      coarsening=coarsening, max_levels=levels))
+                # STMG: the slabs are bisected down to one, as the paper's T_l^{l+1} of size N_t/2^l;
+                # every level is followed by a space bisection, so the slab solves get their whole
+                # inner multigrid (not three Jacobi sweeps) against the anisotropy of mu >> 1; seven
+                # levels (the paper's five leave a 65-point coarse grid, beyond the dense coarse solve)
+                try:
+                    S = stlib.Solver((n,), stlib.NEUMANN, 1.0, Nt, M, u0, T=T, X=X, reaction=rx, rho=rho,
+                                     opts=stlib.make_opts(precision=stlib.FP64, tol=1e-9, max_iters=1000,
+                                                          coarsening=coarsening, max_levels=levels,
+                                                          coarse_max_slabs=1 if cname == "STMG7" else 4,
+                                                          smooth_inner_levels=0 if cname == "STMG7" else 1))
+                except stlib.StError as err:
+                    print(json.dumps({"mode": "paper_tables", "example": ex, "M": M, "Nt": Nt, "coarsening": cname,
+                                      "error": str(err)}), flush=True)
+                    continue
                 U = S.zeros()
                 S.solve(U, raise_on_error=False)  # warm-up (graph capture)
                 U.zero_()
@@ -509,6 +523,8 @@ def run_paper_tables(args):
                         "paper_smg_iterations_1core": paper_it}
                 if cname == "SMMG7" and ex in PAPER_SMMG_ITERS:
                     line["paper_smmg_iterations_1core"] = PAPER_SMMG_ITERS[ex][PAPER_PAIRS.index((M, Nt))]
+                if cname == "STMG7" and ex in PAPER_STMG_ITERS:
+                    line["paper_stmg_iterations_1core"] = PAPER_STMG_ITERS[ex][PAPER_PAIRS.index((M, Nt))]
                 if ex == "heat":
                     x = stgen.coords1d(stlib.NEUMANN, n, X)
                     h = X / (n - 1)

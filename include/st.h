@@ -68,8 +68,11 @@ enum { ST_PREC_FP64 = 0, ST_PREC_FP32_REFINE = 1 };
 /* SPACE: space bisection only (the paper's SMG); AUTO_MU: space bisection while
  * mu_l = nu dt_l / h_l^2 >= mu_crit, slab bisection otherwise (STMG with the mu
  * rule); SPACE_NODES: space bisection with one collocation node fewer per
- * level until M = 1 (the paper's SMMG, Section 5.2). */
-enum { ST_COARSEN_SPACE = 0, ST_COARSEN_AUTO_MU = 1, ST_COARSEN_SPACE_NODES = 2 };
+ * level until M = 1 (the paper's SMMG, Section 5.2); SPACE_TIME: space and
+ * slab bisection on every level at once, M fixed (the paper's STMG, Section
+ * 5.2), continuing in the one direction left once the other reaches its
+ * coarse limit (coarse_max_points, coarse_max_slabs). */
+enum { ST_COARSEN_SPACE = 0, ST_COARSEN_AUTO_MU = 1, ST_COARSEN_SPACE_NODES = 2, ST_COARSEN_SPACE_TIME = 3 };
 /* SDC lower-triangular preconditioner: implicit Euler node to node, or the
  * LU trick (Q^T = L U, QI = U^T). */
 enum { ST_SDC_IE = 0, ST_SDC_LU = 1 };
@@ -191,7 +194,8 @@ typedef struct {
   int Nt;             /* slabs */
   double dt, h[3], mu;
   int next_kind;      /* 0 coarsest, 1 space bisection, 2 slab bisection,
-                         3 space bisection and one node fewer */
+                         3 space bisection and one node fewer, 4 space and
+                         slab bisection */
   double omega;       /* damping used on this level */
   int inner_levels;   /* spatial multigrid depth of the slab solves */
   int M;              /* collocation nodes per slab on this level */

@@ -219,6 +219,20 @@ def prolong_time(M: int, v: np.ndarray) -> np.ndarray:
     return np.einsum("km,nms->nks", Pt, v).reshape(2 * Nc, M, Ns)
 
 
+def restrict_space_time(bc: int, shape, M: int, v: np.ndarray) -> np.ndarray:
+    """Space and slab bisection on one level (the STMG hierarchy of Section
+    5.2): full weighting of every plane, then the slab restriction.  The two
+    act on different indices, so their order does not matter.
+    (Nt, M, Ns) -> (Nt/2, M, Ns_coarse)."""
+    return restrict_time(M, restrict_space(bc, shape, v))
+
+
+def prolong_space_time(bc: int, shape, M: int, v: np.ndarray) -> np.ndarray:
+    """(Nt/2, M, Ns_coarse) -> (Nt, M, Ns): P_t on the coarse grid, then
+    linear interpolation to the fine grid ``shape``."""
+    return prolong_space(bc, shape, prolong_time(M, v))
+
+
 def restrict_cbar_space(bc: int, shape, cb: np.ndarray) -> np.ndarray:
     return restrict_space(bc, shape, cb)
 

@@ -212,7 +212,7 @@ int validate(const st_problem* p, const st_solver_opts* o) {
   if (o) {
     if (o->precision != ST_PREC_FP64 && o->precision != ST_PREC_FP32_REFINE) return ST_ERR_INVALID_ARG;
     if (o->coarsening != ST_COARSEN_SPACE && o->coarsening != ST_COARSEN_AUTO_MU &&
-        o->coarsening != ST_COARSEN_SPACE_NODES)
+        o->coarsening != ST_COARSEN_SPACE_NODES && o->coarsening != ST_COARSEN_SPACE_TIME)
       return ST_ERR_INVALID_ARG;
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8) return ST_ERR_INVALID_ARG;
     if (o->inner_cycles < 1 || o->inner_smooth < 1 || o->inner_coarse_iters < 1) return ST_ERR_INVALID_ARG;
@@ -252,6 +252,10 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
       if (cs && cur.g.Ns > o.coarse_max_points) kind = 1;
     } else if (o.coarsening == ST_COARSEN_SPACE_NODES) {
       if (cs && cur.g.Ns > o.coarse_max_points) kind = cur.M > 1 ? 3 : 1;
+    } else if (o.coarsening == ST_COARSEN_SPACE_TIME) {
+      const bool ss = cs && cur.g.Ns > o.coarse_max_points;
+      const bool tt = ct && cur.Nt > o.coarse_max_slabs;
+      kind = (ss && tt) ? 4 : (ss ? 1 : (tt ? 2 : 0));
     } else {
       const bool small_s = cur.g.Ns <= o.coarse_max_points;
       const bool small_t = cur.Nt <= o.coarse_max_slabs;
@@ -265,7 +269,11 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
     nx.Nt = cur.Nt;
     nx.dt = cur.dt;
     nx.M = kind == 3 ? cur.M - 1 : cur.M;
-    if (kind == 1 || kind == 3) {
+    if (kind == 4) {
+      nx.g = coarsen(d, cur.g, p->X);
+      nx.Nt = cur.Nt / 2;
+      nx.dt = cur.dt * 2;
+    } else if (kind == 1 || kind == 3) {
       nx.g = coarsen(d, cur.g, p->X);
     } else {
       nx.g = cur.g;
@@ -740,6 +748,11 @@ int restrict_level(st_handle* h, int l, int adj, const void* fine, void* coarse,
     launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)Lv.tmp, st);
     CKL();
     launch_node_transfer<T>(Lc.g.Ns, Lc.Nt, M, Lc.M, adj ? Lv.PnT : Lv.Rn, (const T*)Lv.tmp, (T*)coarse, 0, st);
+  } else if (Lv.next == 4) {
+    // full weighting in space (every slab), then the slab restriction on the coarse grid
+    launch_restrict_space<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)fine, (T*)Lv.tmp, st);
+    CKL();
+    launch_restrict_time<T>(Lc.g, Lc.Nt, M, adj ? Lv.ns->RtT : Lv.ns->col.Rt, (const T*)Lv.tmp, (T*)coarse, st);
   } else {
     launch_restrict_time<T>(Lv.g, Lc.Nt, M, adj ? Lv.ns->RtT : Lv.ns->col.Rt, (const T*)fine, (T*)coarse, st);
   }
@@ -757,6 +770,12 @@ int prolong_level(st_handle* h, int l, int adj, const void* coarse, void* fine, 
   } else if (Lv.next == 3) {
     // node-set interpolation on the coarse grid, then linear interpolation
     launch_node_transfer<T>(Lc.g.Ns, Lc.Nt, Lc.M, M, adj ? Lv.RnT : Lv.Pn, (const T*)coarse, (T*)Lv.tmp, 0, st);
+    CKL();
+    launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)Lv.tmp, (T*)fine, st);
+  } else if (Lv.next == 4) {
+    // slab interpolation on the coarse grid, then linear interpolation in space
+    CK(cudaMemsetAsync(Lv.tmp, 0, (size_t)Lc.g.Ns * Lv.Nt * M * h->esz, st));
+    launch_prolong_time_add<T>(Lc.g, Lc.Nt, M, adj ? Lv.ns->PtT : Lv.ns->col.Pt, (const T*)coarse, (T*)Lv.tmp, st);
     CKL();
     launch_prolong_space_add<T>(h->D, Lv.g, Lc.g, (long long)Lv.Nt * M, (const T*)Lv.tmp, (T*)fine, st);
   } else {
@@ -836,10 +855,15 @@ int enqueue_linearize(st_handle* h, cudaStream_t st, cudaEvent_t* ev = nullptr) 
     if (ev) CK(cudaEventRecord(ev[l], st));
     if (rx && l + 1 < L) {
       Level& Lc = h->L[l + 1];
-      if (Lv.next == 1 || Lv.next == 3)
+      if (Lv.next == 1 || Lv.next == 3) {
         launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
-      else
+      } else if (Lv.next == 4) {
+        launch_restrict_space<T>(h->D, Lv.g, Lc.g, Lv.Nt, (const T*)Lv.cbar, (T*)Lv.tmp, st);
+        CKL();
+        launch_cbar_time<T>(Lc.g, Lc.Nt, (const T*)Lv.tmp, (T*)Lc.cbar, st);
+      } else {
         launch_cbar_time<T>(Lv.g, Lc.Nt, (const T*)Lv.cbar, (T*)Lc.cbar, st);
+      }
       CKL();
     }
   }
@@ -1490,6 +1514,7 @@ int st_plan(const st_problem* p, const st_solver_opts* oin, st_plan_info* out) {
     li.M = L.M;
     const size_t D = (size_t)L.g.Ns * L.Nt * L.M;
     bytes += 5 * round_up(D * esz) + (rx ? round_up((size_t)L.g.Ns * L.Nt * esz) : 0);
+    if (L.next == 3 || L.next == 4) bytes += round_up((size_t)pl[l + 1].g.Ns * L.Nt * L.M * esz);
     for (size_t k = 1; k < L.inner.size(); ++k) {
       const size_t Dk = (size_t)L.inner[k].Ns * L.Nt * L.M;
       bytes += 3 * round_up(Dk * esz) + (rx ? round_up((size_t)L.inner[k].Ns * L.Nt * esz) : 0);
@@ -1574,7 +1599,8 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
       // the error modes of its time polynomial that the coarse node set does
       // not represent are left to the smoother at every spatial frequency.
       bool space_below = false;
-      for (size_t q = l; q < pl.size(); ++q) space_below = space_below || pl[q].next == 1 || pl[q].next == 3;
+      for (size_t q = l; q < pl.size(); ++q)
+        space_below = space_below || pl[q].next == 1 || pl[q].next == 3 || pl[q].next == 4;
       const int full = (int)pl[l].inner.size();
       const int cap = h->o.smooth_inner_levels;
       Lv.smooth_depth = (cap > 0 && cap < full && space_below && pl[l].next != 3) ? cap : full;
@@ -1594,6 +1620,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
         }
       s |= alloc_into(h, &Lv.tmp, (size_t)pl[l + 1].g.Ns * Lv.Nt * Lv.M * h->esz);
     }
+    if (Lv.next == 4) s |= alloc_into(h, &Lv.tmp, (size_t)pl[l + 1].g.Ns * Lv.Nt * Lv.M * h->esz);
     s |= alloc_into(h, &Lv.e, D * h->esz);
     s |= alloc_into(h, &Lv.r, D * h->esz);
     if (rx) s |= alloc_into(h, &Lv.cbar, (size_t)Lv.g.Ns * Lv.Nt * h->esz);

@@ -21,7 +21,7 @@ ST_ERR_NOT_CONVERGED, ST_ERR_DIVERGED, ST_ERR_TIMEOUT, ST_ERR_UNSUPPORTED = 4, 5
 DIRICHLET, PERIODIC, NEUMANN = 0, 1, 2
 NONE, LOGISTIC, CUBIC = 0, 1, 2
 FP64, FP32_REFINE = 0, 1
-COARSEN_SPACE, COARSEN_AUTO_MU, COARSEN_SPACE_NODES = 0, 1, 2
+COARSEN_SPACE, COARSEN_AUTO_MU, COARSEN_SPACE_NODES, COARSEN_SPACE_TIME = 0, 1, 2, 3
 SDC_IE, SDC_LU = 0, 1
 MAX_M, MAX_LEVELS, MAX_HISTORY = 5, 32, 64
 

@@ -75,9 +75,14 @@ TILED_M5 = Case("periodic2d_m5_runs", (32, 64), P_, 0.02, 10, 5, reaction=C_, rh
 SMMG2D = Case("smmg2d", (32, 32), P_, 1e-2, 8, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=12884,
               extra=dict(coarsening=2))
 SMMG1D = Case("smmg1d_m5", (65,), N_, 1.0, 8, 5, u0_kind="cosine", extra=dict(coarsening=2))
+# space and slab bisection on every level at once (STMG)
+STMG2D = Case("stmg2d", (32, 32), P_, 1e-2, 8, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=12884,
+              extra=dict(coarsening=3))
+STMG1D = Case("stmg1d_heat", (65,), N_, 0.01, 16, 3, u0_kind="cosine", extra=dict(coarsening=3))
 
 RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5]
-SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D]
+SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, STMG2D,
+               STMG1D]
 
 
 def residual_scale(p: system.Problem, U: np.ndarray) -> float:

@@ -90,6 +90,19 @@ def test_plan_space_nodes_rule(stlib):
     assert [l.next_kind for l in lv] == [3, 3, 3, 3, 1, 1, 0]
 
 
+def test_plan_space_time_rule(stlib):
+    """SPACE_TIME (the paper's STMG): space and slab bisection on one level
+    while both are possible, then the direction that is left."""
+    p = stlib.make_problem((64, 64), stlib.PERIODIC, 1.0, 16, 3)
+    info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE_TIME))
+    kinds = [info.level[l].next_kind for l in range(info.levels)]
+    sizes = [(info.level[l].n[0], info.level[l].Nt) for l in range(info.levels)]
+    assert kinds == [4, 4, 1, 1, 0], kinds
+    assert sizes == [(64, 16), (32, 8), (16, 4), (8, 4), (4, 4)], sizes
+    assert all(info.level[l].M == 3 for l in range(info.levels))
+    assert info.level[1].dt == 2 * info.level[0].dt
+
+
 def test_plan_dirichlet_and_neumann_sizes(stlib):
     p = stlib.make_problem((63,), stlib.DIRICHLET, 1.0, 16, 2)
     info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE))

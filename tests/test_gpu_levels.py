@@ -8,7 +8,8 @@ import pytest
 import stgen
 from oracle import multilevel as ml
 from oracle import space, system
-from tests.gpu_cases import (CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, RAGGED, SMMG1D, SMMG2D, TILED_M5,
+from tests.gpu_cases import (CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, RAGGED, SMMG1D, SMMG2D, STMG1D, STMG2D,
+                             TILED_M5,
                              Case)
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +19,8 @@ P_ = space.PERIODIC
 # a case whose hierarchy mixes space and slab bisection (AUTO_MU) and one
 # with space bisection only (SPACE)
 MIXED = Case("mixed2d", (32, 32), P_, 2e-3, 16, 3, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise", seed=5)
-LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, RAGGED, TILED_M5]
+LEVEL_CASES = [HEAT1D, LOG2D, MIXED, CUB3D, DIR2D_M5, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, RAGGED, TILED_M5,
+               STMG2D, STMG1D]
 
 
 def _oracle_level(S, case, l, cbar, U=None):
@@ -63,6 +65,8 @@ def test_cbar_hierarchy(case, prec):
             lev = _oracle_level(S, case, l, cb)
             if li["next_kind"] in (1, 3):
                 cb = ml.restrict_space(case.bc, lev.shape, cb)
+            elif li["next_kind"] == 4:
+                cb = ml.restrict_cbar_time(ml.restrict_space(case.bc, lev.shape, cb))
             else:
                 cb = ml.restrict_cbar_time(cb)
     S.close()
@@ -111,6 +115,12 @@ def test_level_residual_and_transfers(case, prec, ej):
                 elif kind == 3:
                     X = col.node_prolongation(tf, tc).T if tr else col.node_restriction(tf, tc)
                     ref = np.einsum("cf,nfs->ncs", X, ml.restrict_space(case.bc, lev.shape, rr))
+                elif kind == 4 and tr:
+                    Pt = col.time_prolongation(tf)
+                    rs = ml.restrict_space(case.bc, lev.shape, rr)
+                    ref = np.einsum("km,nks->nms", Pt, rs.reshape(lev.Nt // 2, 2 * M, -1))
+                elif kind == 4:
+                    ref = ml.restrict_space_time(case.bc, lev.shape, M, rr)
                 elif tr:
                     Pt = col.time_prolongation(tf)
                     ref = np.einsum("km,nks->nms", Pt, r_.reshape(lev.Nt // 2, 2 * M, -1))
@@ -128,6 +138,11 @@ def test_level_residual_and_transfers(case, prec, ej):
                 elif kind == 3:
                     X = col.node_restriction(tf, tc).T if tr else col.node_prolongation(tf, tc)
                     add = ml.prolong_space(case.bc, lev.shape, np.einsum("fc,ncs->nfs", X, cv_))
+                elif kind == 4 and tr:
+                    Rt = col.time_restriction(tf)
+                    add = ml.prolong_space(case.bc, lev.shape, np.einsum("mk,nms->nks", Rt, cv_).reshape(lev.Nt, M, -1))
+                elif kind == 4:
+                    add = ml.prolong_space_time(case.bc, lev.shape, M, cv_)
                 elif tr:
                     Rt = col.time_restriction(tf)
                     add = np.einsum("mk,nms->nks", Rt, cv_).reshape(lev.Nt, M, -1)

@@ -216,6 +216,29 @@ def test_time_transfer_roundtrip():
     assert back.shape == v.shape
 
 
+def test_space_time_transfers_commute_and_keep_constants():
+    """The STMG transfers are tensor products of the space and the slab
+    transfers: either order gives the same values; a field constant in space
+    restricts as its slab restriction alone (full weighting keeps spatial
+    constants); the prolongation keeps constants (linear interpolation,
+    nodal polynomial evaluation)."""
+    shape, M = (8, 8), 3
+    v = stgen.random_field((4, M, 64), 31)
+    a = ml.restrict_space_time(P, shape, M, v)
+    b = ml.restrict_space(P, shape, ml.restrict_time(M, v))
+    assert a.shape == (2, M, 16)
+    assert np.abs(a - b).max() < 1e-15
+    t = stgen.random_field((4, M, 1), 33)
+    flat = np.broadcast_to(t, (4, M, 64))
+    assert np.abs(ml.restrict_space_time(P, shape, M, flat) - ml.restrict_time(M, t)).max() < 1e-14
+    assert np.abs(ml.prolong_space_time(P, shape, M, np.full((2, M, 16), -1.3)) + 1.3).max() < 1e-14
+    w = stgen.random_field((2, M, 16), 32)
+    c = ml.prolong_space_time(P, shape, M, w)
+    d = ml.prolong_time(M, ml.prolong_space(P, shape, w))
+    assert c.shape == (4, M, 64)
+    assert np.abs(c - d).max() < 1e-15
+
+
 def test_exact_block_jacobi_with_omega1_is_nilpotent():
     """Undamped block Jacobi in time with exact slab solves solves slab k
     exactly after k sweeps (the system is block lower bidiagonal)."""
