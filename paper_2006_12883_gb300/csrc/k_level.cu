@@ -7,6 +7,8 @@
 // Indexing: one thread per (slab or slab chunk, point), flattened into a
 // 32-bit index (the host guarantees Ns * slabs < 2^31); divisions by the grid
 // sizes use precomputed multiply-shift constants.
+#include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "st_kernels.cuh"
@@ -175,34 +177,31 @@ __global__ void __launch_bounds__(256) k_backtransform(BackParams<T> p) {
 //   out_r = zr - sr L'zr + si L'zi,   out_i = zi - sr L'zi - si L'zr.
 // ---------------------------------------------------------------------------
 
-// One Jacobi sweep at point s of slab n: zout = z + omega D^{-1} (y - A z);
-// with fuse_bt the result is not stored but applied as
-// e = (e_zero ? 0 : e) + omega_bt B zout.
+// The Jacobi update at point s of one slab's shifted systems: zn = z + omega
+// D^{-1} (y - A z), with zs / ys the slab's planes (plane pl at + pl * Ns)
+// and cb the node-averaged reaction coefficient at s.
 template <int D, typename T>
-__device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int n, const Nbr& nb) {
-  const long long Ns = p.g.Ns;
-  const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
+__device__ __forceinline__ void jacobi_core(const InnerParams<T>& p, const T* zs, const T* ys, long long Ns, int s,
+                                            const Nbr& nb, T cb, T zn[MAXM]) {
   const T dprime = p.sc.k2 + cb;  // diagonal of L'
-  const long long base = (long long)n * p.P * Ns + s;
-  T zn[MAXM];
 #pragma unroll
   for (int pl = 0; pl < MAXM; ++pl) {
     const int kd = p.sh.kind[pl];
     if (kd == SH_REAL || kd == SH_RE) {
       const T sr = p.sh.sr[pl], si = p.sh.si[pl];
-      const T* zpr = p.z + (long long)(n * p.P + pl) * Ns;
+      const T* zpr = zs + (long long)pl * Ns;
       const T zr = zpr[s];
       const T Lr = lap_nb<D, T, T>(zpr, s, nb, zr, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zr);
-      const long long o = base + (long long)pl * Ns;
+      const long long o = (long long)pl * Ns + s;
       if (kd == SH_REAL) {
         const T dg = (T)1 - sr * dprime;
-        zn[pl] = zr + jdiv(p.omega * (p.y[o] - (zr - sr * Lr)), dg);
+        zn[pl] = zr + jdiv(p.omega * (ys[o] - (zr - sr * Lr)), dg);
       } else if (pl + 1 < MAXM) {
         const T* zpi = zpr + Ns;
         const T zi = zpi[s];
         const T Li = lap_nb<D, T, T>(zpi, s, nb, zi, p.sc.cx, p.sc.cy, p.sc.cz, p.sc.k2, cb * zi);
-        const T rr = p.y[o] - (zr - sr * Lr + si * Li);
-        const T ri = p.y[o + Ns] - (zi - sr * Li - si * Lr);
+        const T rr = ys[o] - (zr - sr * Lr + si * Li);
+        const T ri = ys[o + Ns] - (zi - sr * Li - si * Lr);
         const T dr = (T)1 - sr * dprime, di = -si * dprime;
         const T inv = jdiv(p.omega, dr * dr + di * di);
         zn[pl] = zr + (rr * dr + ri * di) * inv;
@@ -210,6 +209,18 @@ __device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int
       }
     }
   }
+}
+
+// One Jacobi sweep at point s of slab n: zout = z + omega D^{-1} (y - A z);
+// with fuse_bt the result is not stored but applied as
+// e = (e_zero ? 0 : e) + omega_bt B zout.
+template <int D, typename T>
+__device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int n, const Nbr& nb) {
+  const long long Ns = p.g.Ns;
+  const T cb = p.cbar ? p.cbar[(long long)n * Ns + s] : (T)0;
+  const long long base = (long long)n * p.P * Ns + s;
+  T zn[MAXM];
+  jacobi_core<D, T>(p, p.z + (long long)n * p.P * Ns, p.y + (long long)n * p.P * Ns, Ns, s, nb, cb, zn);
   if (!p.fuse_bt) {
 #pragma unroll
     for (int q = 0; q < MAXM; ++q)
@@ -225,6 +236,131 @@ __device__ __forceinline__ void jacobi_point(const InnerParams<T>& p, int s, int
         const long long o = base + (long long)a * Ns;
         p.e[o] = (p.e_zero ? (T)0 : p.e[o]) + p.omega_bt * acc;
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A whole smoothing step of a small level in one launch, one block per slab
+// (forward operator): the level residual r - A e + C e with the slab coupling
+// (e = 0 when lp.e is null), its Q-eigenbasis transform y, the zero-start
+// Jacobi iterate of the shifted systems, `sweeps - 1` more sweeps and the
+// back-transform with the damped block-Jacobi update, e_out = e + omega_bt B z
+// -- the work of the launches k_lin_residual, k_inner_jacobi make, on the
+// slab's planes held in shared memory.  e_out is another buffer than lp.e:
+// a block reads the previous slab's last node of lp.e while that slab's block
+// may already be writing its update.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(1024) k_slab_smooth(LinParams<T> lp, InnerParams<T> ip, int sweeps, T* eout) {
+  grid_dep_wait();
+  extern __shared__ __align__(16) unsigned char sraw[];
+  const int n = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int M = lp.M;
+  const long long Ns = lp.g.Ns;
+  T* E = reinterpret_cast<T*>(sraw);  // [M][Ns]
+  T* Y = E + (long long)M * Ns;
+  T* Z = Y + (long long)M * Ns;
+  T* Z2 = Z + (long long)M * Ns;
+  T* CB = Z2 + (long long)M * Ns;    // [Ns]
+  const bool hase = lp.e != nullptr;
+  const long long slab = (long long)n * M * Ns;
+  for (int s = tid; s < Ns; s += nth) {
+    CB[s] = lp.cbar ? lp.cbar[(long long)n * Ns + s] : (T)0;
+    for (int b = 0; b < M; ++b) E[(long long)b * Ns + s] = hase ? lp.e[slab + (long long)b * Ns + s] : (T)0;
+  }
+  __syncthreads();
+  for (int s = tid; s < Ns; s += nth) {
+    int i, j, k;
+    point_ijk(s, lp.g, i, j, k);
+    const Nbr nb = make_nbr<D>(i, j, k, lp.g);
+    const T cb = CB[s];
+    T res[MAXM];
+    if (hase) {
+      const T carry = n > 0 ? lp.e[((long long)(n - 1) * M + (M - 1)) * Ns + s] : (T)0;
+      T Fe[MAXM];
+#pragma unroll
+      for (int b = 0; b < MAXM; ++b)
+        if (b < M) {
+          const T* pl = E + (long long)b * Ns;
+          const T eb = pl[s];
+          Fe[b] = lap_nb<D, T, T>(pl, s, nb, eb, lp.sc.cx, lp.sc.cy, lp.sc.cz, lp.sc.k2, cb * eb);
+        }
+#pragma unroll
+      for (int a = 0; a < MAXM; ++a)
+        if (a < M) {
+          T acc = lp.r[slab + (long long)a * Ns + s] - E[(long long)a * Ns + s];
+#pragma unroll
+          for (int b = 0; b < MAXM; ++b)
+            if (b < M) acc = fma(lp.W[a][b], Fe[b], acc);
+          res[a] = acc + carry;
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < MAXM; ++a)
+        if (a < M) res[a] = lp.r[slab + (long long)a * Ns + s];
+    }
+    T y[MAXM];
+#pragma unroll
+    for (int a = 0; a < MAXM; ++a)
+      if (a < M) {
+        T acc = (T)0;
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b)
+          if (b < M) acc = fma(lp.F[a][b], res[b], acc);
+        y[a] = acc;
+        Y[(long long)a * Ns + s] = acc;
+      }
+    const T dprime = lp.sc.k2 + cb;
+#pragma unroll
+    for (int pl = 0; pl < MAXM; ++pl) {
+      const int kd = lp.sh.kind[pl];
+      if (kd == SH_REAL || kd == SH_RE) {
+        T zr, zi;
+        const T yi = (pl + 1 < MAXM && kd == SH_RE) ? y[pl + 1 < MAXM ? pl + 1 : pl] : (T)0;
+        zero_jacobi<T>(y[pl], yi, kd == SH_RE, lp.sh.sr[pl], lp.sh.si[pl], dprime, lp.omega_j, zr, zi);
+        Z[(long long)pl * Ns + s] = zr;
+        if (kd == SH_RE) Z[(long long)(pl + 1) * Ns + s] = zi;
+      }
+    }
+  }
+  __syncthreads();
+  for (int it = 1; it <= sweeps; ++it) {
+    const bool last = it == sweeps;
+    for (int s = tid; s < Ns; s += nth) {
+      T zn[MAXM];
+      if (it == 1 && sweeps == 1) {
+        // the zero-start iterate is the slab solve
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q) zn[q] = q < M ? Z[(long long)q * Ns + s] : (T)0;
+      } else if (it == 1) {
+        continue;  // (the zero-start iterate is in Z)
+      } else {
+        int i, j, k;
+        point_ijk(s, lp.g, i, j, k);
+        jacobi_core<D, T>(ip, Z, Y, Ns, s, make_nbr<D>(i, j, k, lp.g), CB[s], zn);
+      }
+      if (!last) {
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q)
+          if (q < M) Z2[(long long)q * Ns + s] = zn[q];
+      } else {
+#pragma unroll
+        for (int a = 0; a < MAXM; ++a)
+          if (a < M) {
+            T acc = (T)0;
+#pragma unroll
+            for (int b = 0; b < MAXM; ++b)
+              if (b < M) acc = fma(ip.B[a][b], zn[b], acc);
+            eout[slab + (long long)a * Ns + s] = E[(long long)a * Ns + s] + ip.omega_bt * acc;
+          }
+      }
+    }
+    __syncthreads();
+    if (it > 1 && !last) {
+      T* t = Z;
+      Z = Z2;
+      Z2 = t;
     }
   }
 }
@@ -554,6 +690,43 @@ void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t 
   else DISPATCH_D(D, (st_launch(k_inner_jacobi<DD, T>, nb, 256, 0, st, p)));
 }
 
+// shared memory one slab-smoothing block may take (the opt-in is set once)
+constexpr size_t kSlabSmoothSmem = 220 * 1024;
+static int g_slab_smooth_ready = 0;
+
+void slab_smooth_prepare() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    bool ok = true;
+    auto set = [&](auto kern) {
+      ok = ok && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmoothSmem) ==
+                     cudaSuccess;
+    };
+    set(k_slab_smooth<1, float>); set(k_slab_smooth<2, float>); set(k_slab_smooth<3, float>);
+    set(k_slab_smooth<1, double>); set(k_slab_smooth<2, double>); set(k_slab_smooth<3, double>);
+    g_slab_smooth_ready = ok ? 1 : 0;
+    (void)cudaGetLastError();
+  });
+}
+
+template <typename T>
+size_t slab_smooth_smem(int M, long long Ns) {
+  return (size_t)(4 * M + 1) * (size_t)Ns * sizeof(T);
+}
+
+template <typename T>
+bool slab_smooth_fits(int M, long long Ns) {
+  return g_slab_smooth_ready && slab_smooth_smem<T>(M, Ns) <= kSlabSmoothSmem;
+}
+
+template <typename T>
+void launch_slab_smooth(int D, const LinParams<T>& lp, const InnerParams<T>& ip, int sweeps, T* eout,
+                        cudaStream_t st) {
+  const size_t smem = slab_smooth_smem<T>(lp.M, lp.g.Ns);
+  const int threads = (int)std::min<long long>(1024, (lp.g.Ns + 31) / 32 * 32);
+  DISPATCH_D(D, (st_launch(k_slab_smooth<DD, T>, (unsigned)lp.Nt, threads, smem, st, lp, ip, sweeps, eout)));
+}
+
 template <typename T>
 void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value)
@@ -680,7 +853,9 @@ void launch_node_transfer(long long Ns, int Nt, int Mi, int Mo, const double X[M
                                            const T*, T*, cudaStream_t);                            \
   template void launch_cbar_time<T>(const GridP&, int, const T*, T*, cudaStream_t);                \
   template void launch_node_transfer<T>(long long, int, int, int, const double[MAXM][MAXM], const T*, T*, \
-                                        int, cudaStream_t);
+                                        int, cudaStream_t);                                        \
+  template bool slab_smooth_fits<T>(int, long long);                                               \
+  template void launch_slab_smooth<T>(int, const LinParams<T>&, const InnerParams<T>&, int, T*, cudaStream_t);
 
 INST(float)
 INST(double)

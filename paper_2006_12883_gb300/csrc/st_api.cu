@@ -84,6 +84,11 @@ struct Level {
   void* r = nullptr;
   void* cbar = nullptr;
   std::vector<InnerLev> in;
+  // a small level whose forward smoothing steps run as one launch each (one
+  // block per slab): the post-smoothing step writes its e into e2, which the
+  // finer level's prolongation then reads
+  bool fused = false;
+  void* e2 = nullptr;
 };
 
 struct Alloc {
@@ -301,6 +306,32 @@ int plan_levels(const st_problem* p, const st_solver_opts& o, std::vector<PlanLe
   }
   if (out.back().g.Ns * out.back().M > kCoarseKMax) return ST_ERR_UNSUPPORTED;
   return ST_OK;
+}
+
+// Depth of the inner multigrid the slab solves of level l use (the smoother
+// policy): capped to o.smooth_inner_levels while a coarser level of the
+// hierarchy is coarser in space and the next level keeps the node count.
+int smooth_depth_of(const std::vector<PlanLevel>& pl, size_t l, const st_solver_opts& o) {
+  bool space_below = false;
+  for (size_t q = l; q < pl.size(); ++q)
+    space_below = space_below || pl[q].next == 1 || pl[q].next == 3 || pl[q].next == 4;
+  const int full = (int)pl[l].inner.size();
+  const int cap = o.smooth_inner_levels;
+  return (cap > 0 && cap < full && space_below && pl[l].next != 3) ? cap : full;
+}
+
+// Whether level l's forward smoothing steps run as one launch each (one
+// block per slab, planes in shared memory; see k_slab_smooth): a level
+// between the finest and the coarsest whose slab solves are plain Jacobi
+// sweeps from the zero-start iterate, V(1,1), and whose grid is small enough
+// (kFusedSmoothMaxNs) that the separate launches are latency bound; on larger
+// grids N_t blocks are too few to occupy the GPU.
+const long long kFusedSmoothMaxNs = 1024;
+bool fused_smoothing(const std::vector<PlanLevel>& pl, size_t l, const st_solver_opts& o, size_t esz) {
+  const bool multi = !(pl[l].inner.size() == 1 && pl[l].inner[0].Ns <= kInnerCoarseLimit);
+  return l >= 1 && l + 1 < pl.size() && smooth_depth_of(pl, l, o) == 1 && multi && o.nu1 == 1 && o.nu2 == 1 &&
+         o.inner_cycles == 1 && pl[l].g.Ns <= kFusedSmoothMaxNs &&
+         (size_t)(4 * pl[l].M + 1) * (size_t)pl[l].g.Ns * esz <= 220 * 1024;
 }
 
 size_t round_up(size_t b) { return (b + 255) / 256 * 256; }
@@ -711,6 +742,19 @@ template <typename T>
 int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   Level& Lv = h->L[l];
   const int M = Lv.M;
+  if (!adj && Lv.fused) {
+    LinParams<T> lp = lin_params<T>(h, Lv, 0);
+    lp.e = e_zero ? nullptr : (const T*)Lv.e;
+    lp.r = (const T*)Lv.r;
+    InnerParams<T> ip = inner_params<T>(h, Lv, 0, M, level_shifts<T>(*Lv.ns, Lv.dt),
+                                        h->p.reaction != ST_REACTION_NONE);
+    ip.omega_bt = (T)Lv.omega;
+    for (int a = 0; a < MAXM; ++a)
+      for (int b = 0; b < MAXM; ++b) ip.B[a][b] = (T)Lv.ns->Bf[a][b];
+    launch_slab_smooth<T>(h->D, lp, ip, Lv.smooth_sweeps, (T*)(e_zero ? Lv.e : Lv.e2), st);
+    CKL();
+    return ST_OK;
+  }
   const bool multi = !(Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit);
   {
     // residual + Q-eigenbasis transform (+ zero-start Jacobi of the slab systems)
@@ -828,7 +872,8 @@ int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   TRY(level_residual<T>(h, l, adj, Lv.e, Lv.r, Lv.in[0].y, 0, st));
   TRY(restrict_level<T>(h, l, adj, Lv.in[0].y, h->L[l + 1].r, st));
   TRY(vcycle_level<T>(h, l + 1, adj, st));
-  TRY(prolong_level<T>(h, l, adj, h->L[l + 1].e, Lv.e, st));
+  const Level& Lc = h->L[l + 1];
+  TRY(prolong_level<T>(h, l, adj, (!adj && Lc.fused) ? Lc.e2 : Lc.e, Lv.e, st));
   for (int i = 0; i < nu2; ++i) TRY(smooth<T>(h, l, adj, false, st));
   return ST_OK;
 }
@@ -1515,6 +1560,7 @@ int st_plan(const st_problem* p, const st_solver_opts* oin, st_plan_info* out) {
     const size_t D = (size_t)L.g.Ns * L.Nt * L.M;
     bytes += 5 * round_up(D * esz) + (rx ? round_up((size_t)L.g.Ns * L.Nt * esz) : 0);
     if (L.next == 3 || L.next == 4) bytes += round_up((size_t)pl[l + 1].g.Ns * L.Nt * L.M * esz);
+    if (fused_smoothing(pl, l, o, esz)) bytes += round_up(D * esz);
     for (size_t k = 1; k < L.inner.size(); ++k) {
       const size_t Dk = (size_t)L.inner[k].Ns * L.Nt * L.M;
       bytes += 3 * round_up(Dk * esz) + (rx ? round_up((size_t)L.inner[k].Ns * L.Nt * esz) : 0);
@@ -1578,6 +1624,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   const int M = pin->M;
   const bool rx = pin->reaction != ST_REACTION_NONE;
   // levels and buffers
+  slab_smooth_prepare();
   h->L.resize(pl.size());
   for (size_t l = 0; l < pl.size(); ++l) {
     Level& Lv = h->L[l];
@@ -1598,13 +1645,11 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
       // multigrid.  So does a level whose next coarser one has fewer nodes:
       // the error modes of its time polynomial that the coarse node set does
       // not represent are left to the smoother at every spatial frequency.
-      bool space_below = false;
-      for (size_t q = l; q < pl.size(); ++q)
-        space_below = space_below || pl[q].next == 1 || pl[q].next == 3 || pl[q].next == 4;
       const int full = (int)pl[l].inner.size();
-      const int cap = h->o.smooth_inner_levels;
-      Lv.smooth_depth = (cap > 0 && cap < full && space_below && pl[l].next != 3) ? cap : full;
+      Lv.smooth_depth = smooth_depth_of(pl, l, h->o);
       Lv.smooth_sweeps = Lv.smooth_depth < full ? h->o.smooth_sweeps : Lv.bottom_sweeps;
+      Lv.fused = fused_smoothing(pl, l, h->o, h->esz) &&
+                 (h->fp64 ? slab_smooth_fits<double>(Lv.M, Lv.g.Ns) : slab_smooth_fits<float>(Lv.M, Lv.g.Ns));
     }
     const size_t D = (size_t)Lv.g.Ns * Lv.Nt * Lv.M;
     int s = ST_OK;
@@ -1622,6 +1667,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     }
     if (Lv.next == 4) s |= alloc_into(h, &Lv.tmp, (size_t)pl[l + 1].g.Ns * Lv.Nt * Lv.M * h->esz);
     s |= alloc_into(h, &Lv.e, D * h->esz);
+    if (Lv.fused) s |= alloc_into(h, &Lv.e2, D * h->esz);
     s |= alloc_into(h, &Lv.r, D * h->esz);
     if (rx) s |= alloc_into(h, &Lv.cbar, (size_t)Lv.g.Ns * Lv.Nt * h->esz);
     Lv.in.resize(pl[l].inner.size());

@@ -114,6 +114,13 @@ template <typename T>
 void launch_backtransform(const GridP& g, int Nt, int M, const T B[MAXM][MAXM], T omega, int e_zero,
                           const T* z, T* e, cudaStream_t st);
 template <typename T> void launch_inner_jacobi(int D, int zero, const InnerParams<T>& p, cudaStream_t st);
+// a whole forward smoothing step of a small level, one block per slab, planes
+// in shared memory (k_level.cu); eout must not alias lp.e
+void slab_smooth_prepare();
+template <typename T> bool slab_smooth_fits(int M, long long Ns);
+template <typename T>
+void launch_slab_smooth(int D, const LinParams<T>& lp, const InnerParams<T>& ip, int sweeps, T* eout,
+                        cudaStream_t st);
 template <typename T> void launch_inner_restrict(int D, const InnerParams<T>& p, cudaStream_t st);
 template <typename T> void launch_shifted_residual(int D, const InnerParams<T>& p, cudaStream_t st);
 template <typename T> size_t inner_coarse_smem(const InnerParams<T>& p);
