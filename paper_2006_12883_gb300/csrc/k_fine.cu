@@ -286,11 +286,9 @@ static FFC split_const(double v) {
   return c;
 }
 
-static bool al16(const void* q) { return ((unsigned long long)(size_t)q & 15ull) == 0; }
-
 static bool ff4_ok(int D, const ResidParams& p) {
   return D >= 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 >= 4 && p.g.n0 % 4 == 0 &&
-         al16(p.U) && al16(p.u0) && al16(p.R) && al16(p.cbar) && al16(p.cnode);
+         aligned16(p.U) && aligned16(p.u0) && aligned16(p.R) && aligned16(p.cbar) && aligned16(p.cnode);
 }
 
 long long residual_ff_blocks(int D, const ResidParams& p) {

@@ -276,8 +276,6 @@ __global__ void __launch_bounds__(256, M == 3 ? 3 : 2) k_residual_tile(ResidPara
   }
 }
 
-bool aligned16(const void* q) { return ((unsigned long long)(size_t)q & 15ull) == 0; }
-
 bool tile_ok(int D, const ResidParams& p) {
   return D == 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 >= kRW && p.g.n0 % kRW == 0 &&
          p.g.n1 >= kRH && p.g.n1 % kRH == 0 && p.tau == nullptr && aligned16(p.U) && aligned16(p.u0) &&

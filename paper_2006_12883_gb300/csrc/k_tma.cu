@@ -498,8 +498,6 @@ bool encode(CUtensorMap* map, const float* base, int n0, long long rows) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
-
 }  // namespace
 
 bool jacobi_tma_ok(int D, const InnerParams<float>& p) {

@@ -46,6 +46,10 @@ struct GridP {
   FastDiv f0, f1, fNs;  // division by n0, n1 and Ns
 };
 
+// True when p sits on a 16-byte boundary (float4 / double2 and TMA access; a
+// null pointer counts as aligned).
+inline bool aligned16(const void* p) { return ((unsigned long long)(size_t)p & 15ull) == 0; }
+
 // Grid construction (host) ---------------------------------------------------
 
 inline double spacing(int bc, int n, double X) {
