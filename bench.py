@@ -155,8 +155,8 @@ class ClockSampler:
 # was taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
     # filled from the ncu capture summarised in profiles/hot_kernels_logistic2d_256_Nt256_M3.md
-    # (level-0 launch): 469.8 MB read + 175.7 MB written
-    "k_inner4<2, 3, 1>": {"file": "k_level4.cu", "sha256": "51c2248a10ebaaad439435e89c0f72cfe41a7dbdfb7a9f17d79d81cdf45f7279", "dram_bytes": 645487616},
+    # (level-0 launch, 128-thread blocks; profiles/k_inner4_logistic2d_256_Nt256_M3.md): 469.8 MB read + 175.1 MB written
+    "k_inner4<2, 3, 1>": {"file": "k_level4.cu", "sha256": "c47f933cc3a7a5c5dd9b15b80759de4c243b020ed900f1061b999a3399b44c79", "dram_bytes": 644838144},
 }
 
 
