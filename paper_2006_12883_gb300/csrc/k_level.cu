@@ -1,8 +1,9 @@
 // Cycle-precision kernels of the space-time V-cycle (templated on T = float
 // or double): the level operator residual with the Q-eigenbasis transform,
 // the spatial multigrid of the shifted slab systems (with the back-transform
-// and damped block-Jacobi update fused into its last sweep), and the space /
-// slab transfers (Eq. 4.1).
+// and damped block-Jacobi update fused into its last sweep), a whole
+// smoothing step of a small level in one launch (k_slab_smooth), and the
+// space / slab transfers (Eq. 4.1).
 //
 // Indexing: one thread per (slab or slab chunk, point), flattened into a
 // 32-bit index (the host guarantees Ns * slabs < 2^31); divisions by the grid

@@ -1,14 +1,19 @@
-// TMA-staged Jacobi sweep of the Q-diagonalised slab systems on 2D periodic
-// grids (x size a multiple of 64, y size a multiple of 16, M = 3 or 5, FP32),
-// used for the sweep that also updates e (the last of a slab solve):
-// the same arithmetic as k_inner4<2, M, 1> in k_level4.cu, with the operands
-// of a 64 x 16 tile (z, y, e of every plane and cbar) brought into shared
-// memory by cp.async.bulk.tensor copies and the one-point halo of z by plain
-// loads.  A persistent grid (two blocks per SM) walks the tiles with two
-// stages: the copies of the next tile are in flight while the current one is
-// computed.  Every wait on a stage's mbarrier is bounded; on expiry the block
-// records an error flag (read back with the norms), stops computing and
+// TMA-staged level kernels on 2D periodic grids (x size a multiple of 64, y
+// size a multiple of 16, M = 3 or 5, FP32):
+//  * k_jacobi_tma: the Jacobi sweep of the Q-diagonalised slab systems that
+//    also updates e (the last of a slab solve), the same arithmetic as
+//    k_inner4<2, M, 1> in k_level4.cu, with the operands of a 64 x 16 tile
+//    (z, y, e of every plane and cbar) brought into shared memory by
+//    cp.async.bulk.tensor copies and the one-point halo of z by plain loads;
+//  * k_linres_tma: the level residual with e (and the eigenbasis transform),
+//    e, r, cbar and the previous slab's last node plane staged the same way.
+// A persistent grid (two blocks per SM) walks the tiles with two stages: the
+// copies of the next tile are in flight while the current one is computed.
+// Every wait on a stage's mbarrier is bounded; on expiry the block counts the
+// event in a device counter (read back with the norms), stops computing and
 // returns after waiting, again bounded, for its copies in flight.
+// k_wait_expiry exercises that path on purpose (a wait nothing completes)
+// for the self-check st_wait_selftest.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
