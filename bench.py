@@ -566,7 +566,8 @@ def run_paper_tables(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    # about a second of timed steps, so the 200 ms clock sampler sees several samples
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="logistic2d_256", choices=sorted(WORKLOADS))
