@@ -103,6 +103,19 @@ def test_plan_space_time_rule(stlib):
     assert info.level[1].dt == 2 * info.level[0].dt
 
 
+def test_plan_space_time_respects_the_reaction_guard(stlib):
+    """With a fast reaction the slabs are not bisected (2 dt |rho| max|lambda(Q)|
+    above 1/2 would leave the coarse slab systems without meaning): SPACE_TIME
+    then coarsens in space only, and slab bisection resumes where dt allows."""
+    fast = stlib.make_problem((64, 64), stlib.PERIODIC, 1.0, 16, 3, T=1.0, reaction=stlib.LOGISTIC, rho=50.0)
+    info = stlib.st_plan(fast, stlib.make_opts(coarsening=stlib.COARSEN_SPACE_TIME))
+    kinds = [info.level[l].next_kind for l in range(info.levels)]
+    assert 2 not in kinds and 4 not in kinds and kinds[0] == 1, kinds
+    mild = stlib.make_problem((64, 64), stlib.PERIODIC, 1.0, 16, 3, T=1.0, reaction=stlib.LOGISTIC, rho=0.1)
+    info = stlib.st_plan(mild, stlib.make_opts(coarsening=stlib.COARSEN_SPACE_TIME))
+    assert info.level[0].next_kind == 4
+
+
 def test_plan_dirichlet_and_neumann_sizes(stlib):
     p = stlib.make_problem((63,), stlib.DIRICHLET, 1.0, 16, 2)
     info = stlib.st_plan(p, stlib.make_opts(coarsening=stlib.COARSEN_SPACE))
