@@ -1,20 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: space-time dof-updates per second per V-cycle on the 2D logistic
-reaction-diffusion workload (256^2 periodic grid, Nt = 256 slabs, M = 3
-right-Radau nodes, 50.3M space-time dofs), FP32 cycle inside FP64 defect
-correction, on one GB300 per rank.
+reaction-diffusion workload at full size (1024^2 periodic grid, Nt = 1024
+slabs, M = 5 right-Radau nodes: 5.37e9 space-time dofs, U alone 43 GB in
+FP64), FP32 cycle inside FP64 defect correction, on one GB300 per rank.  The
+same workload at M = 3 (3.22e9 dofs) is reported beside it under "extras".
 
-One step = one st_vcycle call through the C ABI: FP64 residual G(U) with its
-norm (one device->host read), relinearisation, one space-time V-cycle, and
-the update U += e.  Inputs (U: 403 MB, workspace ~1.9 GB) are larger than the
-129 MB L2, so no flush is needed between steps.
+One step = one st_vcycle call through the C ABI: FP64-accurate residual G(U)
+with its norm (one device->host read), relinearisation, one space-time
+V-cycle, and the update U += e.  Inputs are far larger than the 129 MB L2, so
+no flush is needed between steps.
 
 Ranks run independent replicas of the workload (each its own seeded problem,
 no collective on the data path: weak scaling); value = all ranks' dofs per
 step / the slowest rank's time per step.
 
---impl reference times the CPU oracle (slab-by-slab Newton, GMRES slab solves)
-on a bounded sample of the same workload on the host cores.
+--impl reference times the CPU oracle on the host cores, single-threaded:
+each step is one evaluation of the collocation residual (Eq. 2.3 with the
+slab coupling of Eq. 3.4) over the first K slabs of the same workload (one
+update of every dof those slabs hold), K chosen so that a step takes about a
+second.
 """
 from __future__ import annotations
 
@@ -35,7 +39,7 @@ METRIC = "space-time dof-updates/s per V-cycle"
 UNIT = "dof/s"
 NOISE = "uniform[0,1) noise smoothed by 10 neighbour-averaging passes"
 WORKLOADS = {
-    # the default: 2D logistic, 256^2 periodic, 256 slabs, 3 nodes (50.3M dofs)
+    # 2D logistic, 256^2 periodic, 256 slabs, 3 nodes (50.3M dofs)
     "logistic2d_256": dict(workload="logistic2d_256x256_Nt256_M3", grid=[256, 256], bc="periodic", Nt=256, M=3,
                            nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12884, u0=NOISE),
     "heat1d_63": dict(workload="heat1d_dirichlet63_Nt16_M2", grid=[63], bc="dirichlet", Nt=16, M=2, nu=1.0,
@@ -50,7 +54,8 @@ WORKLOADS = {
     "logistic2d_512": dict(workload="logistic2d_512x512_Nt512_M3", grid=[512, 512], bc="periodic", Nt=512, M=3,
                            nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12887, u0=NOISE),
 }
-WORKLOAD = WORKLOADS["logistic2d_256"]
+DEFAULT_CONFIG = "logistic2d_1024_m5"
+WORKLOAD = WORKLOADS[DEFAULT_CONFIG]
 
 
 def make_u0(w, rank=0):
@@ -68,10 +73,12 @@ def make_solver(stlib, w, u0, **opts):
     rx = {"none": stlib.NONE, "logistic": stlib.LOGISTIC, "cubic": stlib.CUBIC}[w["reaction"]]
     return stlib.Solver(tuple(w["grid"]), bc, w["nu"], w["Nt"], w["M"], u0, T=w["T"], reaction=rx,
                         rho=w["rho"], opts=stlib.make_opts(**opts))
-FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor) per the pool's hardware notes
+
+
+HBM_DATASHEET_GBS = 7900.0  # GB300 HBM3e, vendor figure (context beside the measured copy bandwidth)
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
-                 ("prolong_add", 7), ("slab_jacobi_plain", 8), ("vcycle_graph", 4))
+                 ("prolong_add", 7), ("slab_jacobi_plain", 8), ("update", 9), ("vcycle_graph", 4))
 
 
 def reduce_max(x, dist, device):
@@ -150,14 +157,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one fine-level launch, from an ncu capture of
-# `python bench.py --probe` (profiles/); valid only for the kernel source it
-# was taken on (sha256 of the file that holds the kernel).
-NCU_TRAFFIC = {
-    # filled from the ncu capture summarised in profiles/hot_kernels_logistic2d_256_Nt256_M3.md
-    # (level-0 launch, 128-thread blocks; profiles/k_inner4_logistic2d_256_Nt256_M3.md): 469.8 MB read + 175.1 MB written
-    "k_inner4<2, 3, 1>": {"file": "k_level4.cu", "sha256": "c47f933cc3a7a5c5dd9b15b80759de4c243b020ed900f1061b999a3399b44c79", "dram_bytes": 644838144},
-}
+# DRAM bytes (read + write) per space-time dof of one level-0 launch of the
+# roofline kernel, from one ncu capture of `python bench.py --probe` on a
+# smaller workload of the same kernel instance (its traffic grows in
+# proportion to the dofs: every array is streamed once); scaled to a full
+# launch by the dofs it processes.  Valid only for the kernel source it was
+# taken on (sha256 of the file that holds the kernel).
+NCU_TRAFFIC = {}
 
 
 def ncu_traffic(kernel, dofs):
@@ -168,7 +174,7 @@ def ncu_traffic(kernel, dofs):
     path = os.path.join(ROOT, "paper_2006_12883_gb300", "csrc", rec["file"])
     with open(path, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    return rec["dram_bytes"] if sha == rec["sha256"] else None
+    return rec["dram_bytes_per_dof"] * dofs if sha == rec["sha256"] else None
 
 
 def measured_peaks():
@@ -182,6 +188,9 @@ def measured_peaks():
 
 # ------------------------------------------------------------------ oracle
 
+# One oracle residual evaluation over the first K slabs, timed in a fresh
+# single-threaded process.  The iterate is u0 on every node plus seeded noise
+# of amplitude 0.1 (any iterate costs the same).
 ORACLE_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
@@ -189,51 +198,251 @@ import numpy as np
 import stgen
 from oracle import space, system
 w = json.loads({wl!r})
-nslabs = int({nslabs})
+K = int({nslabs})
 shape = tuple(w["grid"])
 bc = dict(periodic=space.PERIODIC, dirichlet=space.DIRICHLET)[w["bc"]]
 rx = dict(none=space.NONE, logistic=space.LOGISTIC, cubic=space.CUBIC)[w["reaction"]]
-p = system.Problem(shape=shape, bc=bc, nu=w["nu"], Nt=w["Nt"], M=w["M"], T=w["T"], reaction=rx, rho=w["rho"])
+dt = w["T"] / w["Nt"]
+p = system.Problem(shape=shape, bc=bc, nu=w["nu"], Nt=K, M=w["M"], T=K * dt, reaction=rx, rho=w["rho"])
 if w["bc"] == "dirichlet":
     u0 = stgen.sine_modes(shape[0])
 elif w["reaction"] == "cubic":
     u0 = stgen.gaussian_bumps(shape, w["seed"]).ravel()
 else:
     u0 = stgen.smoothed_noise(shape, w["seed"]).ravel()
+U = u0[None, None, :] + stgen.random_field((K, p.M, p.Ns), 4242, 0.1)
+p.L
 out = []
 for rep in range(int({reps})):
     t = time.perf_counter()
-    system.solve_sequential(p, u0, nslabs=nslabs)
+    system.residual(p, U, u0)
     out.append(time.perf_counter() - t)
 print(json.dumps(out))
 """
 
 
+def oracle_slabs(w, seconds=1.0, rate=2.5e7):
+    """K: how many of the workload's slabs one oracle residual step covers, so
+    that a step takes about `seconds` at about `rate` dof/s on one core."""
+    per_slab = w["M"] * int(math.prod(w["grid"]))
+    return int(max(1, min(w["Nt"], round(seconds * rate / per_slab))))
+
+
+def host_info():
+    """The host's core count and CPU model (the oracle's machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+    return {"host_nproc": os.cpu_count(), "host_cpu": model or platform.processor() or platform.machine(),
+            "host_arch": platform.machine()}
+
+
 def time_oracle(w, nslabs=1, reps=1):
-    """Seconds per oracle solve of the first `nslabs` slabs, in a fresh
-    single-threaded process (BLAS / OpenMP pinned to one thread)."""
+    """Seconds per oracle residual evaluation over the first `nslabs` slabs,
+    in a fresh process pinned to one core (BLAS / OpenMP on one thread)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     code = ORACLE_SNIPPET.format(root=ROOT, wl=json.dumps(w), nslabs=nslabs, reps=reps)
-    r = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
-                       text=True, timeout=1800)
+    cmd = [sys.executable, "-c", code]
+    try:
+        cpus = sorted(os.sched_getaffinity(0))
+        if cpus:
+            cmd = ["taskset", "-c", str(cpus[-1])] + cmd
+    except Exception:
+        pass
+    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1500)
+    if r.returncode != 0 and cmd[0] == "taskset":
+        r = subprocess.run(cmd[3:], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           timeout=1500)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_baseline(w, nslabs=1, reps=1):
-    ts = time_oracle(w, nslabs, reps)
-    Ns = int(math.prod(w["grid"]))
-    dofs = nslabs * w["M"] * Ns
+def oracle_sample(w, K, n):
+    return (f"oracle residual G(U) (Eq. 2.3 + slab coupling, numpy FP64) over the first {K} of {w['Nt']} slabs "
+            f"({K * w['M'] * int(math.prod(w['grid']))} dofs), {n} evaluation(s); one evaluation = one update "
+            f"of each of those dofs")
+
+
+def oracle_baseline(w, reps=12):
+    """cpu_baseline: the oracle's residual-evaluation throughput (dof/s), best of
+    `reps` evaluations over the first K slabs (about 10-15 s of one core)."""
+    K = oracle_slabs(w)
+    ts = time_oracle(w, K, reps)
+    dofs = K * w["M"] * int(math.prod(w["grid"]))
     t = min(ts)
-    return {"value": dofs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"slab-by-slab Newton (GMRES / sparse-LU slab solves) of the first {nslabs} of {w['Nt']} "
-                      f"slabs ({dofs} dofs, {t:.2f} s, best of {len(ts)})"}
+    return dict({"value": dofs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": oracle_sample(w, K, len(ts)) + f", best {t:.3f} s"}, **host_info())
 
 
 # ------------------------------------------------------------------ ours
+
+def host_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def pinned_host(shape):
+    """A pinned host tensor of doubles (pageable if pinning fails), or None
+    when it would take more than half of the host's available memory."""
+    import torch
+    need = 8 * math.prod(shape)
+    avail = host_available_bytes()
+    if avail is not None and need > avail // 2:
+        return None, f"skipped: {need / 1e9:.1f} GB host buffer > half of {avail / 1e9:.1f} GB available"
+    try:
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).zero_(), "pinned"
+    except RuntimeError:
+        return torch.zeros(shape, dtype=torch.float64), "pageable (pinning failed)"
+
+
+def free_device():
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def timed_solve(stlib, w, u0, prec, tol=1e-8, max_iters=100):
+    """Time to `tol` from the zero iterate (second solve; the first captures
+    the graphs), through st_solve on a device iterate."""
+    import torch
+    S = make_solver(stlib, w, u0, precision=prec, tol=tol, max_iters=max_iters)
+    V = S.zeros()
+    S.solve(V)
+    V.zero_()
+    torch.cuda.synchronize()
+    info = S.solve(V)
+    out = {"seconds": info["seconds"], "iterations": info["iterations"], "cycles": info["cycles"],
+           "rel_residual": info["rel_residual"]}
+    S.close()
+    del V
+    free_device()
+    return out
+
+
+def vcycle_rate(stlib, w, u0, steps, warmup):
+    """dof-updates/s per V-cycle of another workload (device iterate, CUDA events)."""
+    import torch
+    S = make_solver(stlib, w, u0, precision=stlib.FP32_REFINE, tol=1e-8)
+    D = w["Nt"] * w["M"] * int(math.prod(w["grid"]))
+    U = S.zeros()
+    for _ in range(warmup):
+        S.vcycle(U)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        S.vcycle(U)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    S.close()
+    del U
+    free_device()
+    return {"value": D / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dofs": D, "steps": steps}
+
+
+def extras_small(stlib, w, u0):
+    """Times to 1e-8 (both precisions), the end-to-end solve, SDC sweeps, the
+    adjoint and PFASST on a workload that fits many times over."""
+    import torch
+    D = w["Nt"] * w["M"] * int(math.prod(w["grid"]))
+    extras = {"time_to_1e-8_fp32_refine": timed_solve(stlib, w, u0, stlib.FP32_REFINE),
+              "time_to_1e-8_fp64": timed_solve(stlib, w, u0, stlib.FP64)}
+    extras["e2e_solve"] = e2e_solve(stlib, w, u0, D)
+    S3 = make_solver(stlib, w, u0)
+    V = S3.zeros()
+    S3.sdc_sweep(V, 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S3.sdc_sweep(V, 5)
+    torch.cuda.synchronize()
+    extras["sdc_sweep_dof_per_s"] = D * 5 / (time.perf_counter() - t0)
+    S3.close()
+    if w["bc"] == "periodic":
+        # adjoint: gradient of 1/2 h^d |u(T) - u_target|^2 w.r.t. nu, rho, u0
+        S4 = make_solver(stlib, w, u0, tol=1e-8)
+        S4.set_params(1.3e-2, 0.8)
+        V = S4.zeros()
+        S4.solve(V)
+        target = V[-1, -1].reshape(-1).clone()
+        S4.set_params(w["nu"], w["rho"])
+        V.zero_()
+        S4.solve(V)
+        du0 = torch.empty_like(target)
+        S4.adjoint(V, target=target, du0=du0)  # warm (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dnu, drho, ainfo = S4.adjoint(V, target=target, du0=du0)
+        torch.cuda.synchronize()
+        extras["adjoint_solve"] = {"seconds": time.perf_counter() - t0, "iterations": ainfo["iterations"],
+                                   "rel_residual": ainfo["rel_residual"], "dPhi_dnu": dnu, "dPhi_drho": drho}
+        S4.close()
+    # PFASST (3 levels, M = 1 above the finest, one sweep each) to the same
+    # tolerance from u0 spread over every node, on a space-bisected hierarchy
+    S5 = make_solver(stlib, w, u0, tol=1e-8, max_iters=300, coarsening=stlib.COARSEN_SPACE, pfasst_levels=3)
+    u0t = torch.tensor(u0, dtype=torch.float64, device="cuda").reshape(tuple(w["grid"]))
+    V = u0t.expand(S5.field_shape).contiguous()
+    S5.pfasst(V.clone(), raise_on_error=False)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pinfo = S5.pfasst(V, raise_on_error=False)
+    torch.cuda.synchronize()
+    extras["time_to_1e-8_pfasst3"] = {"seconds": time.perf_counter() - t0, "iterations": pinfo["iterations"],
+                                      "status": pinfo["status"], "rel_residual": pinfo["rel_residual"]}
+    S5.close()
+    free_device()
+    return extras
+
+
+def e2e_solve(stlib, w, u0, D):
+    """End to end through st_solve with a host iterate: U copied in once, the
+    V-cycles to 1e-8 on the device, the solution copied back once."""
+    import torch
+    S = make_solver(stlib, w, u0, precision=stlib.FP32_REFINE, tol=1e-8, max_iters=100)
+    Uh, kind = pinned_host(S.field_shape)
+    if Uh is None:
+        S.close()
+        return {"skipped": kind}
+    S.solve(Uh)  # warm (graph capture)
+    Uh.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = S.solve(Uh)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    S.close()
+    del Uh
+    free_device()
+    return {"value": D * info["cycles"] / t, "unit": UNIT, "seconds": t, "cycles": info["cycles"],
+            "rel_residual": info["rel_residual"], "h2d_bytes": D * 8, "d2h_bytes": D * 8, "host_buffer": kind}
+
 
 def run_ours(args):
     import torch
@@ -262,7 +471,10 @@ def run_ours(args):
         S.linearize(U)
         out = {}
         for name, which in KERNEL_PROBES[:-1]:
-            kms, kb = S.time_kernel(which, U, iters=2)
+            try:
+                kms, kb = S.time_kernel(which, U, iters=2)
+            except stlib.StError:
+                continue
             out[name] = {"ms": kms, "GBps": kb / (kms / 1e3) / 1e9}
         if rank == 0:
             print(json.dumps({"mode": "probe", "kernels": out}), flush=True)
@@ -298,123 +510,84 @@ def run_ours(args):
         S.close()
         return
 
-    # e2e through the C ABI with host buffers (H2D + D2H of U inside every step)
-    Uh = torch.zeros(S.field_shape, dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        S.vcycle(Uh)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        S.vcycle(Uh)
-    torch.cuda.synchronize()
-    ms_e2e = reduce_max((time.perf_counter() - t0) * 1e3 / args.steps, dist, "cuda")
-    e2e = {"value": job_value(world, D, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": D * 8,
-           "d2h_bytes_per_step": D * 8 + 8}
-
     stats = S.stats()
     # per-kernel live timings (CUDA events on the library's launching stream)
     kernels = {}
     for name, which in KERNEL_PROBES:
-        kms, kb = S.time_kernel(which, U, iters=max(5, args.steps // 2))
+        try:
+            kms, kb = S.time_kernel(which, U, iters=max(5, min(20, args.steps // 2)))
+        except stlib.StError as err:
+            kernels[name] = {"error": str(err)[:120]}
+            continue
         kernels[name] = {"ms": kms, "bytes": kb, "GBps": (kb / (kms / 1e3) / 1e9) if kb else None}
+    final_rel = norms[-1] / (math.sqrt(w["M"]) * float((u0 ** 2).sum()) ** 0.5)
+
+    # e2e through the C ABI with host buffers (H2D + D2H of U inside every
+    # step); the device iterate is released first (the library stages a host
+    # iterate in a device copy of its own)
+    del U
+    free_device()
+    Uh, host_kind = pinned_host(S.field_shape)
+    e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": D * 8, "d2h_bytes_per_step": D * 8 + 8,
+           "host_buffer": host_kind}
+    if Uh is not None:
+        for _ in range(2):
+            S.vcycle(Uh)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            S.vcycle(Uh)
+        torch.cuda.synchronize()
+        ms_e2e = reduce_max((time.perf_counter() - t0) * 1e3 / args.steps, dist, "cuda")
+        e2e.update(value=job_value(world, D, ms_e2e), ms_per_step=ms_e2e)
+    S.close()
+    del Uh
+    free_device()
+
     hbm, src = measured_peaks()
-    # dominant kernel (largest share of the step's time in the ncu launch
-    # list): the Jacobi sweep of the shifted slab systems that updates z
-    # (k_inner4<2, 3, 1>, every sweep but a slab solve's last), timed here at
-    # level 0 where it moves the most bytes; HBM bound
+    # dominant kernel: the Jacobi sweep of the shifted slab systems that
+    # updates z (k_inner4<2, M, 1>, every sweep but a slab solve's last),
+    # timed here at level 0 where it moves the most bytes; HBM bound
     k = kernels["slab_jacobi_plain"]
-    roofline = {"bound": "hbm", "kernel": "k_inner4<2,3,1>: level-0 Jacobi sweep of the shifted slab systems "
-                                          "(z, y, cbar in, z out; direct float4 loads)",
-                "achieved": k["GBps"], "peak": hbm, "unit": "GB/s", "frac": k["GBps"] / hbm,
-                "traffic": ncu_traffic("k_inner4<2, 3, 1>", D),
+    kname = f"k_inner4<2, {w['M']}, 1>"
+    roofline = {"bound": "hbm", "kernel": kname + ": level-0 Jacobi sweep of the shifted slab systems "
+                                                  "(z, y, cbar in, z out; direct float4 loads)",
+                "achieved": k.get("GBps"), "peak": hbm, "unit": "GB/s",
+                "frac": (k["GBps"] / hbm) if k.get("GBps") else None,
+                "traffic": ncu_traffic(kname, D),
                 "peak_source": f"{src} copy bandwidth (burst; kernel timed alone)",
-                "bytes_per_dof": k["bytes"] / D}
+                "frac_of_datasheet_7900": (k["GBps"] / HBM_DATASHEET_GBS) if k.get("GBps") else None,
+                "bytes_per_dof": (k["bytes"] / D) if k.get("bytes") else None}
     kf = kernels["fine_residual_fp64"]
-    fine_residual = {"kernel": "k_residual_tile<3>: FP64-accurate residual on the FP32 pipes (tiles split once)",
-                     "ms": kf["ms"], "GBps": kf["GBps"], "frac_of_hbm": kf["GBps"] / hbm,
-                     "note": "issue bound on the FP32/integer pipes (compensated double-float arithmetic)"}
-    fp32_kernels = {n: {"GBps": kernels[n]["GBps"], "frac_of_" + src + "_hbm": kernels[n]["GBps"] / hbm}
-                    for n in ("level_residual_transform", "slab_jacobi", "slab_jacobi_plain", "shifted_residual",
-                              "inner_restrict", "prolong_add")}
+    fine_residual = {"kernel": f"k_residual_tile<{w['M']}>: FP64-accurate residual on the FP32 pipes",
+                     "ms": kf.get("ms"), "GBps": kf.get("GBps"),
+                     "frac_of_hbm": (kf["GBps"] / hbm) if kf.get("GBps") else None}
+    hbm_kernels = {n: {"GBps": kernels[n]["GBps"], "frac_of_" + src + "_hbm": kernels[n]["GBps"] / hbm}
+                   for n in ("level_residual_transform", "slab_jacobi", "slab_jacobi_plain", "shifted_residual",
+                             "inner_restrict", "prolong_add", "update") if kernels[n].get("GBps")}
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
-        for name, prec in (("fp32_refine", stlib.FP32_REFINE), ("fp64", stlib.FP64)):
-            S2 = make_solver(stlib, w, u0, precision=prec, tol=1e-8, max_iters=100)
-            V = S2.zeros()
-            S2.solve(V)  # warm (graph capture)
-            V.zero_()
-            torch.cuda.synchronize()
-            info = S2.solve(V)
-            extras["time_to_1e-8_" + name] = {"seconds": info["seconds"], "iterations": info["iterations"],
-                                              "rel_residual": info["rel_residual"]}
-            S2.close()
-        # end to end through st_solve with a host iterate: U copied in once, the
-        # V-cycles to 1e-8 on the device, the solution copied back once
-        S6 = make_solver(stlib, w, u0, precision=stlib.FP32_REFINE, tol=1e-8, max_iters=100)
-        Uh6 = torch.zeros(S6.field_shape, dtype=torch.float64).pin_memory()
-        S6.solve(Uh6)  # warm (graph capture)
-        Uh6.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        info6 = S6.solve(Uh6)
-        torch.cuda.synchronize()
-        t6 = time.perf_counter() - t0
-        extras["e2e_solve"] = {"value": D * info6["cycles"] / t6, "unit": UNIT, "seconds": t6,
-                               "cycles": info6["cycles"], "rel_residual": info6["rel_residual"],
-                               "h2d_bytes": D * 8, "d2h_bytes": D * 8}
-        S6.close()
-        del Uh6
-        # SDC sweep throughput on the same workload
-        S3 = make_solver(stlib, w, u0)
-        V = S3.zeros()
-        S3.sdc_sweep(V, 2)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        S3.sdc_sweep(V, 5)
-        torch.cuda.synchronize()
-        extras["sdc_sweep_dof_per_s"] = D * 5 / (time.perf_counter() - t0)
-        S3.close()
-        if w["bc"] == "periodic":
-            # adjoint: gradient of 1/2 h^d |u(T) - u_target|^2 w.r.t. nu, rho, u0
-            S4 = make_solver(stlib, w, u0, tol=1e-8)
-            S4.set_params(1.3e-2, 0.8)
-            V = S4.zeros()
-            S4.solve(V)
-            target = V[-1, -1].reshape(-1).clone()
-            S4.set_params(w["nu"], w["rho"])
-            V.zero_()
-            S4.solve(V)
-            du0 = torch.empty_like(target)
-            S4.adjoint(V, target=target, du0=du0)  # warm (graph capture)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dnu, drho, ainfo = S4.adjoint(V, target=target, du0=du0)
-            torch.cuda.synchronize()
-            extras["adjoint_solve"] = {"seconds": time.perf_counter() - t0, "iterations": ainfo["iterations"],
-                                       "rel_residual": ainfo["rel_residual"], "dPhi_dnu": dnu, "dPhi_drho": drho}
-            S4.close()
-        # PFASST (3 levels, M = 1 above the finest, one sweep each) to the same
-        # tolerance from u0 spread over every node, on a space-bisected hierarchy
-        S5 = make_solver(stlib, w, u0, tol=1e-8, max_iters=300, coarsening=stlib.COARSEN_SPACE, pfasst_levels=3)
-        u0t = torch.tensor(u0, dtype=torch.float64, device="cuda").reshape(tuple(w["grid"]))
-        V = u0t.expand(S5.field_shape).contiguous()
-        S5.pfasst(V.clone(), raise_on_error=False)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pinfo = S5.pfasst(V, raise_on_error=False)
-        torch.cuda.synchronize()
-        extras["time_to_1e-8_pfasst3"] = {"seconds": time.perf_counter() - t0, "iterations": pinfo["iterations"],
-                                          "status": pinfo["status"], "rel_residual": pinfo["rel_residual"]}
-        S5.close()
+        if D > 1e9:
+            # full-size workloads: what fits beside nothing else in HBM
+            extras["time_to_1e-8_fp32_refine"] = timed_solve(stlib, w, u0, stlib.FP32_REFINE)
+            extras["e2e_solve"] = e2e_solve(stlib, w, u0, D)
+            if args.config == "logistic2d_1024_m5":
+                w3 = WORKLOADS["logistic2d_1024_m3"]
+                u03 = make_u0(w3)
+                m3 = vcycle_rate(stlib, w3, u03, steps=max(3, min(args.steps, 20)), warmup=3)
+                m3["workload"] = w3["workload"]
+                m3["time_to_1e-8_fp32_refine"] = timed_solve(stlib, w3, u03, stlib.FP32_REFINE)
+                m3["time_to_1e-8_fp64"] = timed_solve(stlib, w3, u03, stlib.FP64)
+                extras["logistic2d_1024x1024_Nt1024_M3"] = m3
+        else:
+            extras = extras_small(stlib, w, u0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            # about 10-30 s of single-core oracle work
-            ns = {"logistic2d_256": 4, "heat1d_63": 16}.get(args.config, 1)
-            cpu = oracle_baseline(w, nslabs=ns, reps=1)
+            cpu = oracle_baseline(w)
         except Exception as ex:  # the GPU number stands without it
             cpu = {"error": str(ex)[:200]}
 
@@ -426,12 +599,10 @@ def run_ours(args):
                                parallelism=f"replicas{world}", l2="inputs larger than L2 (no flush)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": stats["launches_per_vcycle"] * args.steps,
-                "clocks": clk, "kernels": kernels, "fp32_kernels_hbm": fp32_kernels,
-                "fine_residual": fine_residual,
-                "final_rel_residual": norms[-1] / (math.sqrt(w["M"]) * float((u0 ** 2).sum()) ** 0.5),
+                "clocks": clk, "kernels": kernels, "hbm_kernels": hbm_kernels,
+                "fine_residual": fine_residual, "final_rel_residual": final_rel,
                 "extras": extras, "stats": stats}
         print(json.dumps(line), flush=True)
-    S.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -442,19 +613,19 @@ def run_reference(args):
     if rank != 0:
         return
     w = WORKLOADS[args.config]
-    ts = time_oracle(w, nslabs=1, reps=args.warmup + args.steps)
+    K = oracle_slabs(w)
+    ts = time_oracle(w, nslabs=K, reps=args.warmup + args.steps)
     timed = ts[args.warmup:]
-    Ns = int(math.prod(w["grid"]))
-    dofs = w["M"] * Ns
+    dofs = K * w["M"] * int(math.prod(w["grid"]))
     t = sum(timed) / len(timed)
     value = dofs / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(w, dofs=w["Nt"] * dofs, parallelism="cpu oracle, 1 thread"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: Newton (GMRES / sparse-LU slab solves) on slab 1 of "
-                                       f"{w['Nt']} ({dofs} dofs)"},
+            "config": dict(w, dofs=dofs, dofs_full_workload=w["Nt"] * w["M"] * int(math.prod(w["grid"])),
+                           slabs_per_step=K, parallelism="cpu oracle, 1 thread"),
+            "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": "each step: " + oracle_sample(w, K, 1)}, **host_info()),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -566,11 +737,11 @@ def run_paper_tables(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # about a second of timed steps, so the 200 ms clock sampler sees several samples
-    ap.add_argument("--steps", type=int, default=500)
+    # several seconds of timed steps at full size, so the 200 ms clock sampler sees many samples
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="logistic2d_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="warm-up and timed steps only (profiling)")

@@ -382,15 +382,19 @@ enum {
   ST_KERNEL_SHIFTED_RESIDUAL = 5, /* residual of the level-0 shifted slab systems */
   ST_KERNEL_INNER_RESTRICT = 6,   /* full weighting of that residual to the next inner grid */
   ST_KERNEL_PROLONG = 7,          /* linear interpolation + correction, inner grid 1 -> 0 */
-  ST_KERNEL_JACOBI_PLAIN = 8      /* level-0 Jacobi sweep of the shifted slab systems that only
+  ST_KERNEL_JACOBI_PLAIN = 8,     /* level-0 Jacobi sweep of the shifted slab systems that only
                                      updates z (the sweeps before the cycle's last) */
+  ST_KERNEL_UPDATE = 9            /* the defect-correction update U += alpha e in FP64, run with
+                                     alpha = 0: the update's traffic (U and e read, U written)
+                                     with U's values left unchanged */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream
  * between two CUDA events (after one untimed launch) and return the mean
  * duration per launch in milliseconds, plus the algorithmic bytes one launch
  * must move (each input read once, each output written once).  U (device,
- * Nt*M*Ns doubles) is the input of ST_KERNEL_FINE_RESIDUAL; the other kernels
+ * Nt*M*Ns doubles) is the input of ST_KERNEL_FINE_RESIDUAL and the buffer
+ * ST_KERNEL_UPDATE rewrites in place (with its own values); the other kernels
  * run on the handle's level-0 work buffers (contents unspecified). */
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch);
@@ -430,15 +434,20 @@ int st_stats(st_handle* h, st_stats_info* out);
  *   norm_out host double receiving ||G(U)||_2, or NULL (then the call does
  *           not synchronise)
  *   stream  cudaStream_t (NULL = legacy default stream)
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * Every call looks up the array's device address in the current device's
+ * context (the caller's device must be current).  Under lazy module loading
+ * (the CUDA default) the first call on a device may load the library's
+ * module, and that load allocates device memory for the module's code and
+ * this array: make one warm-up call on each device at start-up, outside any
+ * stream capture and outside any allocator callback or fixed-budget pool.
  * All calls share the one array and it keeps the last call's contents:
  * calls that overlap on the GPU (different streams or devices' host
  * threads racing on the same device) race on it - serialise them.
  * Errors: ST_ERR_INVALID_ARG for bad sizes or host pointers;
  * ST_ERR_UNSUPPORTED when a spatial plane has more than 2^26 points (the
  * partial sums would not fit) or Ns*Nt >= 2^31; ST_ERR_CUDA on a CUDA error.
- * It calls no cudaMalloc, cudaFree or other allocating routine. */
+ * Apart from that first module load, it calls no cudaMalloc, cudaFree or
+ * other allocating routine. */
 int st_residual_noalloc(const st_problem* p, const double* U, double* R, double* norm_out, void* stream);
 
 #ifdef __cplusplus

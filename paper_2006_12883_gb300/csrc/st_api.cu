@@ -2272,10 +2272,11 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
   PdlScope pdl_scope(h);
-  if (!h || iters < 1 || which < 0 || which > 8) return ST_ERR_INVALID_ARG;
+  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_UPDATE) return ST_ERR_INVALID_ARG;
   if (which >= ST_KERNEL_SHIFTED_RESIDUAL && which <= ST_KERNEL_PROLONG && h->L[0].in.size() < 2)
     return ST_ERR_UNSUPPORTED;
-  if (which == ST_KERNEL_FINE_RESIDUAL && (!U || !is_device_ptr(U))) return ST_ERR_INVALID_ARG;
+  if ((which == ST_KERNEL_FINE_RESIDUAL || which == ST_KERNEL_UPDATE) && (!U || !is_device_ptr(U)))
+    return ST_ERR_INVALID_ARG;
   Level& L0 = h->L[0];
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   const double D = (double)h->D_total;
@@ -2361,6 +2362,12 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         };
         return h->fp64 ? go(double(0)) : go(float(0));
       }
+      case ST_KERNEL_UPDATE:
+        // U + 0 * e with e zeroed above: the loads and stores of the cycle's
+        // update, U's values unchanged
+        launch_update(h->fp64, const_cast<double*>(U), L0.e, h->D_total, st, 0.0);
+        CKL();
+        return ST_OK;
       default:
         return cycle(h, 0);
     }
@@ -2371,6 +2378,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_JACOBI: bytes = D * 4 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_JACOBI_PLAIN: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
+    case ST_KERNEL_UPDATE: bytes = D * (8 + es + 8); break;
     case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_INNER_RESTRICT: {
       const double Dc = (double)L0.in[1].g.Ns * L0.Nt * h->p.M;
@@ -2384,6 +2392,8 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     }
     default: bytes = 0;
   }
+  // the update runs on a zeroed e, so U + 0 * e == U whatever e held before
+  if (which == ST_KERNEL_UPDATE) CK(cudaMemsetAsync(L0.e, 0, (size_t)h->D_total * h->esz, h->stream));
   TRY(one(h->stream));  // warm (and capture, for the cycle)
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

@@ -10,7 +10,6 @@
 // them: its scratch is a fixed file-scope device array, so the call itself
 // allocates nothing.
 #include <cmath>
-#include <mutex>
 
 #include "st_kernels.cuh"
 #include "st_setup.h"
@@ -22,29 +21,18 @@ namespace {
 constexpr long long kMaxBlocks = 1LL << 18;
 static __device__ __align__(256) double g_scratch[kMaxBlocks + 1];
 
-std::mutex g_mu;
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array for the current device.  In host code
-// the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in, so the address is
+// looked up on every call with the caller's device current: the lookup is
+// cheap, and an address cached across calls would go stale if the context
+// were torn down and the module loaded again at another address.
 int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
     return ST_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return ST_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (double*)p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = (double*)p;
   return ST_OK;
 }
 
