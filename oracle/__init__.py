@@ -21,8 +21,12 @@ Modules
   adjoint      the transposed all-at-once system and gradients
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py`` except ``multilevel.smoothing_step_exact`` (its
-relaxation weight and block choice are solver design, not paper content):
-parity unpinned for that one helper.
+``tests/test_oracle_*.py`` except three helpers whose content is solver
+design, not paper content - parity unpinned for
+``multilevel.smoothing_step_exact`` (relaxation weight and block choice),
+``multilevel.smoothing_step_jacobi`` (sweep count and weights) and
+``multilevel.restrict_cbar_time`` (the slab average of the coarse levels'
+reaction coefficient).  The slab transfers are pinned by the Galerkin
+identity R_t (A_f - C_f) P_t = A_c - C_c.
 """
 from . import collocation, space, system, multilevel, sdc, adjoint  # noqa: F401

@@ -238,5 +238,7 @@ def restrict_cbar_space(bc: int, shape, cb: np.ndarray) -> np.ndarray:
 
 
 def restrict_cbar_time(cb: np.ndarray) -> np.ndarray:
-    """Average of the two fine slabs' coefficients."""
+    """Average of the two fine slabs' coefficients.  Parity unpinned: how the
+    coarse levels' reaction coefficient is formed is solver design (any
+    choice leaves the converged solution unchanged)."""
     return 0.5 * (cb[0::2] + cb[1::2])

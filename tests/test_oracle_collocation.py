@@ -151,6 +151,64 @@ def test_time_transfers(M):
         assert abs(one @ (K @ (R @ v)) - np.ones(2 * M) @ (np.kron(np.eye(2), K) @ v)) < 1e-12
 
 
+def _two_slab_operator(M, Q, dt, lam):
+    """-dG/dU of the scalar problem u' = lam u over two slabs of length dt/2
+    (the collocation form of Eq. 2.3 on each, chained by the slab coupling
+    of Eq. 3.4): [[I - (dt/2) lam Q, 0], [-1 e_M^T, I - (dt/2) lam Q]]."""
+    I = np.eye(M)
+    eM = np.eye(M)[-1]
+    B = I - 0.5 * dt * lam * Q
+    return np.block([[B, np.zeros((M, M))], [-np.outer(np.ones(M), eM), B]])
+
+
+LAMBDAS = (-3.7, 0.8, -50.0, 2.0 + 1.5j, -1.0e3, -0.25 - 4.0j)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
+def test_time_restriction_galerkin_identity(M):
+    """Slab bisection is a Galerkin coarsening (the DG spaces of Eq. 2.9 on
+    the coarse slab are a subspace of those on its two halves, and the DG
+    form integrates polynomials exactly), so for the scalar problem
+    u' = lam u the restricted two-half-slab operator is the coarse slab's
+    collocation operator:  R_t A_f P_t = A_c = I - dt lam Q, for real
+    negative, positive and complex lam.  The data entering a coarse slab
+    from its predecessor (1 (x) u_prev on the first half) restricts to the
+    coarse slab's own coupling (1 (x) u_prev)."""
+    tau = col.radau_right_nodes(M)
+    Q = col.collocation_matrix(tau)
+    P = col.time_prolongation(tau)
+    R = col.time_restriction(tau)
+    dt = 0.37
+    for lam in LAMBDAS:
+        Ac = np.eye(M) - dt * lam * Q
+        got = R @ _two_slab_operator(M, Q, dt, lam) @ P
+        assert np.abs(got - Ac).max() <= 1e-12 * np.abs(Ac).max(), lam
+    inflow = R @ np.concatenate([np.ones(M), np.zeros(M)])
+    assert np.abs(inflow - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("M", [2, 3, 5])
+def test_time_restriction_galerkin_identity_rejects_wrong_forms(M):
+    """Plausible mistakes in R_t = K^-1 P_t^T blockdiag(K, K) break the
+    Galerkin identity: P_t^T alone (rows rescaled to keep constants), K
+    applied on the wrong side, and the two fine slabs' blocks swapped."""
+    tau = col.radau_right_nodes(M)
+    Q = col.collocation_matrix(tau)
+    P = col.time_prolongation(tau)
+    K, _, _ = col.dg_matrices(tau)
+    dt, lam = 0.37, -3.7
+    Af = _two_slab_operator(M, Q, dt, lam)
+    Ac = np.eye(M) - dt * lam * Q
+    swap = np.block([[np.zeros((M, M)), np.eye(M)], [np.eye(M), np.zeros((M, M))]])
+    wrong = {
+        "P^T row-normalised": P.T / P.T.sum(axis=1, keepdims=True),
+        "K on the wrong side": K @ P.T @ np.kron(np.eye(2), np.linalg.inv(K)),
+        "halves swapped": col.time_restriction(tau) @ swap,
+    }
+    for name, Rw in wrong.items():
+        assert np.abs(Rw @ Af @ P - Ac).max() > 1e-6, name
+
+
 @pytest.mark.parametrize("kind", ["IE", "LU"])
 @pytest.mark.parametrize("M", [1, 2, 3, 5])
 def test_sdc_qdelta(kind, M):
