@@ -53,6 +53,10 @@ WORKLOADS = {
                         u0="8 periodic Gaussian bumps, sigma 0.05, amplitude 1"),
     "logistic2d_512": dict(workload="logistic2d_512x512_Nt512_M3", grid=[512, 512], bc="periodic", Nt=512, M=3,
                            nu=1e-2, rho=1.0, T=1.0, reaction="logistic", seed=12887, u0=NOISE),
+    # a small case of the M = 5 kernel instances (1.3e8 dofs, inputs above L2, ~7 GB on the device) for
+    # profiler captures
+    "logistic2d_512_m5_nt96": dict(workload="logistic2d_512x512_Nt96_M5", grid=[512, 512], bc="periodic", Nt=96,
+                                   M=5, nu=1e-2, rho=1.0, T=96 / 1024, reaction="logistic", seed=12885, u0=NOISE),
 }
 DEFAULT_CONFIG = "logistic2d_1024_m5"
 WORKLOAD = WORKLOADS[DEFAULT_CONFIG]

@@ -200,22 +200,81 @@ def full_jacobian_dense(p: Problem, U: np.ndarray) -> np.ndarray:
 _DIRECT_MAX = 20000  # slab systems up to this size use sparse LU, larger ones GMRES
 
 
+def periodic_slab_inverse(p: Problem, c: float, dt: float | None = None) -> spla.LinearOperator:
+    """Exact inverse of the constant-coefficient slab matrix
+    dt (Q (x) (L + c I)) - I on a periodic grid (the slab Jacobian of Eq. 2.3
+    with R'(u) replaced by the constant c).  Q = V diag(mu) V^-1 decouples
+    the nodes and the discrete Fourier transform diagonalises the periodic
+    FD Laplacian (eigenvalue sum_a (2 cos(2 pi k_a / n_a) - 2) / h_a^2 for
+    mode k), so the inverse divides mode k of node q by
+    dt mu_q (nu lambda_k + c) - 1.  Used as the preconditioner of the
+    Newton steps' Krylov solves on large periodic slabs."""
+    dt = p.dt if dt is None else dt
+    M, Ns, shape = p.M, p.Ns, p.shape
+    mu, V = np.linalg.eig(p.Q)
+    Vinv = np.linalg.inv(V)
+    lam = np.zeros(shape)
+    for a, n in enumerate(shape):
+        h = space.spacing(space.PERIODIC, n, p.X)
+        k = np.arange(n)
+        ev = (2.0 * np.cos(2.0 * np.pi * k / n) - 2.0) / (h * h)
+        lam = lam + ev.reshape([n if b == a else 1 for b in range(len(shape))])
+    denom = dt * mu.reshape((M,) + (1,) * len(shape)) * (p.nu * lam[None] + c) - 1.0
+    axes = tuple(range(1, len(shape) + 1))
+
+    def apply(b):
+        B = np.asarray(b).reshape((M,) + shape)
+        Y = np.fft.fftn(np.tensordot(Vinv, B, axes=1), axes=axes) / denom
+        return np.tensordot(V, np.fft.ifftn(Y, axes=axes), axes=1).real.reshape(-1)
+
+    return spla.LinearOperator((M * Ns, M * Ns), matvec=apply, dtype=np.float64)
+
+
+def slab_jacobian_operator(p: Problem, Un: np.ndarray) -> spla.LinearOperator:
+    """dG_n/dU_n (``slab_jacobian``) applied without assembling it:
+    v -> dt Q (L v_j + R'(U_{n,j}) v_j)_j - v."""
+    M, Ns = p.M, p.Ns
+    dR = p.dR(Un.reshape(M, Ns))
+
+    def apply(v):
+        V = np.asarray(v).reshape(M, Ns)
+        LV = (p.L @ V.T).T
+        return (p.dt * (p.Q @ (LV + dR * V)) - V).reshape(-1)
+
+    return spla.LinearOperator((M * Ns, M * Ns), matvec=apply, dtype=np.float64)
+
+
 class _SlabSolver:
     """Linear solves with one slab Jacobian: sparse LU for small systems;
     restarted GMRES(50) to a 1e-14 relative residual for large ones (the slab
-    matrix I - dt Q (x) (L + D) is well conditioned for these step sizes)."""
+    matrix I - dt Q (x) (L + D) is well conditioned for these step sizes),
+    matrix-free, preconditioned on periodic grids by the exact inverse of the
+    constant-coefficient slab matrix (``periodic_slab_inverse``)."""
 
-    def __init__(self, A):
-        self.A = A
-        self.lu = spla.splu(A) if A.shape[0] <= _DIRECT_MAX else None
+    def __init__(self, p: Problem, Un: np.ndarray):
+        self.p, self.Un = p, Un
+        n = p.M * p.Ns
+        self.lu = spla.splu(slab_jacobian(p, Un)) if n <= _DIRECT_MAX else None
+        self.precond = None
+        if self.lu is None and p.bc == space.PERIODIC:
+            self.precond = periodic_slab_inverse(p, float(np.mean(p.dR(Un))))
 
     def solve(self, b):
         if self.lu is not None:
             return self.lu.solve(b)
-        x, info = spla.gmres(self.A, b, rtol=1e-14, atol=0.0, restart=50, maxiter=200)
+        A = slab_jacobian_operator(self.p, self.Un)
+        # preconditioned, the relative residual stalls at its rounding floor
+        # (a few 1e-14); the Newton iteration around the solve takes G itself
+        # to 1e-14, so a 1e-12 linear solve costs no accuracy
+        rtol = 1e-14 if self.precond is None else 1e-12
+        x, info = spla.gmres(A, b, rtol=rtol, atol=0.0, restart=50, maxiter=200, M=self.precond)
         if info != 0:
-            x = spla.spsolve(self.A, b)
+            x = spla.spsolve(slab_jacobian(self.p, self.Un), b)
         return x
+
+
+def _slab_solver(p: Problem, Un: np.ndarray) -> _SlabSolver:
+    return _SlabSolver(p, Un.copy())
 
 
 def _newton_slab(p: Problem, prev: np.ndarray, guess: np.ndarray, lu_cache: dict | None,
@@ -239,10 +298,10 @@ def _newton_slab(p: Problem, prev: np.ndarray, guess: np.ndarray, lu_cache: dict
             break
         if linear and lu_cache is not None:
             if "lu" not in lu_cache:
-                lu_cache["lu"] = _SlabSolver(slab_jacobian(p, Un))
+                lu_cache["lu"] = _slab_solver(p, Un)
             lu = lu_cache["lu"]
         else:
-            lu = _SlabSolver(slab_jacobian(p, Un))
+            lu = _slab_solver(p, Un)
         delta = lu.solve(-g.ravel()).reshape(M, Ns)
         if linear:
             Un = Un + delta

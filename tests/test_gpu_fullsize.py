@@ -5,14 +5,15 @@ configuration bench.py uses (FP32 cycle + FP64-accurate residual):
   3D cubic 128^3 periodic, Nt=128, M=3 (8e8 dofs)
   adjoint: 2D logistic 512^2, Nt=512, M=3 (4e8 dofs)
 
-The oracle cannot solve them whole, so each is checked on what it can compute
-one piece at a time: the collocation residual (Eq. 2.3 + slab coupling)
-evaluated point by point at sampled (slab, point) pairs of the GPU solution,
-and completely on the first and the last slab.  (Causality of the block lower
-bidiagonal system, Eq. 3.4, is checked against the oracle's one-slab solve at
-256^2 in test_gpu_solve.py; a full-resolution one-slab oracle solve here takes
-minutes.)  The adjoint gradients are checked by the transposition identity and by
-exact directional derivatives of the FP64 residual."""
+The oracle cannot solve them whole, so each is checked on what it can compute:
+the error against the oracle's solution of the first K slabs at full spatial
+resolution (the system of Eq. 3.4 is block lower bidiagonal, so by causality
+the first K slabs of the full solution are the K-slab problem's solution);
+the collocation residual (Eq. 2.3 + slab coupling) evaluated point by point at
+sampled (slab, point) pairs of the GPU solution; and the complete residual of
+the first and the last slab.  The adjoint gradients are checked by the
+transposition identity and by exact directional derivatives of the FP64
+residual."""
 import numpy as np
 import pytest
 
@@ -47,7 +48,17 @@ def _sampled_residual(case, p, U, u0, nsamples=48, seed=0):
     return worst, scale
 
 
-def _check_solution(case, tol=1e-10):
+def _truncation_error(p, U, u0, K):
+    """Relative 2-norm error of the GPU's first K slabs against the oracle's
+    solve of the K-slab problem (same dt, full spatial resolution)."""
+    pk = p.with_params(Nt=K, T=K * p.dt)
+    ref = system.solve_sequential(pk, u0)
+    got = U[:K].reshape(K, p.M, -1).double().cpu().numpy()
+    assert np.abs(system.residual(pk, ref, u0)).max() < 1e-13
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), float(np.abs(got[-1, -1] - ref[-1, -1]).max())
+
+
+def _check_solution(case, tol=1e-10, K=2):
     from paper_2006_12883_gb300 import stlib
     p = case.problem()
     u0 = case.u0()
@@ -55,6 +66,12 @@ def _check_solution(case, tol=1e-10):
     U = S.zeros()
     info = S.solve(U)
     assert info["status"] == 0 and info["rel_residual"] <= tol, info
+    # error against the oracle by time truncation (FP32 cycle + FP64
+    # refinement: within 1e-8 relative)
+    rel, mx = _truncation_error(p, U, u0, K)
+    print(f"\n[truncation] {case.name}: first {K} slabs, rel 2-norm error {rel:.3e}, max error at the "
+          f"last node {mx:.3e}, GPU rel residual {info['rel_residual']:.3e}, cycles {info['cycles']}")
+    assert rel <= 1e-8, rel
     worst, scale = _sampled_residual(case, p, U, u0)
     ref = system.reference_norm(p, u0)
     assert worst <= tol * ref + 1e-13 * scale, (worst, tol * ref, scale)

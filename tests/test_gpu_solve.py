@@ -91,8 +91,8 @@ def test_host_pointer_solve():
 def test_full_size_sampled_residual_and_truncation():
     """2D logistic at 256^2 x 256 slabs x M=3 (50M space-time dofs): the GPU
     solution's collocation residual, evaluated point by point by the oracle at
-    sampled points, is at the solver tolerance; slab 1 equals the oracle's
-    one-slab solve (causality of Eq. 3.4)."""
+    sampled points, is at the solver tolerance; the whole solution matches the
+    oracle's slab-by-slab solve of all 256 slabs."""
     from paper_2006_12883_gb300 import stlib
     case = Case("logistic2d_256", (256, 256), space.PERIODIC, 1e-2, 256, 3, reaction=space.LOGISTIC, rho=1.0,
                 u0_kind="noise", seed=12884)
@@ -110,8 +110,11 @@ def test_full_size_sampled_residual_and_truncation():
     from tests.gpu_cases import residual_scale
     bound = 1e-10 * system.reference_norm(p, u0) + 1e-13 * residual_scale(p, Uh[:2])
     assert np.abs(Gs).max() <= bound, (np.abs(Gs).max(), bound)
-    first = system.solve_sequential(p, u0, nslabs=1)
-    assert _rel(Uh[:1], first) < 1e-8
+    ref = system.solve_sequential(p, u0)
+    err = _rel(Uh, ref)
+    print(f"\n[oracle] logistic2d_256: all {case.Nt} slabs, rel 2-norm error {err:.3e}, GPU rel residual "
+          f"{info['rel_residual']:.3e}, cycles {info['cycles']}")
+    assert err < 1e-8
     S.close()
 
 
@@ -311,7 +314,11 @@ def test_heat_paper_configs_closed_form(M, Nt):
     from paper_2006_12883_gb300 import stlib
     n = 1025
     case = Case(f"heat_paper_m{M}", (n,), space.NEUMANN, 1.0, Nt, M, u0_kind="cosine")
-    S = case.solver(precision=stlib.FP64, tol=1e-10, max_iters=200, coarsening=stlib.COARSEN_SPACE, max_levels=7)
+    # the FP64 residual's rounding floor relative to ||G(0)|| grows like
+    # eps * dt * nu * ||Delta_h|| (about 2e-11 at Nt = 32, 1e-10 at Nt = 8), so
+    # the large steps stop at 1e-10; the error is still at rounding level
+    tol = 1e-12 if Nt >= 256 else 1e-10
+    S = case.solver(precision=stlib.FP64, tol=tol, max_iters=400, coarsening=stlib.COARSEN_SPACE, max_levels=7)
     U = S.zeros()
     info = S.solve(U)
     assert info["status"] == 0, info
@@ -321,6 +328,12 @@ def test_heat_paper_configs_closed_form(M, Nt):
     dt = 1.0 / Nt
     exact = sum(a * col.stability_function(dt * (2 * np.cos(k * np.pi * h) - 2) / h ** 2, Q).real ** Nt
                 * np.cos(k * np.pi * x) for k, a in ((1, 1.0), (3, 2.0), (4, 3.0)))
-    # u(T) has decayed to about 5e-5 (e^{-pi^2}) of u0; compare relative to it
-    assert np.abs(U[-1, -1].cpu().numpy() - exact).max() <= 1e-5 * np.abs(exact).max()
+    # exact up to rounding: within 1e-12 of the data's size; u(T) has
+    # decayed to about 5e-5 (e^{-pi^2}) of u0, so also within 1e-7 of itself
+    u0 = case.u0()
+    err = np.abs(U[-1, -1].cpu().numpy() - exact).max()
+    print(f"\n[closed form] heat M={M} Nt={Nt}: max error {err:.3e} (max|u0| {np.abs(u0).max():.2f}, "
+          f"max|u(T)| {np.abs(exact).max():.3e})")
+    assert err <= 1e-12 * np.abs(u0).max()
+    assert err <= 1e-7 * np.abs(exact).max()
     S.close()

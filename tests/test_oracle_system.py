@@ -380,3 +380,35 @@ def test_residual_points_matches_full_residual():
         Gp = system.residual_points(p, U, u0, slabs, pts)
         for t, (n, s) in enumerate(zip(slabs, pts)):
             assert np.abs(Gp[t] - G[n, :, s]).max() < 1e-11
+
+
+@pytest.mark.parametrize("shape,bc,M,rx", [((24, 20), space.PERIODIC, 3, space.LOGISTIC),
+                                           ((6, 8, 4), space.PERIODIC, 2, space.CUBIC),
+                                           ((17, 9), space.DIRICHLET, 3, space.LOGISTIC),
+                                           ((33,), space.NEUMANN, 5, space.CUBIC)])
+def test_krylov_slab_solves_match_direct(monkeypatch, shape, bc, M, rx):
+    """The large-slab path of the sequential solve (matrix-free GMRES, with the
+    exact constant-coefficient inverse as preconditioner on periodic grids)
+    gives the solution of the sparse-LU path, forced here on small sizes."""
+    p = system.Problem(shape=shape, bc=bc, nu=0.05, Nt=3, M=M, T=0.3, reaction=rx, rho=1.5)
+    u0 = stgen.random_field(shape, 77, 0.4).ravel() + 0.5
+    direct = system.solve_sequential(p, u0)
+    monkeypatch.setattr(system, "_DIRECT_MAX", 0)
+    krylov = system.solve_sequential(p, u0)
+    assert np.abs(krylov - direct).max() <= 1e-13 * np.abs(direct).max()
+    assert np.abs(system.residual(p, krylov, u0)).max() < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 10), (12, 16), (20,), (2, 5)])
+def test_periodic_slab_inverse_is_exact_for_constant_coefficient(shape):
+    """periodic_slab_inverse(c) inverts the assembled slab Jacobian when
+    R'(U) = c everywhere (logistic at U = (1 - c/rho)/2), on 1D-3D grids,
+    including the two-point periodic Laplacian."""
+    p = system.Problem(shape=shape, bc=space.PERIODIC, nu=0.2, Nt=4, M=3, T=0.4, reaction=space.LOGISTIC, rho=2.0)
+    c = -0.7
+    Un = np.full((p.M, p.Ns), (1.0 - c / p.rho) / 2.0)
+    assert np.allclose(p.dR(Un), c)
+    A = system.slab_jacobian(p, Un).toarray()
+    Pinv = system.periodic_slab_inverse(p, c)
+    v = stgen.random_field((p.M * p.Ns,), 5)
+    assert np.abs(Pinv.matvec(A @ v) - v).max() < 1e-12
