@@ -293,7 +293,9 @@ int st_solve(st_handle* h, double* U, st_solve_info* info);
  * J^T lambda = -dPhi/dU backward in time with the transposed V-cycle and
  * FP64 refinement, then returns dPhi/dnu, dPhi/drho (host doubles, may be
  * NULL) and dPhi/du0 (Ns doubles, host or device, may be NULL).
- * ST_ERR_UNSUPPORTED for NEUMANN (non-symmetric Delta_h). */
+ * NEUMANN: the mirrored-ghost Delta_h is not symmetric; the solve uses
+ * Delta_h^T = W Delta_h W^-1 (W the lumped mass weights of the vertex grid,
+ * 1/2 per boundary axis) and solves for W^-1 lambda with the same kernels. */
 int st_adjoint_solve(st_handle* h, const double* U, const double* u_target,
                      double* dnu, double* drho, double* du0, st_solve_info* info);
 

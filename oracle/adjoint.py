@@ -17,7 +17,32 @@ import numpy as np
 import scipy.sparse.linalg as spla
 
 from . import space
+from . import system
 from .system import Problem, slab_jacobian, solve_sequential
+
+
+def _transposed_slab_solve(p: Problem, Un: np.ndarray, rhs: np.ndarray) -> np.ndarray:
+    """x with J_nn^T x = rhs, J_nn = dG_n/dU_n at U_n.  Sparse LU up to the
+    oracle's direct-solve size; beyond it (periodic grids) matrix-free GMRES
+    on J_nn^T v = dt (L^T + D)(Q^T v) - v with the exact inverse of the
+    constant-coefficient transposed slab matrix as preconditioner, to a
+    1e-13 relative residual."""
+    M, Ns = p.M, p.Ns
+    if M * Ns <= system._DIRECT_MAX or p.bc != space.PERIODIC:
+        return spla.spsolve(slab_jacobian(p, Un).T.tocsc(), rhs.ravel()).reshape(M, Ns)
+    dR = p.dR(Un.reshape(M, Ns))
+    LT = p.L.T.tocsr()
+
+    def apply(v):
+        W = p.Q.T @ np.asarray(v).reshape(M, Ns)
+        return (p.dt * ((LT @ W.T).T + dR * W) - np.asarray(v).reshape(M, Ns)).reshape(-1)
+
+    A = spla.LinearOperator((M * Ns, M * Ns), matvec=apply, dtype=np.float64)
+    pre = system.periodic_slab_inverse(p, float(np.mean(dR)), transpose=True)
+    x, info = spla.gmres(A, rhs.ravel(), rtol=1e-13, atol=0.0, restart=50, maxiter=200, M=pre)
+    if info != 0:
+        raise RuntimeError(f"transposed slab solve did not converge ({info})")
+    return x.reshape(M, Ns)
 
 
 def cell_volume(p: Problem) -> float:
@@ -45,8 +70,7 @@ def adjoint_solve(p: Problem, U: np.ndarray, gT: np.ndarray) -> np.ndarray:
         if n == p.Nt - 1:
             rhs[-1] -= gT.reshape(-1)
         rhs[-1] -= carry
-        Jt = slab_jacobian(p, U[n]).T.tocsc()
-        lam[n] = spla.spsolve(Jt, rhs.ravel()).reshape(p.M, p.Ns)
+        lam[n] = _transposed_slab_solve(p, U[n], rhs)
         carry = lam[n].sum(axis=0)
     return lam
 

@@ -200,7 +200,8 @@ def full_jacobian_dense(p: Problem, U: np.ndarray) -> np.ndarray:
 _DIRECT_MAX = 20000  # slab systems up to this size use sparse LU, larger ones GMRES
 
 
-def periodic_slab_inverse(p: Problem, c: float, dt: float | None = None) -> spla.LinearOperator:
+def periodic_slab_inverse(p: Problem, c: float, dt: float | None = None,
+                          transpose: bool = False) -> spla.LinearOperator:
     """Exact inverse of the constant-coefficient slab matrix
     dt (Q (x) (L + c I)) - I on a periodic grid (the slab Jacobian of Eq. 2.3
     with R'(u) replaced by the constant c).  Q = V diag(mu) V^-1 decouples
@@ -208,10 +209,12 @@ def periodic_slab_inverse(p: Problem, c: float, dt: float | None = None) -> spla
     FD Laplacian (eigenvalue sum_a (2 cos(2 pi k_a / n_a) - 2) / h_a^2 for
     mode k), so the inverse divides mode k of node q by
     dt mu_q (nu lambda_k + c) - 1.  Used as the preconditioner of the
-    Newton steps' Krylov solves on large periodic slabs."""
+    Newton steps' Krylov solves on large periodic slabs.  ``transpose``: the
+    inverse of the transposed matrix (Q^T in place of Q; the periodic FD
+    Laplacian is symmetric), for the adjoint's backward slab solves."""
     dt = p.dt if dt is None else dt
     M, Ns, shape = p.M, p.Ns, p.shape
-    mu, V = np.linalg.eig(p.Q)
+    mu, V = np.linalg.eig(p.Q.T if transpose else p.Q)
     Vinv = np.linalg.inv(V)
     lam = np.zeros(shape)
     for a, n in enumerate(shape):

@@ -602,6 +602,26 @@ void launch_add_state(double* W, const double* U, const double* u0, long long Ns
   st_launch(k_add_state, blocks_for(Ns * Nt * M, 256), 256, 0, st, W, U, u0, Ns, Nt, M);
 }
 
+// v <- W v (inverse = 0) or W^-1 v (inverse = 1) on every plane, W the lumped
+// mass weights of a Neumann vertex grid relative to h^d: a factor 1/2 for
+// each axis on which the point is a boundary vertex.  Exact (powers of two).
+__global__ void __launch_bounds__(256) k_mass_weight(double* __restrict__ v, GridP g, long long planes,
+                                                     int inverse) {
+  grid_dep_wait();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= planes * g.Ns) return;
+  int i, j, k;
+  decompose(idx % g.Ns, g, i, j, k);
+  int nb = (i == 0 || i == g.n0 - 1) ? 1 : 0;
+  if (g.n1 > 1 && (j == 0 || j == g.n1 - 1)) ++nb;
+  if (g.n2 > 1 && (k == 0 || k == g.n2 - 1)) ++nb;
+  if (nb) v[idx] = inverse ? ldexp(v[idx], nb) : ldexp(v[idx], -nb);
+}
+
+void launch_mass_weight(double* v, const GridP& g, long long planes, int inverse, cudaStream_t st) {
+  st_launch(k_mass_weight, blocks_for(planes * g.Ns, 256), 256, 0, st, v, g, planes, inverse);
+}
+
 void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha) {
   if (((uintptr_t)U & 15) == 0 && ((uintptr_t)e & 15) == 0) {
     const unsigned nb = blocks_for((n + 3) / 4, 256);

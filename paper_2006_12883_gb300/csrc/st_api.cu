@@ -2036,12 +2036,23 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, d
                               double* du0, st_solve_info* info) {
   PdlScope pdl_scope(h);
   if (!h || !U || !gT) return ST_ERR_INVALID_ARG;
-  if (h->p.bc == ST_BC_NEUMANN) return ST_ERR_UNSUPPORTED;
   const double t0 = now_s();
   double* Ud = nullptr;
   TRY(stage_in(h, U, &Ud, true));
   const double* gd = nullptr;
   TRY(stage_plane(h, gT, h->plane, &gd));
+  // Neumann: the mirrored-ghost Laplacian is not symmetric, L^T = W L W^-1
+  // with W the lumped mass weights (L = -M_h^-1 K_h, K_h symmetric), so
+  // J^T = W J^ W^-1, J^ being J^T with L in place of L^T - the operator the
+  // transposed kernels apply.  Solve J^ mu = -W^-1 g, then lambda = W mu.
+  const bool neumann = h->p.bc == ST_BC_NEUMANN;
+  if (neumann) {
+    if (gd != h->plane)
+      CK(cudaMemcpyAsync(h->plane, gd, h->L[0].g.Ns * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    launch_mass_weight(h->plane, h->L[0].g, 1, 1, h->stream);
+    CKL();
+    gd = h->plane;
+  }
   if (!h->lam) TRY(alloc_typed(h, &h->lam, h->D_total * sizeof(double)));
   CK(cudaMemsetAsync(h->lam, 0, h->D_total * sizeof(double), h->stream));
   // linearise at U (cbar of every level, coarsest blocks)
@@ -2071,6 +2082,10 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT, d
     if (it >= h->o.max_iters) { status = ST_ERR_NOT_CONVERGED; break; }
     TRY(cycle(h, 1));
     launch_update(h->fp64, h->lam, h->L[0].e, h->D_total, h->stream);
+    CKL();
+  }
+  if (neumann) {
+    launch_mass_weight(h->lam, h->L[0].g, (long long)h->L[0].Nt * h->p.M, 0, h->stream);
     CKL();
   }
   // gradients

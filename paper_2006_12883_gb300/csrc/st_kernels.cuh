@@ -102,6 +102,7 @@ void launch_sum_partials(const double* part, long long n, double* out, cudaStrea
 void launch_add_state(double* W, const double* U, const double* u0, long long Ns, int Nt, int M, cudaStream_t st);
 // U += alpha * e (n values)
 void launch_update(int fp64, double* U, const void* e, long long n, cudaStream_t st, double alpha = 1.0);
+void launch_mass_weight(double* v, const GridP& g, long long planes, int inverse, cudaStream_t st);
 void launch_sdc_rhs(int D, int fp64, const GridP& g, int Nt, int M, int m, double nu, int reaction,
                     double rho, const SdcCoef& cf, const void* G, const void* delta, const double* U,
                     void* y, cudaStream_t st);

@@ -132,6 +132,17 @@ def test_adjoint_512_exact_identities():
     assert info["status"] == 0, info
     lam = S.adjoint_lambda()
     gT = h2 * (U[-1, -1].reshape(-1) - target)
+    # the last K slabs of lambda against the oracle's backward solve of those
+    # slabs: J^T is block upper bidiagonal, so the window needs only the
+    # terminal data and the window's U
+    K = 2
+    pk = p.with_params(Nt=K, T=K * p.dt)
+    lam_ref = oadj.adjoint_solve(pk, U[-K:].reshape(K, p.M, -1).double().cpu().numpy(), gT.cpu().numpy())
+    lam_w = lam[-K:].reshape(K, p.M, -1).double().cpu().numpy()
+    err = float(np.linalg.norm(lam_w - lam_ref) / np.linalg.norm(lam_ref))
+    print(f"\n[adjoint window] adjoint_512: last {K} slabs, rel 2-norm error of lambda {err:.3e}, "
+          f"adjoint rel residual {info['rel_residual']:.3e}")
+    assert err <= 1e-6, err
 
     def G(Uv, nu=case.nu, rho=case.rho, u0=None):
         S.set_params(nu, rho)

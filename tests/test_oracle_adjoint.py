@@ -67,3 +67,18 @@ def test_adjoint_central_fd(kind):
     direction = stgen.random_field((64,), 46)
     fd_u0 = adjoint.fd_gradient_u0(p, u0, target, direction)
     assert abs(float(du0 @ direction) - fd_u0) < 1e-6 * abs(fd_u0)
+
+
+def test_large_periodic_transposed_solves_match_direct(monkeypatch):
+    """The adjoint's Krylov path for large periodic slabs (matrix-free J^T,
+    preconditioned by the exact transposed constant-coefficient inverse)
+    gives the sparse-LU adjoint, forced here on a small grid."""
+    p = system.Problem(shape=(12, 16), bc=space.PERIODIC, nu=0.05, Nt=3, M=3, T=0.3, reaction=space.LOGISTIC,
+                       rho=1.2)
+    u0 = stgen.random_field(p.shape, 31, 0.3).ravel() + 0.5
+    U = system.solve_sequential(p, u0)
+    gT = stgen.random_field((p.Ns,), 32)
+    direct = adjoint.adjoint_solve(p, U, gT)
+    monkeypatch.setattr(system, "_DIRECT_MAX", 0)
+    krylov = adjoint.adjoint_solve(p, U, gT)
+    assert np.abs(krylov - direct).max() <= 1e-12 * np.abs(direct).max()
