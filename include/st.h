@@ -162,6 +162,9 @@ typedef struct {
                            tiles through TMA copies (persistent, two stages); a
                            wait that expires makes the call report
                            ST_ERR_TIMEOUT.  0: direct float4 loads. */
+  int recompute_slabs;  /* slab recomputation checkpointing (st_ckpt_*): slabs
+                           per block, a divisor of Nt; 0 (default) = off.
+                           st_create ignores it. */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -308,6 +311,52 @@ int st_adjoint_solve_terminal(st_handle* h, const double* U, const double* gT,
  * of U, Nt*M*Ns doubles, host or device) into out.  ST_ERR_INVALID_ARG if no
  * adjoint solve has run on this handle. */
 int st_adjoint_lambda(st_handle* h, double* out);
+
+/* ---------------------------------------------------------------------
+ * Slab recomputation checkpointing (not in the paper; the adjoint is
+ * derived from (*)).  The system (*) is block lower bidiagonal in time, so
+ * the slabs can be solved block after block, each block (K = recompute_slabs
+ * slabs) taking as initial value the last node plane of the block before it;
+ * J^T is block upper bidiagonal, so the adjoint runs block after block
+ * backward, each block's terminal data being dPhi/d(initial value) of the
+ * block after it (the du0 of that block's adjoint solve).  An st_ckpt keeps
+ * only the initial planes of the Nt/K blocks and a K-slab workspace; the
+ * adjoint pass recomputes each block's U from its initial plane.  Device
+ * memory: a K-slab handle, K*M*Ns doubles for the block iterate and
+ * (Nt/K + 2)*Ns doubles, instead of the Nt-slab handle and U.
+ * ------------------------------------------------------------------- */
+typedef struct st_ckpt st_ckpt;
+
+/* Create: o->recompute_slabs = K >= 1 must divide p->Nt (else
+ * ST_ERR_INVALID_ARG); the block handle is st_create of p with Nt = K and
+ * T = K dt (same dt), so every option of o applies to the block solves. */
+int st_ckpt_create(const st_problem* p, const st_solver_opts* o, const st_runtime* rt, st_ckpt** out);
+
+/* Forward pass: solve the Nt slabs block after block (st_solve from the zero
+ * guess on each block, to o->tol relative to the block's own ||G(0)||),
+ * keeping each block's initial plane; uT (Ns doubles, host or device, may
+ * be NULL) receives u_{Nt,M}.  info sums iterations and cycles over the
+ * blocks and reports the largest block residual; the first block that fails
+ * ends the pass with its status. */
+int st_ckpt_forward(st_ckpt* c, double* uT, st_solve_info* info);
+
+/* Adjoint pass after st_ckpt_forward: for the blocks from the last to the
+ * first, recompute U of the block from its initial plane, then
+ * st_adjoint_solve_terminal on the block with the terminal data gT (last
+ * block) or the previous result's du0.  dnu, drho (host, may be NULL) sum
+ * the blocks' contributions; du0 (Ns doubles, host or device, may be NULL)
+ * is the first block's.  ST_ERR_INVALID_ARG without a forward pass since the
+ * last st_ckpt_set_params / st_ckpt_set_u0. */
+int st_ckpt_adjoint(st_ckpt* c, const double* gT, double* dnu, double* drho, double* du0,
+                    st_solve_info* info);
+
+/* Replace nu, rho / the initial value (Ns doubles, host or device); the next
+ * st_ckpt_adjoint needs a new forward pass. */
+int st_ckpt_set_params(st_ckpt* c, double nu, double rho);
+int st_ckpt_set_u0(st_ckpt* c, const double* u0);
+
+/* Release everything (stream-ordered); NULL is allowed. */
+void st_ckpt_destroy(st_ckpt* c);
 
 const char* st_status_str(int status);
 

@@ -1513,6 +1513,7 @@ void st_default_opts(st_solver_opts* o) {
   o->pfasst_coarse_M = 1;
   o->pfasst_sweeps = 1;
   o->use_tma = 1;
+  o->recompute_slabs = 0;
 }
 
 const char* st_status_str(int s) {

@@ -42,7 +42,7 @@ class StSolverOpts(ctypes.Structure):
                 ("smooth_sweeps", c_int), ("line_search", c_int),
                 ("exact_jacobian", c_int), ("krylov", c_int), ("krylov_rtol", c_double),
                 ("krylov_fallback", c_int), ("pfasst_levels", c_int), ("pfasst_coarse_M", c_int),
-                ("pfasst_sweeps", c_int), ("use_tma", c_int)]
+                ("pfasst_sweeps", c_int), ("use_tma", c_int), ("recompute_slabs", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -122,6 +122,13 @@ _SIGS = {
     "st_stats": (c_int, [c_void_p, POINTER(StStatsInfo)]),
     "st_wait_selftest": (c_int, [c_void_p]),
     "st_residual_noalloc": (c_int, [POINTER(StProblem), c_void_p, c_void_p, POINTER(c_double), c_void_p]),
+    "st_ckpt_create": (c_int, [POINTER(StProblem), POINTER(StSolverOpts), POINTER(StRuntime), POINTER(c_void_p)]),
+    "st_ckpt_forward": (c_int, [c_void_p, c_void_p, POINTER(StSolveInfo)]),
+    "st_ckpt_adjoint": (c_int, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double), c_void_p,
+                                POINTER(StSolveInfo)]),
+    "st_ckpt_set_params": (c_int, [c_void_p, c_double, c_double]),
+    "st_ckpt_set_u0": (c_int, [c_void_p, c_void_p]),
+    "st_ckpt_destroy": (None, [c_void_p]),
 }
 
 KERNEL_FINE_RESIDUAL, KERNEL_LEVEL_RESIDUAL, KERNEL_JACOBI, KERNEL_BACKTRANSFORM, KERNEL_VCYCLE = 0, 1, 2, 3, 4
@@ -471,23 +478,30 @@ def _stsolve_function():
         def forward(ctx, solver, nu, rho, u0):
             solver.set_params(float(nu), float(rho))
             solver.set_u0(u0.detach().to(solver.device))
-            U = solver.zeros()
-            solver.solve(U)
             ctx.solver = solver
             ctx.theta = (float(nu), float(rho))
             ctx.u0 = u0.detach()
+            if isinstance(solver, CheckpointSolver):
+                # only the blocks' initial planes are kept; backward recomputes
+                uT, _ = solver.forward()
+                return uT
+            U = solver.zeros()
+            solver.solve(U)
             ctx.save_for_backward(U)
             return U[-1, -1].clone()
 
         @staticmethod
         def backward(ctx, g):
-            (U,) = ctx.saved_tensors
             S = ctx.solver
-            S.set_params(*ctx.theta)
-            S.set_u0(ctx.u0.to(S.device))
             gT = g.detach().to(device=S.device, dtype=torch.float64).contiguous().reshape(-1)
             du0 = torch.empty(S.Ns, dtype=torch.float64, device=S.device)
-            dnu, drho, _ = S.adjoint(U, gT=gT, du0=du0)
+            if isinstance(S, CheckpointSolver):
+                dnu, drho, _ = S.adjoint(gT, du0=du0)
+            else:
+                (U,) = ctx.saved_tensors
+                S.set_params(*ctx.theta)
+                S.set_u0(ctx.u0.to(S.device))
+                dnu, drho, _ = S.adjoint(U, gT=gT, du0=du0)
             dev, dt = ctx.u0.device, torch.float64
             return (None, torch.tensor(dnu, dtype=dt, device=dev), torch.tensor(drho, dtype=dt, device=dev),
                     du0.reshape(ctx.u0.shape).to(dev))
@@ -509,3 +523,87 @@ class STSolve:
     @staticmethod
     def apply(solver, nu, rho, u0):
         return _stsolve_function().apply(solver, nu, rho, u0)
+
+
+class CheckpointSolver:
+    """Slab recomputation checkpointing (st_ckpt_*): the Nt-slab problem solved
+    in blocks of `block_slabs` slabs on one block-sized handle, keeping only
+    each block's initial plane; the adjoint recomputes each block's U from
+    it.  forward() -> u(T); adjoint(gT) -> (dnu, drho, du0).  Usable with
+    STSolve.apply in place of a Solver."""
+
+    def __init__(self, grid_shape, bc, nu, Nt, M, u0, block_slabs, T=1.0, X=1.0, reaction=NONE, rho=0.0,
+                 opts: StSolverOpts | None = None, stream=None):
+        torch = _torch()
+        self.grid_shape = tuple(grid_shape)
+        self.Nt, self.M, self.block_slabs = Nt, M, block_slabs
+        self.Ns = 1
+        for n in self.grid_shape:
+            self.Ns *= n
+        self.opts = opts if opts is not None else st_default_opts()
+        self.opts.recompute_slabs = int(block_slabs)
+        u0t = torch.as_tensor(u0, dtype=torch.float64).reshape(-1).contiguous()
+        self._u0 = u0t
+        self.problem = make_problem(self.grid_shape[::-1], bc, nu, Nt, M, T, X, reaction, rho, u0t.data_ptr())
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        rt = StRuntime()
+        rt.stream = self.stream.cuda_stream
+        rt.ctx = None
+        dev = self.device.index
+
+        def _alloc(nbytes, st, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st or 0)
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, st, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        rt.alloc = ALLOC_FN(_alloc)
+        rt.free = FREE_FN(_free)
+        self._rt = rt
+        h = c_void_p()
+        check(lib().st_ckpt_create(ctypes.byref(self.problem), ctypes.byref(self.opts), ctypes.byref(rt),
+                                   ctypes.byref(h)), "st_ckpt_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().st_ckpt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, nu, rho):
+        check(lib().st_ckpt_set_params(self.h, float(nu), float(rho)), "st_ckpt_set_params")
+
+    def set_u0(self, u0):
+        torch = _torch()
+        u0t = torch.as_tensor(u0, dtype=torch.float64).reshape(-1).contiguous()
+        check(lib().st_ckpt_set_u0(self.h, u0t.data_ptr()), "st_ckpt_set_u0")
+
+    def forward(self, uT=None, raise_on_error=True):
+        torch = _torch()
+        if uT is None:
+            uT = torch.empty(self.grid_shape, dtype=torch.float64, device=self.device)
+        info = StSolveInfo()
+        s = lib().st_ckpt_forward(self.h, uT.data_ptr(), ctypes.byref(info))
+        if raise_on_error:
+            check(s, "st_ckpt_forward")
+        return uT, info.as_dict()
+
+    def adjoint(self, gT, du0=None, raise_on_error=True):
+        dnu, drho = c_double(), c_double()
+        info = StSolveInfo()
+        assert gT.is_contiguous() and (du0 is None or du0.is_contiguous())
+        s = lib().st_ckpt_adjoint(self.h, gT.data_ptr(), ctypes.byref(dnu), ctypes.byref(drho),
+                                  None if du0 is None else du0.data_ptr(), ctypes.byref(info))
+        if raise_on_error:
+            check(s, "st_ckpt_adjoint")
+        return dnu.value, drho.value, info.as_dict()

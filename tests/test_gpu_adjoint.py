@@ -154,3 +154,66 @@ def test_stsolve_autograd_matches_oracle_gradients():
     assert abs(rho.grad.item() - rrho) <= 1e-8 * abs(rrho)
     assert np.linalg.norm(u0.grad.cpu().numpy().ravel() - rdu0) <= 1e-8 * np.linalg.norm(rdu0)
     S.close()
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpointed_adjoint_matches_stored(K, prec):
+    """Slab recomputation checkpointing: blocks of K slabs solved one after
+    another (exact by causality of Eq. 3.4), the adjoint recomputing each
+    block's U; u(T) and the gradients equal the stored-U path's to the solve
+    tolerance, and the oracle's."""
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    pr = stlib.FP64 if prec == "fp64" else stlib.FP32_REFINE
+    S = case.solver(precision=pr, tol=1e-12)
+    U = S.zeros()
+    assert S.solve(U)["status"] == 0
+    gT = torch.tensor(stgen.random_field((p.Ns,), 79), device="cuda")
+    du0 = torch.empty(p.Ns, dtype=torch.float64, device="cuda")
+    dnu, drho, _ = S.adjoint(U, gT=gT, du0=du0)
+    C = stlib.CheckpointSolver(case.shape, case.bc, case.nu, case.Nt, case.M, case.u0(), K, T=case.T,
+                               reaction=case.reaction, rho=case.rho, opts=stlib.make_opts(precision=pr, tol=1e-12))
+    uT, finfo = C.forward()
+    assert finfo["status"] == 0
+    assert torch.allclose(uT.reshape(-1), U[-1, -1].reshape(-1), rtol=0, atol=1e-10 * float(U.abs().max()))
+    cdu0 = torch.empty_like(du0)
+    cnu, crho, ainfo = C.adjoint(gT, du0=cdu0)
+    assert ainfo["status"] == 0
+    assert abs(cnu - dnu) <= 1e-9 * abs(dnu) and abs(crho - drho) <= 1e-9 * abs(drho), (cnu, dnu, crho, drho)
+    assert float((cdu0 - du0).norm()) <= 1e-9 * float(du0.norm())
+    Uh = U.cpu().numpy().reshape(p.Nt, p.M, -1)
+    rnu, rrho, rdu0 = oadj.gradients(p, Uh, oadj.adjoint_solve(p, Uh, gT.cpu().numpy()))
+    assert abs(cnu - rnu) <= 1e-8 * abs(rnu)
+    # a parameter change invalidates the stored planes: the adjoint refuses
+    # until the next forward pass
+    C.set_params(case.nu * 1.01, case.rho)
+    s = stlib.lib().st_ckpt_adjoint(C.h, gT.data_ptr(), None, None, None, None)
+    assert s == stlib.ST_ERR_INVALID_ARG
+    C.close()
+    S.close()
+
+
+def test_checkpointed_stsolve_autograd():
+    """STSolve.apply on a CheckpointSolver: the forward keeps only the blocks'
+    initial planes, the backward recomputes; gradients equal the oracle's."""
+    from paper_2006_12883_gb300 import stlib
+    case = ADJ
+    p = case.problem()
+    C = stlib.CheckpointSolver(case.shape, case.bc, case.nu, case.Nt, case.M, case.u0(), 2, T=case.T,
+                               reaction=case.reaction, rho=case.rho,
+                               opts=stlib.make_opts(precision=stlib.FP64, tol=1e-12))
+    target = torch.tensor(_target(case), device="cuda")
+    nu = torch.tensor(case.nu, dtype=torch.float64, requires_grad=True)
+    rho = torch.tensor(case.rho, dtype=torch.float64, requires_grad=True)
+    u0 = torch.tensor(case.u0(), device="cuda").reshape(case.shape).requires_grad_(True)
+    uT = stlib.STSolve.apply(C, nu, rho, u0)
+    h2 = float(np.prod([space.spacing(case.bc, n, case.X) for n in case.shape]))
+    loss = 0.5 * h2 * ((uT.reshape(-1) - target) ** 2).sum()
+    loss.backward()
+    _, _, (rnu, rrho, rdu0) = oadj.solve_and_gradients(p, case.u0(), target.cpu().numpy())
+    assert abs(nu.grad.item() - rnu) <= 1e-8 * abs(rnu)
+    assert abs(rho.grad.item() - rrho) <= 1e-8 * abs(rrho)
+    assert np.linalg.norm(u0.grad.cpu().numpy().ravel() - rdu0) <= 1e-8 * np.linalg.norm(rdu0)
+    C.close()

@@ -171,3 +171,50 @@ def test_adjoint_512_exact_identities():
     dG = (G(U, u0=u0 + e * w) - G(U, u0=u0 - e * w)) / (2 * e)
     assert abs(dot(du0, w) - dot(lam, dG)) <= 1e-8 * abs(dot(lam, dG))
     S.close()
+
+
+def test_adjoint_512_checkpointed_matches_stored_and_saves_memory():
+    """The adjoint workload (512^2 x 512 slabs x M = 3, gradient of
+    1/2 h^2 |u(T) - u_target|^2) with slab recomputation checkpointing in
+    blocks of 64 slabs: the gradients equal the stored-U path's, with a
+    fraction of its device memory."""
+    from paper_2006_12883_gb300 import stlib
+    case = Case("adjoint_512", (512, 512), space.PERIODIC, 1e-2, 512, 3, reaction=space.LOGISTIC, rho=1.0,
+                u0_kind="noise", seed=12887)
+    p = case.problem()
+    h2 = (1.0 / 512) ** 2
+    gT = torch.tensor(stgen.random_field((p.Ns,), 81, h2), device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    S = case.solver(precision=stlib.FP32_REFINE, tol=1e-11, max_iters=80)
+    U = S.zeros()
+    assert S.solve(U)["status"] == 0
+    du0 = torch.empty(p.Ns, dtype=torch.float64, device="cuda")
+    dnu, drho, info = S.adjoint(U, gT=gT, du0=du0)
+    assert info["status"] == 0
+    uT = U[-1, -1].clone()
+    peak_stored = torch.cuda.max_memory_allocated() - base
+    S.close()
+    del U
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    C = stlib.CheckpointSolver(case.shape, case.bc, case.nu, case.Nt, case.M, case.u0(), 64, T=case.T,
+                               reaction=case.reaction, rho=case.rho,
+                               opts=stlib.make_opts(precision=stlib.FP32_REFINE, tol=1e-11, max_iters=80))
+    cuT, finfo = C.forward()
+    assert finfo["status"] == 0
+    cdu0 = torch.empty_like(du0)
+    cnu, crho, ainfo = C.adjoint(gT, du0=cdu0)
+    assert ainfo["status"] == 0
+    peak_ckpt = torch.cuda.max_memory_allocated() - base
+    C.close()
+    print(f"\n[checkpointing] adjoint_512: blocks of 64 slabs, peak device memory {peak_ckpt / 1e9:.2f} GB "
+          f"vs {peak_stored / 1e9:.2f} GB stored; dnu {cnu:.9e} vs {dnu:.9e}, drho {crho:.9e} vs {drho:.9e}")
+    assert float((cuT - uT).abs().max()) <= 1e-9 * float(uT.abs().max())
+    assert abs(cnu - dnu) <= 1e-8 * abs(dnu) and abs(crho - drho) <= 1e-8 * abs(drho)
+    assert float((cdu0 - du0).norm()) <= 1e-8 * float(du0.norm())
+    assert peak_ckpt < 0.3 * peak_stored
