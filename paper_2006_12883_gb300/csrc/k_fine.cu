@@ -460,6 +460,19 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ U, const T*
   if (i < n) U[i] += alpha * (double)e[i];
 }
 
+// Exact float -> double by bit manipulation: the conversion instruction runs
+// on the FP64 pipe, 1/64 of the FP32 rate on this GPU, and with the FP64 add
+// it made the update bound by that pipe rather than by memory.  Normal
+// floats and zeros convert exactly, infinities and NaNs stay so; subnormal
+// floats (|e| < 2^-126) become a zero of the same sign.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+  const unsigned hi = (ex == 0u) ? sign : sign | ((ex == 0xffu ? 0x7ffu : ex + 896u) << 20) | (man >> 3);
+  const unsigned lo = (ex == 0u) ? 0u : (man << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Four values per thread; U and e 16-byte aligned (checked by the launcher).
 template <typename T>
 __global__ void __launch_bounds__(256) k_update4(double* __restrict__ U, const T* __restrict__ e, long long n,
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(256) k_update4(double* __restrict__ U, const T
     double e0, e1, e2, e3;
     if constexpr (sizeof(T) == 4) {
       const float4 v = *reinterpret_cast<const float4*>(e + i);
-      e0 = v.x; e1 = v.y; e2 = v.z; e3 = v.w;
+      e0 = f2d_bits(v.x); e1 = f2d_bits(v.y); e2 = f2d_bits(v.z); e3 = f2d_bits(v.w);
     } else {
       const double2 v0 = *reinterpret_cast<const double2*>(e + i);
       const double2 v1 = *reinterpret_cast<const double2*>(e + i + 2);

@@ -91,11 +91,12 @@ __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// 2D, M = 3 fits 64 registers (the equivalent of 4 blocks of 256 per SM), as does one plane
-// (the SDC node solves); larger instances keep their registers rather than
-// spill.
-template <int D, int M>
-constexpr int inner4_min_blocks() { return ((D == 2 && M == 3) || M == 1) ? 4 : 1; }
+// 2D, M = 3 fits 64 registers (the equivalent of 4 blocks of 256 per SM), as
+// do one plane (the SDC node solves) and the 2D, M = 5 Jacobi sweep (more
+// warps in flight for a latency-bound stream); the other instances keep their
+// registers rather than spill.
+template <int D, int M, int MODE>
+constexpr int inner4_min_blocks() { return ((D == 2 && (M == 3 || (M == 5 && MODE == 1))) || M == 1) ? 4 : 1; }
 
 // The level residual keeps M planes of e and their stencil sums live: at most
 // 128 registers (2 blocks per SM) except 2D, M = 3 (64, 4 blocks).
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
 // fused back-transform into e.
 
 template <int D, int M, int MODE>
-__global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M>()) k_inner4(InnerParams<float> p, FastDiv fG) {
+__global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_inner4(InnerParams<float> p, FastDiv fG) {
   grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.Nt * (unsigned)(p.g.Ns >> 2)) return;
