@@ -91,20 +91,22 @@ __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// 2D, M = 3 fits 64 registers (the equivalent of 4 blocks of 256 per SM), as
-// do one plane (the SDC node solves) and the 2D, M = 5 Jacobi sweep (more
-// warps in flight for a latency-bound stream); the other instances keep their
-// registers rather than spill.
+// One plane (the SDC node solves) fits 64 registers (8 blocks of 128 per SM);
+// with every plane's z and y loaded up front, 2D instances take up to 128
+// (4 blocks of 128: the loads in flight, not the warps, hide the latency);
+// 3D instances keep their registers rather than spill.
 template <int D, int M, int MODE>
-constexpr int inner4_min_blocks() { return ((D == 2 && (M == 3 || (M == 5 && MODE == 1))) || M == 1) ? 4 : 1; }
+constexpr int inner4_min_blocks() { return M == 1 ? 4 : (D == 2 ? 2 : 1); }
 
-// The level residual keeps M planes of e and their stencil sums live: at most
-// 128 registers (2 blocks per SM) except 2D, M = 3 (64, 4 blocks).
-template <int D, int M>
-constexpr int lin4_min_blocks() { return (D == 2 && M == 3) ? 4 : 2; }
+// With e (E = true) the level residual keeps M planes of e and r (all loaded
+// up front) and their stencil sums live: at most 128 registers (2 blocks of
+// 256 per SM).  Without e (the zero start of a pre-smoothing step) only r is
+// read: M = 3 fits 64 registers (4 blocks), M = 5 85 (3 blocks).
+template <int D, int M, bool E>
+constexpr int lin4_min_blocks() { return E ? 2 : (M == 3 ? 4 : 3); }
 
-template <int D, int M>
-__global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(LinParams<float> p, FastDiv fG) {
+template <int D, int M, bool E>
+__global__ void __launch_bounds__(256, lin4_min_blocks<D, M, E>()) k_lin_residual4(LinParams<float> p, FastDiv fG) {
   grid_dep_wait();
   const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (unsigned)p.nchunks * (unsigned)(p.g.Ns >> 2)) return;
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
   const long long Ns = p.g.Ns;
   const int n0 = c * p.chunk;
   const int n1 = min(n0 + p.chunk, p.Nt);
-  const bool hase = (p.e != nullptr);
+  constexpr bool hase = E;  // the launcher picks E = (p.e != nullptr)
   float carry[4] = {0.f, 0.f, 0.f, 0.f};
   if (hase) {
     if (!p.transpose) {
@@ -138,10 +140,16 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
     if (hase) {
       float ev[M][4], Fe[M][4];
       float sum[4] = {0.f, 0.f, 0.f, 0.f};
+      // every plane of e and r of this slab in flight before any arithmetic
+      float4 r4v[M];
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        to4(ld4(p.e + base + (long long)b * Ns), ev[b]);
+        r4v[b] = p.r ? ld4(p.r + base + (long long)b * Ns) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
       for (int b = 0; b < M; ++b) {
         const float* pl = p.e + base + (long long)b * Ns - s0;
-        to4(ld4(pl + s0), ev[b]);
         float cr[4] = {cb[0], cb[1], cb[2], cb[3]};
         if (p.cnode) to4(ld4(p.cnode + base + (long long)b * Ns), cr);
 #pragma unroll
@@ -154,8 +162,7 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         float r4[4];
-        if (p.r) to4(ld4(p.r + base + (long long)a * Ns), r4);
-        else r4[0] = r4[1] = r4[2] = r4[3] = 0.f;
+        to4(r4v[a], r4);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float acc = r4[q] - ev[a][q];
@@ -210,8 +217,9 @@ __global__ void __launch_bounds__(256, lin4_min_blocks<D, M>()) k_lin_residual4(
 }
 
 // Shifted-system operator at 4 points of all planes: out[pl][q] = y - A z
-// (mode 0: residual into zout) or a Jacobi sweep (mode 1) with optional
-// fused back-transform into e.
+// (mode 0: residual into zout), a Jacobi sweep into zout (mode 1), or a
+// Jacobi sweep fused with the back-transform and the damped update of e
+// (mode 2, p.fuse_bt).
 
 template <int D, int M, int MODE>
 __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_inner4(InnerParams<float> p, FastDiv fG) {
@@ -225,6 +233,21 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
   const long long base = (long long)n * M * Ns + s0;
   float cb[4] = {0.f, 0.f, 0.f, 0.f};
   if (p.cbar) to4(ld4(p.cbar + (long long)n * Ns + s0), cb);
+  // every plane's z and y streamed in before any arithmetic: all of the
+  // thread's DRAM loads in flight at once (the neighbour rows and columns
+  // that follow mostly hit L2)
+  float4 zv[M], yv[M];
+#pragma unroll
+  for (int pl = 0; pl < M; ++pl) {
+    zv[pl] = ld4(p.z + base + (long long)pl * Ns);
+    yv[pl] = ld4(p.y + base + (long long)pl * Ns);
+  }
+  // the sweep fused with the damped update of e (MODE 2) reads e too
+  constexpr int ME = MODE == 2 ? M : 1;
+  float4 ev0[ME];
+  const bool pre_e = MODE == 2 && !p.e_zero;
+#pragma unroll
+  for (int a = 0; a < ME; ++a) ev0[a] = pre_e ? ld4(p.e + base + (long long)a * Ns) : make_float4(0.f, 0.f, 0.f, 0.f);
   float out[M][4];
 #pragma unroll
   for (int pl = 0; pl < M; ++pl) {
@@ -233,8 +256,8 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
       const float sr = p.sh.sr[pl], si = p.sh.si[pl];
       const float* zrp = p.z + base - s0 + (long long)pl * Ns;
       float zr[4], Lr[4], yr[4];
-      to4(ld4(zrp + s0), zr);
-      to4(ld4(p.y + base + (long long)pl * Ns), yr);
+      to4(zv[pl], zr);
+      to4(yv[pl], yr);
 #pragma unroll
       for (int q = 0; q < 4; ++q) Lr[q] = cb[q] * zr[q];
       lap4<D>(zrp, s0, nb, zr, p.sc, Lr);
@@ -247,8 +270,8 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
       } else if (pl + 1 < M) {
         const float* zip = zrp + Ns;
         float zi[4], Li[4], yi[4];
-        to4(ld4(zip + s0), zi);
-        to4(ld4(p.y + base + (long long)(pl + 1) * Ns), yi);
+        to4(zv[pl + 1 < M ? pl + 1 : pl], zi);
+        to4(yv[pl + 1 < M ? pl + 1 : pl], yi);
 #pragma unroll
         for (int q = 0; q < 4; ++q) Li[q] = cb[q] * zi[q];
         lap4<D>(zip, s0, nb, zi, p.sc, Li);
@@ -270,14 +293,14 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
       }
     }
   }
-  if (MODE == 0 || !p.fuse_bt) {
+  if (MODE != 2) {
 #pragma unroll
     for (int pl = 0; pl < M; ++pl) st4(p.zout + base + (long long)pl * Ns, out[pl]);
   } else {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      float ev[4] = {0.f, 0.f, 0.f, 0.f};
-      if (!p.e_zero) to4(ld4(p.e + base + (long long)a * Ns), ev);
+      float ev[4];
+      to4(ev0[a < ME ? a : 0], ev);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float acc = 0.f;
@@ -434,10 +457,16 @@ bool launch_lin_residual4(int D, const LinParams<float>& p, cudaStream_t st) {
   if (!vec4_ok(p.g, D, p.M)) return false;
   const FastDiv fG((unsigned)(p.g.Ns >> 2));
   const unsigned nb = nblk4((p.g.Ns >> 2) * p.nchunks);
-  if (D == 2 && p.M == 3) st_launch(k_lin_residual4<2, 3>, nb, 256, 0, st, p, fG);
-  else if (D == 2 && p.M == 5) st_launch(k_lin_residual4<2, 5>, nb, 256, 0, st, p, fG);
-  else if (D == 3 && p.M == 3) st_launch(k_lin_residual4<3, 3>, nb, 256, 0, st, p, fG);
-  else st_launch(k_lin_residual4<3, 5>, nb, 256, 0, st, p, fG);
+#define L4(DD, MM)                                                                      \
+  do {                                                                                  \
+    if (p.e) st_launch(k_lin_residual4<DD, MM, true>, nb, 256, 0, st, p, fG);           \
+    else st_launch(k_lin_residual4<DD, MM, false>, nb, 256, 0, st, p, fG);              \
+  } while (0)
+  if (D == 2 && p.M == 3) L4(2, 3);
+  else if (D == 2 && p.M == 5) L4(2, 5);
+  else if (D == 3 && p.M == 3) L4(3, 3);
+  else L4(3, 5);
+#undef L4
   return true;
 }
 
@@ -456,6 +485,7 @@ bool launch_inner4(int D, int mode, const InnerParams<float>& p, cudaStream_t st
 #define K4(DD, MM)                                                         \
   do {                                                                     \
     if (mode == 0) st_launch(k_inner4<DD, MM, 0>, nb, 128, 0, st, p, fG);         \
+    else if (p.fuse_bt) st_launch(k_inner4<DD, MM, 2>, nb, 128, 0, st, p, fG);    \
     else st_launch(k_inner4<DD, MM, 1>, nb, 128, 0, st, p, fG);                   \
   } while (0)
   if (D == 2 && p.P == 3) K4(2, 3);

@@ -1,8 +1,10 @@
 // TMA-staged level kernels on 2D periodic grids (x size a multiple of 64, y
-// size a multiple of 16, M = 3 or 5, FP32):
-//  * k_jacobi_tma: the Jacobi sweep of the Q-diagonalised slab systems that
-//    also updates e (the last of a slab solve), the same arithmetic as
-//    k_inner4<2, M, 1> in k_level4.cu, with the operands of a 64 x 16 tile
+// size a multiple of 16, M = 3, FP32; at M = 5 two stages of a tile take a
+// block's shared memory, and the direct float4 kernels that issue all of a
+// thread's loads up front are faster):
+//  * k_jacobi_tma (M = 3): the Jacobi sweep of the Q-diagonalised slab
+//    systems that also updates e (the last of a slab solve), the same
+//    arithmetic as k_inner4<2, 3, 2> in k_level4.cu, with the operands of a 64 x 16 tile
 //    (z, y, e of every plane and cbar) brought into shared memory by
 //    cp.async.bulk.tensor copies and the one-point halo of z by plain loads;
 //  * k_linres_tma: the level residual with e (and the eigenbasis transform),
@@ -488,8 +490,8 @@ __global__ void __launch_bounds__(256, 2) k_linres_tma(const __grid_constant__ L
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-int g_resident[2] = {0, 0};  // resident blocks on the device (M = 3, M = 5)
-int g_resident_lin[2] = {0, 0};
+int g_resident[1] = {0};  // resident blocks of k_jacobi_tma<3> on the device
+int g_resident_lin[1] = {0};  // resident blocks of k_linres_tma<3> on the device
 std::mutex g_prepare_mu;
 
 bool encode(CUtensorMap* map, const float* base, int n0, long long rows) {
@@ -506,7 +508,7 @@ bool encode(CUtensorMap* map, const float* base, int n0, long long rows) {
 }  // namespace
 
 bool jacobi_tma_ok(int D, const InnerParams<float>& p) {
-  return D == 2 && (p.P == 3 || p.P == 5) && p.g.bc == BC_PER && p.g.n0 % kTW == 0 && p.g.n1 % kTH == 0 &&
+  return D == 2 && p.P == 3 && p.g.bc == BC_PER && p.g.n0 % kTW == 0 && p.g.n1 % kTH == 0 &&
          aligned16(p.z) && aligned16(p.y) && (!p.fuse_bt || aligned16(p.e)) && (p.fuse_bt || aligned16(p.zout)) &&
          (!p.cbar || aligned16(p.cbar));
 }
@@ -514,43 +516,45 @@ bool jacobi_tma_ok(int D, const InnerParams<float>& p) {
 bool launch_jacobi_tma(int D, const InnerParams<float>& p, cudaStream_t st) {
   if (!jacobi_tma_ok(D, p)) return false;
   // measured: staging pays for the sweep that also reads and updates e (ten
-  // tiles per stage); with seven the direct float4 loads are as fast
-  if (!(p.fuse_bt && !p.e_zero)) return false;
+  // tiles per stage); with seven the direct float4 loads are as fast.  At
+  // M = 5 a block's two stages take 130 KB, one block per SM, and the direct
+  // kernel with every load issued up front is faster (14.8 against 17.2 ms
+  // on 1024^2 x 1024 slabs), so only M = 3 stages its tiles.
+  if (!(p.fuse_bt && !p.e_zero) || p.P != 3) return false;
   TmaMaps m;
   memset(&m, 0, sizeof(m));
   const long long rows = (long long)p.Nt * p.P * p.g.n1;
   if (!encode(&m.z, p.z, p.g.n0, rows) || !encode(&m.y, p.y, p.g.n0, rows)) return false;
   if (p.fuse_bt && !p.e_zero && !encode(&m.e, p.e, p.g.n0, rows)) return false;
   if (p.cbar && !encode(&m.cb, p.cbar, p.g.n0, (long long)p.Nt * p.g.n1)) return false;
-  if (g_resident[p.P == 3 ? 0 : 1] < 1) return false;  // tma_prepare not run or no room
+  if (g_resident[0] < 1) return false;  // tma_prepare not run or no room
   const long long ntiles = (long long)(p.g.n0 / kTW) * (p.g.n1 / kTH) * p.Nt;
   // the two-stage pipeline pays only when every block walks enough tiles
-  if (ntiles < (long long)kMinTilesPerBlock * g_resident[p.P == 3 ? 0 : 1]) return false;
+  if (ntiles < (long long)kMinTilesPerBlock * g_resident[0]) return false;
   // persistent grid: the resident blocks of every SM, no more than tiles
-  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident[p.P == 3 ? 0 : 1]);
-  if (p.P == 3) st_launch(k_jacobi_tma<3>, grid, 256, sizeof(TileSmem<3>), st, m, p);
-  else st_launch(k_jacobi_tma<5>, grid, 256, sizeof(TileSmem<5>), st, m, p);
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident[0]);
+  st_launch(k_jacobi_tma<3>, grid, 256, sizeof(TileSmem<3>), st, m, p);
   return true;
 }
 
 bool launch_linres_tma(int D, const LinParams<float>& p, cudaStream_t st) {
-  // forward operator with e (the stencil variants), node-averaged cbar only
-  if (!(D == 2 && (p.M == 3 || p.M == 5) && p.g.bc == BC_PER && p.g.n0 % kTW == 0 && p.g.n1 % kTH == 0 &&
+  // forward operator with e (the stencil variants), node-averaged cbar only;
+  // M = 3 only: at M = 5 the direct float4 kernel with every load of a slab
+  // issued up front is faster (11.2 against 12.2 ms on 1024^2 x 1024 slabs)
+  if (!(D == 2 && p.M == 3 && p.g.bc == BC_PER && p.g.n0 % kTW == 0 && p.g.n1 % kTH == 0 &&
         p.e && !p.transpose && !p.cnode && aligned16(p.e) && aligned16(p.r) && aligned16(p.out) &&
         (!p.zout || aligned16(p.zout)) && (!p.cbar || aligned16(p.cbar))))
     return false;
-  const int slot = p.M == 3 ? 0 : 1;
-  if (g_resident_lin[slot] < 1) return false;
+  if (g_resident_lin[0] < 1) return false;
   const long long ntiles = (long long)(p.g.n0 / kTW) * (p.g.n1 / kTH) * p.Nt;
-  if (ntiles < (long long)kMinTilesPerBlock * g_resident_lin[slot]) return false;
+  if (ntiles < (long long)kMinTilesPerBlock * g_resident_lin[0]) return false;
   LinMaps m;
   memset(&m, 0, sizeof(m));
   const long long rows = (long long)p.Nt * p.M * p.g.n1;
   if (!encode(&m.e, p.e, p.g.n0, rows) || !encode(&m.r, p.r, p.g.n0, rows)) return false;
   if (p.cbar && !encode(&m.cb, p.cbar, p.g.n0, (long long)p.Nt * p.g.n1)) return false;
-  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident_lin[slot]);
-  if (p.M == 3) st_launch(k_linres_tma<3>, grid, 256, sizeof(LinSmem<3>), st, m, p);
-  else st_launch(k_linres_tma<5>, grid, 256, sizeof(LinSmem<5>), st, m, p);
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)g_resident_lin[0]);
+  st_launch(k_linres_tma<3>, grid, 256, sizeof(LinSmem<3>), st, m, p);
   return true;
 }
 
@@ -575,9 +579,7 @@ void tma_prepare() {
     return per_sm * sms;
   };
   g_resident[0] = setup(k_jacobi_tma<3>, sizeof(TileSmem<3>));
-  g_resident[1] = setup(k_jacobi_tma<5>, sizeof(TileSmem<5>));
   g_resident_lin[0] = setup(k_linres_tma<3>, sizeof(LinSmem<3>));
-  g_resident_lin[1] = setup(k_linres_tma<5>, sizeof(LinSmem<5>));
   cudaGetLastError();  // a failed query leaves the TMA path off, not an error
 }
 

@@ -12,6 +12,7 @@ namespace st {
 // which hides most of the launch latency of the many small kernels of a cycle;
 // set per call from the handle's options.
 extern thread_local int tl_pdl;
+constexpr unsigned long long kPdlMaxBlocks = 152ull * 32;  // about 4 waves of 8 blocks per SM
 
 // Kernel launch used by every launcher: the kernel's first instruction is
 // grid_dep_wait(), so ordering against the previous launch on `st` holds with or
@@ -28,7 +29,12 @@ inline void st_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = tl_pdl ? 1 : 0;
+  // only launches of a few waves: their blocks' early residency hides the
+  // launch latency, which is a large part of a short kernel; a grid of many
+  // waves gains nothing from it, and its waiting blocks held SM slots while a
+  // long predecessor drained (a V-cycle at 5.4e9 dofs ran 10 % slower with it)
+  const unsigned long long nblk = (unsigned long long)grid.x * grid.y * grid.z;
+  cfg.numAttrs = (tl_pdl && nblk <= kPdlMaxBlocks) ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 

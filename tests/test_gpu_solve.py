@@ -39,6 +39,8 @@ def test_solve_matches_oracle(case, prec):
     assert info["status"] == 0 and info["rel_residual"] <= tol
     ref = _oracle_solution(case)
     err = _rel(U.cpu().numpy().reshape(ref.shape), ref)
+    print(f"\n[oracle] {case.name} {prec}: rel 2-norm error {err:.3e}, rel residual {info['rel_residual']:.3e}, "
+          f"cycles {info['cycles']}")
     # all-FP64 path within 1e-10, FP32 cycle + FP64 refinement within 1e-8
     assert err <= (1e-10 if prec == "fp64" else 1e-8), err
     h = info["history"]
