@@ -167,7 +167,12 @@ class ClockSampler:
 # proportion to the dofs: every array is streamed once); scaled to a full
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_inner4<2, 5, 2> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.65 MB read + 477.37 MB written per launch
+    "k_inner4<2, 5, 2>": {"file": "k_level4.cu",
+                          "sha256": "e305c72967d1abed7edb159f2ea60dbf51c6d110cc9cbf12186f7e815bf2924b",
+                          "dram_bytes_per_dof": 2088020224 / 125829120},
+}
 
 
 def ncu_traffic(kernel, dofs):
@@ -550,13 +555,16 @@ def run_ours(args):
     free_device()
 
     hbm, src = measured_peaks()
-    # dominant kernel: the Jacobi sweep of the shifted slab systems that
-    # updates z (k_inner4<2, M, 1>, every sweep but a slab solve's last),
-    # timed here at level 0 where it moves the most bytes; HBM bound
-    k = kernels["slab_jacobi_plain"]
-    kname = f"k_inner4<2, {w['M']}, 1>"
-    roofline = {"bound": "hbm", "kernel": kname + ": level-0 Jacobi sweep of the shifted slab systems "
-                                                  "(z, y, cbar in, z out; direct float4 loads)",
+    # dominant kernel (largest share of the step in the ncu launch list): the
+    # last Jacobi sweep of a slab solve, fused with the back-transform and
+    # the damped block-Jacobi update of e, timed here at level 0 where it
+    # moves the most bytes; HBM bound.  TMA-staged on 2D grids at M = 3.
+    k = kernels["slab_jacobi"]
+    d = len(w["grid"])
+    kname = "k_jacobi_tma<3>" if (d == 2 and w["M"] == 3 and w["bc"] == "periodic") else \
+        f"k_inner4<{d}, {w['M']}, 2>"
+    roofline = {"bound": "hbm", "kernel": kname + ": level-0 Jacobi sweep of the shifted slab systems fused with "
+                                                  "the back-transform and update of e (z, y, e, cbar in, e out)",
                 "achieved": k.get("GBps"), "peak": hbm, "unit": "GB/s",
                 "frac": (k["GBps"] / hbm) if k.get("GBps") else None,
                 "traffic": ncu_traffic(kname, D),
