@@ -80,7 +80,13 @@ STMG2D = Case("stmg2d", (32, 32), P_, 1e-2, 8, 3, reaction=L_, rho=1.0, u0_kind=
               extra=dict(coarsening=3))
 STMG1D = Case("stmg1d_heat", (65,), N_, 0.01, 16, 3, u0_kind="cosine", extra=dict(coarsening=3))
 
-RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5]
+# square periodic grids in whole 64 x 16 tiles (h_x = h_y: the tiled residual adds
+# the two exact second differences before its product with nu/h^2)
+TILED_SQ3 = Case("tiled_square_m3", (64, 64), P_, 1e-2, 5, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=21)
+TILED_SQ5 = Case("tiled_square_m5", (64, 64), P_, 2e-2, 4, 5, reaction=C_, rho=1.5, u0_kind="noise", seed=22)
+
+RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5,
+                  TILED_SQ3, TILED_SQ5]
 SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, STMG2D,
                STMG1D]
 

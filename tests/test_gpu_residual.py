@@ -50,7 +50,8 @@ def test_residual_parity(case, prec):
 
 def test_residual_norm_deterministic():
     from paper_2006_12883_gb300 import stlib
-    case = RESIDUAL_CASES[-2]
+    from tests.gpu_cases import PER3D_M5
+    case = PER3D_M5
     p = case.problem()
     U = stgen.random_field((p.Nt, p.M, p.Ns), 9)
     S = case.solver(precision=stlib.FP32_REFINE)
@@ -86,7 +87,8 @@ def _tile_scales(p, U, tw=64, th=16):
     return out.ravel()
 
 
-def test_tiled_residual_dynamic_range_and_nonfinite():
+@pytest.mark.parametrize("which", ["ragged", "square"])
+def test_tiled_residual_dynamic_range_and_nonfinite(which):
     """The residual for the FP32 cycle on 2D periodic grids in whole 64 x 16
     tiles holds every value as a high part on a grid set by its tile's
     largest exponent plus a float low part.  With tiles whose magnitudes
@@ -94,7 +96,10 @@ def test_tiled_residual_dynamic_range_and_nonfinite():
     its own terms; a non-finite value gives a non-finite norm and leaves the
     tiles away from it exact as before."""
     from paper_2006_12883_gb300 import stlib
-    from tests.gpu_cases import RAGGED
+    from tests.gpu_cases import RAGGED, Case
+    if which == "square":
+        RAGGED = Case("square_dyn", (128, 128), space.PERIODIC, 1e-2, 6, 3, reaction=space.LOGISTIC, rho=1.0,
+                      u0_kind="noise", seed=4)
     p = RAGGED.problem()
     ny, nx = p.shape
     U = stgen.random_field((p.Nt, p.M, p.Ns), 11, 0.4) + 0.5
