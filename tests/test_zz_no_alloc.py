@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import stgen
+from oracle import system
 from tests.gpu_cases import LOG2D, residual_scale
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +46,10 @@ def test_noalloc_matches_handle_residual_twice():
         tol = 1e-13 * residual_scale(p, U.cpu().numpy())
         assert np.abs((R - R_ref).cpu().numpy()).max() <= tol
         assert abs(n - n_ref) <= 1e-12 * n_ref
+        # and directly against the oracle's G(U) (Eq. 2.3 with the slab coupling)
+        G = system.residual(p, U.cpu().numpy(), case.u0())
+        assert np.abs(R.cpu().numpy().reshape(G.shape) - G).max() <= tol
+        assert abs(n - np.linalg.norm(G)) <= 1e-12 * np.linalg.norm(G) + 1e-13 * residual_scale(p, U.cpu().numpy())
     S.close()
 
 
@@ -88,6 +93,9 @@ def test_noalloc_long_slab_runs_and_optional_outputs():
     n1 = _call_noalloc(stlib, case, u0_dev, U, R)
     assert np.abs((R - R_ref).cpu().numpy()).max() <= tol
     assert abs(n1 - n_ref) <= 1e-12 * n_ref
+    G = system.residual(p, U.cpu().numpy(), case.u0())
+    assert np.abs(R.cpu().numpy().reshape(G.shape) - G).max() <= tol
+    del G
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     n2 = _call_noalloc(stlib, case, u0_dev, U, None)  # norm only
