@@ -82,7 +82,8 @@ def make_solver(stlib, w, u0, **opts):
 HBM_DATASHEET_GBS = 7900.0  # GB300 HBM3e, vendor figure (context beside the measured copy bandwidth)
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
-                 ("prolong_add", 7), ("slab_jacobi_plain", 8), ("update", 9), ("vcycle_graph", 4))
+                 ("prolong_add", 7), ("slab_jacobi_plain", 8), ("update", 9), ("two_sweeps", 10),
+                 ("vcycle_graph", 4))
 
 
 def reduce_max(x, dist, device):

@@ -165,6 +165,11 @@ typedef struct {
   int recompute_slabs;  /* slab recomputation checkpointing (st_ckpt_*): slabs
                            per block, a divisor of Nt; 0 (default) = off.
                            st_create ignores it. */
+  int fuse_sweeps;      /* 1 (default): the last two Jacobi sweeps of a slab
+                           solve on 2D periodic grids in whole 64 x 16 tiles,
+                           M = 3 or 5, FP32, run as one kernel with the middle
+                           iterate in shared memory (same arithmetic); 0: two
+                           launches */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -435,9 +440,12 @@ enum {
   ST_KERNEL_PROLONG = 7,          /* linear interpolation + correction, inner grid 1 -> 0 */
   ST_KERNEL_JACOBI_PLAIN = 8,     /* level-0 Jacobi sweep of the shifted slab systems that only
                                      updates z (the sweeps before the cycle's last) */
-  ST_KERNEL_UPDATE = 9            /* the defect-correction update U += alpha e in FP64, run with
+  ST_KERNEL_UPDATE = 9,           /* the defect-correction update U += alpha e in FP64, run with
                                      alpha = 0: the update's traffic (U and e read, U written)
                                      with U's values left unchanged */
+  ST_KERNEL_SWEEP2 = 10           /* the last two level-0 Jacobi sweeps of a slab solve as one
+                                     kernel, the second fused with the back-transform and update
+                                     of e (ST_ERR_UNSUPPORTED where that kernel does not apply) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream

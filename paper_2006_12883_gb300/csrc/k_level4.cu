@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
       if (kd == SH_REAL) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float r = yr[q] - (zr[q] - sr * Lr[q]);
-          out[pl][q] = (MODE == 0) ? r : zr[q] + jdiv(p.omega * r, 1.f - sr * (p.sc.k2 + cb[q]));
+          if (MODE == 0) out[pl][q] = yr[q] - (zr[q] - sr * Lr[q]);
+          else out[pl][q] = jac_real(yr[q], zr[q], Lr[q], sr, p.omega, p.sc.k2 + cb[q]);
         }
       } else if (pl + 1 < M) {
         const float* zip = zrp + Ns;
@@ -277,17 +277,12 @@ __global__ void __launch_bounds__(128, 2 * inner4_min_blocks<D, M, MODE>()) k_in
         lap4<D>(zip, s0, nb, zi, p.sc, Li);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float rr = yr[q] - (zr[q] - sr * Lr[q] + si * Li[q]);
-          const float ri = yi[q] - (zi[q] - sr * Li[q] - si * Lr[q]);
           if (MODE == 0) {
-            out[pl][q] = rr;
-            out[pl + 1 < M ? pl + 1 : pl][q] = ri;
+            out[pl][q] = yr[q] - (zr[q] - sr * Lr[q] + si * Li[q]);
+            out[pl + 1 < M ? pl + 1 : pl][q] = yi[q] - (zi[q] - sr * Li[q] - si * Lr[q]);
           } else {
-            const float dprime = p.sc.k2 + cb[q];
-            const float dr = 1.f - sr * dprime, di = -si * dprime;
-            const float inv = jdiv(p.omega, dr * dr + di * di);
-            out[pl][q] = zr[q] + (rr * dr + ri * di) * inv;
-            out[pl + 1 < M ? pl + 1 : pl][q] = zi[q] + (ri * dr - rr * di) * inv;
+            jac_cplx(yr[q], yi[q], zr[q], zi[q], Lr[q], Li[q], sr, si, p.omega, p.sc.k2 + cb[q], out[pl][q],
+                     out[pl + 1 < M ? pl + 1 : pl][q]);
           }
         }
       }

@@ -1,0 +1,274 @@
+// The last two Jacobi sweeps of a depth-capped slab solve in one kernel
+// (2D periodic grids in whole 64 x 16 tiles, M = 3 or 5, FP32): the sweep
+// z -> z' and the sweep z' -> z'' fused with the back-transform and the
+// damped block-Jacobi update of e, e = (e_zero ? 0 : e) + omega_bt B z''.
+// The separate kernels stream z, y and cbar twice and z' out and back in;
+// here a block brings z with a two-point halo, y and cbar with a one-point
+// halo into shared memory (cp.async copies, all of a thread's copies in
+// flight at once), computes z' on the tile and its one-point ring, keeps it
+// in shared memory, and computes the second sweep on the tile: 16.8 instead
+// of 29.6 bytes per dof at M = 5.  The arithmetic is that of k_inner4's
+// sweep (k_level4.cu), term for term, so the result equals the two-launch
+// sequence.
+#include <mutex>
+
+#include "st_kernels.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int kW = 64, kH = 16;   // tile: x points, rows
+constexpr int kS = 72;            // shared row stride: columns -4..67, the tile's at 4..67
+constexpr int kZR = kH + 4;       // z rows -2..17
+constexpr int kYR = kH + 2;       // y, cbar, z' rows -1..16
+
+template <int M>
+struct Sweep2Smem {
+  float z[M][kZR][kS];
+  float y[M][kYR][kS];
+  float z1[M][kYR][kS];
+  float cb[kYR][kS];
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+
+// One damped Jacobi update at NQ points of one real plane (kd == SH_REAL:
+// the r-arrays) or of one complex pair (kd == SH_RE: planes r and i), from
+// the centre values z, the right-hand sides y, the sums of the two x and the
+// two y neighbours and cbar: k_inner4's arithmetic, in its order, with the
+// update itself in jac_real / jac_cplx as there.
+template <int NQ>
+__device__ __forceinline__ void jacobi_pair(const InnerParams<float>& p, int kd, float sr, float si,
+                                            const float (&zr)[NQ], const float (&yr)[NQ], const float (&sxr)[NQ],
+                                            const float (&syr)[NQ], const float (&zi)[NQ], const float (&yi)[NQ],
+                                            const float (&sxi)[NQ], const float (&syi)[NQ], const float (&cb)[NQ],
+                                            float (&outr)[NQ], float (&outi)[NQ]) {
+  float Lr[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    Lr[q] = cb[q] * zr[q];
+    Lr[q] = fmaf(p.sc.k2, zr[q], Lr[q]);
+    Lr[q] = fmaf(p.sc.cx, sxr[q], Lr[q]);
+    Lr[q] = fmaf(p.sc.cy, syr[q], Lr[q]);
+  }
+  if (kd == SH_REAL) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) outr[q] = jac_real(yr[q], zr[q], Lr[q], sr, p.omega, p.sc.k2 + cb[q]);
+    return;
+  }
+  float Li[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    Li[q] = cb[q] * zi[q];
+    Li[q] = fmaf(p.sc.k2, zi[q], Li[q]);
+    Li[q] = fmaf(p.sc.cx, sxi[q], Li[q]);
+    Li[q] = fmaf(p.sc.cy, syi[q], Li[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    jac_cplx(yr[q], yi[q], zr[q], zi[q], Lr[q], Li[q], sr, si, p.omega, p.sc.k2 + cb[q], outr[q], outi[q]);
+}
+
+__device__ __forceinline__ void ld4s(const float* s, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(s);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+// The operands of one plane at a group of 4 points (shared column c0, a
+// multiple of 4): centre, y, x-neighbour sums, y-neighbour sums; zc is the
+// centre row of the plane's z (or z') in shared memory, zu / zd the rows
+// above and below, yrow the plane's y row.
+__device__ __forceinline__ void group_operands(const float* zc, const float* zu, const float* zd,
+                                               const float* yrow, int c0, float (&z)[4], float (&y)[4],
+                                               float (&sx)[4], float (&sy)[4]) {
+  ld4s(zc + c0, z);
+  ld4s(yrow + c0, y);
+  float u[4], d[4];
+  ld4s(zu + c0, u);
+  ld4s(zd + c0, d);
+  const float v[6] = {zc[c0 - 1], z[0], z[1], z[2], z[3], zc[c0 + 4]};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    sx[q] = v[q] + v[q + 2];
+    sy[q] = u[q] + d[q];
+  }
+}
+
+constexpr int kThreads = kYR * 16;  // one thread per group of 4 points of the first sweep's region
+
+template <int M>
+__global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
+  grid_dep_wait();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Sweep2Smem<M>& S = *reinterpret_cast<Sweep2Smem<M>*>(smraw);
+  const int tid = threadIdx.x;
+  const int nx = p.g.n0, ny = p.g.n1;
+  const long long Ns = p.g.Ns;
+  const int ntx = nx / kW;
+  const int per_slab = ntx * (ny / kH);
+  const int tile = (int)(blockIdx.x % (unsigned)per_slab), n = (int)(blockIdx.x / (unsigned)per_slab);
+  const int j0 = (tile / ntx) * kH, i0 = (tile % ntx) * kW;
+  const long long base = (long long)n * M * Ns;
+  auto row = [&](int r) -> long long {  // periodic row r of the tile (r may be -2..17)
+    int j = j0 + r;
+    j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+    return (long long)j * nx;
+  };
+  auto col = [&](int c) -> int {  // periodic column c of the tile (c may be -2..65)
+    int i = i0 + c;
+    return i < 0 ? i + nx : (i >= nx ? i - nx : i);
+  };
+  const bool has_cb = p.cbar != nullptr;
+  // every copy of the block in flight at once
+  for (int q = tid; q < M * kZR * 16; q += kThreads) {  // z: the tile's columns of rows -2..17
+    const int pl = q / (kZR * 16), rem = q - pl * (kZR * 16), r = rem >> 4, g = rem & 15;
+    cp_async16(&S.z[pl][r][4 + 4 * g], p.z + base + pl * Ns + row(r - 2) + i0 + 4 * g);
+  }
+  for (int q = tid; q < M * kZR * 4; q += kThreads) {  // z: columns -2, -1, 64, 65 of rows -2..17
+    const int pl = q / (kZR * 4), rem = q - pl * (kZR * 4), r = rem >> 2, k = rem & 3;
+    const int c = k < 2 ? k - 2 : 62 + k;
+    cp_async4(&S.z[pl][r][4 + c], p.z + base + pl * Ns + row(r - 2) + col(c));
+  }
+  for (int q = tid; q < M * kYR * 16; q += kThreads) {  // y: the tile's columns of rows -1..16
+    const int pl = q / (kYR * 16), rem = q - pl * (kYR * 16), r = rem >> 4, g = rem & 15;
+    cp_async16(&S.y[pl][r][4 + 4 * g], p.y + base + pl * Ns + row(r - 1) + i0 + 4 * g);
+  }
+  for (int q = tid; q < M * kYR * 2; q += kThreads) {  // y: columns -1, 64 of rows -1..16
+    const int pl = q / (kYR * 2), rem = q - pl * (kYR * 2), r = rem >> 1, c = (rem & 1) ? kW : -1;
+    cp_async4(&S.y[pl][r][4 + c], p.y + base + pl * Ns + row(r - 1) + col(c));
+  }
+  if (has_cb) {
+    const long long cbase = (long long)n * Ns;
+    for (int q = tid; q < kYR * 16; q += kThreads) {
+      const int r = q >> 4, g = q & 15;
+      cp_async16(&S.cb[r][4 + 4 * g], p.cbar + cbase + row(r - 1) + i0 + 4 * g);
+    }
+    for (int q = tid; q < kYR * 2; q += kThreads) {
+      const int r = q >> 1, c = (q & 1) ? kW : -1;
+      cp_async4(&S.cb[r][4 + c], p.cbar + cbase + row(r - 1) + col(c));
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  // the e of the tile's thread (4 points of tile row ty, every plane), for the epilogue
+  const bool in_tile = tid < kH * 16;
+  const int ty = tid >> 4, tx = tid & 15;
+  const long long own = base + (in_tile ? row(ty) : 0) + i0 + 4 * tx;
+  float4 e0[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+    e0[a] = (p.e_zero || !in_tile) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : *reinterpret_cast<const float4*>(p.e + own + a * Ns);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+
+  // first sweep on rows -1..16: thread tid takes the group of 4 points at
+  // shared row r (tile row r - 1) and columns c0..c0+3
+  {
+    const int r = tid >> 4, c0 = 4 + 4 * (tid & 15);
+    float cb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (has_cb) ld4s(&S.cb[r][c0], cb);
+#pragma unroll
+    for (int pl = 0; pl < M; ++pl) {
+      const int kd = p.sh.kind[pl];
+      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
+      const int pi = pl + 1 < M ? pl + 1 : pl;
+      float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4], outr[4], outi[4];
+      group_operands(S.z[pl][r + 1], S.z[pl][r], S.z[pl][r + 2], S.y[pl][r], c0, zr, yr, sxr, syr);
+      if (kd == SH_RE) group_operands(S.z[pi][r + 1], S.z[pi][r], S.z[pi][r + 2], S.y[pi][r], c0, zi, yi, sxi, syi);
+      jacobi_pair<4>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, outr, outi);
+      *reinterpret_cast<float4*>(&S.z1[pl][r][c0]) = make_float4(outr[0], outr[1], outr[2], outr[3]);
+      if (kd == SH_RE) *reinterpret_cast<float4*>(&S.z1[pi][r][c0]) = make_float4(outi[0], outi[1], outi[2], outi[3]);
+    }
+  }
+  // first sweep at the ring's columns -1 and 64 of rows -1..16
+  if (tid < kYR * 2) {
+    const int r = tid >> 1, c = 4 + ((tid & 1) ? kW : -1);
+    float cb[1] = {has_cb ? S.cb[r][c] : 0.f};
+#pragma unroll
+    for (int pl = 0; pl < M; ++pl) {
+      const int kd = p.sh.kind[pl];
+      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
+      const int pi = pl + 1 < M ? pl + 1 : pl;
+      float zr[1] = {S.z[pl][r + 1][c]}, yr[1] = {S.y[pl][r][c]};
+      float sxr[1] = {S.z[pl][r + 1][c - 1] + S.z[pl][r + 1][c + 1]}, syr[1] = {S.z[pl][r][c] + S.z[pl][r + 2][c]};
+      float zi[1] = {S.z[pi][r + 1][c]}, yi[1] = {S.y[pi][r][c]};
+      float sxi[1] = {S.z[pi][r + 1][c - 1] + S.z[pi][r + 1][c + 1]}, syi[1] = {S.z[pi][r][c] + S.z[pi][r + 2][c]};
+      float outr[1], outi[1];
+      jacobi_pair<1>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, outr, outi);
+      S.z1[pl][r][c] = outr[0];
+      if (kd == SH_RE) S.z1[pi][r][c] = outi[0];
+    }
+  }
+  __syncthreads();
+
+  // second sweep on the tile, fused with the back-transform and the update of e
+  if (in_tile) {
+    const int r = ty + 1, c0 = 4 + 4 * tx;
+    float cb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (has_cb) ld4s(&S.cb[r][c0], cb);
+    float out[M][4];
+#pragma unroll
+    for (int pl = 0; pl < M; ++pl) {
+      const int kd = p.sh.kind[pl];
+      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
+      const int pi = pl + 1 < M ? pl + 1 : pl;
+      float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4];
+      group_operands(S.z1[pl][r], S.z1[pl][r - 1], S.z1[pl][r + 1], S.y[pl][r], c0, zr, yr, sxr, syr);
+      if (kd == SH_RE) group_operands(S.z1[pi][r], S.z1[pi][r - 1], S.z1[pi][r + 1], S.y[pi][r], c0, zi, yi, sxi, syi);
+      jacobi_pair<4>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, out[pl], out[pi]);
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      float ev[4] = {e0[a].x, e0[a].y, e0[a].z, e0[a].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) acc = fmaf(p.B[a][b], out[b][q], acc);
+        ev[q] = fmaf(p.omega_bt, acc, ev[q]);
+      }
+      *reinterpret_cast<float4*>(p.e + own + a * Ns) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+    }
+  }
+}
+
+int g_sweep2_ready = 0;  // 1 once the shared-memory opt-in is set
+
+}  // namespace
+
+void sweep2_prepare() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    bool ok = cudaFuncSetAttribute(k_sweep2<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(Sweep2Smem<3>)) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_sweep2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(Sweep2Smem<5>)) == cudaSuccess;
+    cudaGetLastError();  // without the opt-in the two sweeps stay separate launches
+    g_sweep2_ready = ok ? 1 : 0;
+  });
+}
+
+bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st) {
+  if (g_sweep2_ready != 1) return false;
+  if (!(D == 2 && (p.P == 3 || p.P == 5) && p.g.bc == BC_PER && p.g.n0 >= kW && p.g.n0 % kW == 0 &&
+        p.g.n1 >= kH && p.g.n1 % kH == 0 && p.fuse_bt && p.e && aligned16(p.z) && aligned16(p.y) &&
+        aligned16(p.e) && aligned16(p.cbar)))
+    return false;
+  const long long nb = (long long)(p.g.n0 / kW) * (p.g.n1 / kH) * p.Nt;
+  if (nb >= 0x7fffffffLL) return false;
+  if (p.P == 3) st_launch(k_sweep2<3>, (unsigned)nb, kThreads, sizeof(Sweep2Smem<3>), st, p);
+  else st_launch(k_sweep2<5>, (unsigned)nb, kThreads, sizeof(Sweep2Smem<5>), st, p);
+  return true;
+}
+
+}  // namespace st

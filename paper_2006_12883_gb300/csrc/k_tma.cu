@@ -220,8 +220,7 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
         if (kd == SH_REAL) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float rres = yr[q] - (zr[q] - sr * Lr[q]);
-            out[pl][q] = zr[q] + jdiv(p.omega * rres, 1.f - sr * (p.sc.k2 + cb[q]));
+            out[pl][q] = jac_real(yr[q], zr[q], Lr[q], sr, p.omega, p.sc.k2 + cb[q]);
           }
         } else if (pl + 1 < M) {
           const int pi = pl + 1 < M ? pl + 1 : pl;
@@ -237,13 +236,8 @@ __global__ void __launch_bounds__(256, 2) k_jacobi_tma(const __grid_constant__ T
           lap(pi, zi, Li);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float rr = yr[q] - (zr[q] - sr * Lr[q] + si * Li[q]);
-            const float ri = yi[q] - (zi[q] - sr * Li[q] - si * Lr[q]);
-            const float dprime = p.sc.k2 + cb[q];
-            const float dr = 1.f - sr * dprime, di = -si * dprime;
-            const float inv = jdiv(p.omega, dr * dr + di * di);
-            out[pl][q] = zr[q] + (rr * dr + ri * di) * inv;
-            out[pi][q] = zi[q] + (ri * dr - rr * di) * inv;
+            jac_cplx(yr[q], yi[q], zr[q], zi[q], Lr[q], Li[q], sr, si, p.omega, p.sc.k2 + cb[q], out[pl][q],
+                     out[pi][q]);
           }
         }
       }

@@ -599,6 +599,14 @@ void apply_fuse(InnerParams<T>& ip, const BtFuse<T>& f) {
 }
 
 template <typename T>
+InnerParams<T> inner_params_fused(st_handle* h, Level& Lv, int k, int P, const Shifts<T>& sh, bool use_cbar,
+                                  const BtFuse<T>& f) {
+  InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+  apply_fuse(ip, f);
+  return ip;
+}
+
+template <typename T>
 int inner_vcycle(st_handle* h, Level& Lv, int k, int depth, int sweeps, int P, const Shifts<T>& sh, bool use_cbar,
                  bool presmoothed, const BtFuse<T>* fuse, cudaStream_t st) {
   InnerLev& I = Lv.in[k];
@@ -616,6 +624,31 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int depth, int sweeps, int P, c
     // non-stiff bottom grid: Jacobi sweeps continuing from z (which holds
     // the zero-start iterate when `presmoothed`)
     const int todo = presmoothed ? sweeps - 1 : sweeps;
+    if constexpr (std::is_same<T, float>::value) {
+      // the last two sweeps as one kernel, the middle iterate kept on chip
+      if (fuse && todo >= 2 && h->o.fuse_sweeps) {
+        for (int it = 0; it < todo - 2; ++it) {
+          InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+          launch_inner_jacobi<T>(h->D, 0, ip, st);
+          CKL();
+          std::swap(I.z, I.t);
+        }
+        InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+        apply_fuse(ip, *fuse);
+        if (launch_sweep2(h->D, ip, st)) {
+          CKL();
+          return ST_OK;
+        }
+        // not applicable here: the two sweeps run as separate launches
+        InnerParams<T> ip1 = inner_params<T>(h, Lv, k, P, sh, use_cbar);
+        launch_inner_jacobi<T>(h->D, 0, ip1, st);
+        CKL();
+        std::swap(I.z, I.t);
+        launch_inner_jacobi<T>(h->D, 0, inner_params_fused<T>(h, Lv, k, P, sh, use_cbar, *fuse), st);
+        CKL();
+        return ST_OK;
+      }
+    }
     for (int it = 0; it < todo; ++it) {
       InnerParams<T> ip = inner_params<T>(h, Lv, k, P, sh, use_cbar);
       if (fuse && it == todo - 1) {
@@ -1514,6 +1547,7 @@ void st_default_opts(st_solver_opts* o) {
   o->pfasst_sweeps = 1;
   o->use_tma = 1;
   o->recompute_slabs = 0;
+  o->fuse_sweeps = 1;
 }
 
 const char* st_status_str(int s) {
@@ -1626,6 +1660,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   const bool rx = pin->reaction != ST_REACTION_NONE;
   // levels and buffers
   slab_smooth_prepare();
+  sweep2_prepare();
   h->L.resize(pl.size());
   for (size_t l = 0; l < pl.size(); ++l) {
     Level& Lv = h->L[l];
@@ -2288,7 +2323,7 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
   PdlScope pdl_scope(h);
-  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_UPDATE) return ST_ERR_INVALID_ARG;
+  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_SWEEP2) return ST_ERR_INVALID_ARG;
   if (which >= ST_KERNEL_SHIFTED_RESIDUAL && which <= ST_KERNEL_PROLONG && h->L[0].in.size() < 2)
     return ST_ERR_UNSUPPORTED;
   if ((which == ST_KERNEL_FINE_RESIDUAL || which == ST_KERNEL_UPDATE) && (!U || !is_device_ptr(U)))
@@ -2378,6 +2413,21 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         };
         return h->fp64 ? go(double(0)) : go(float(0));
       }
+      case ST_KERNEL_SWEEP2: {
+        if (h->fp64) return ST_ERR_UNSUPPORTED;
+        InnerParams<float> ip = inner_params<float>(h, L0, 0, h->p.M, level_shifts<float>(*L0.ns, L0.dt), rx);
+        BtFuse<float> f;
+        f.on = true;
+        f.e_zero = 0;
+        f.omega = (float)L0.omega;
+        f.e = (float*)L0.e;
+        for (int a2 = 0; a2 < MAXM; ++a2)
+          for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (float)h->fine->Bf[a2][b];
+        apply_fuse(ip, f);
+        if (!launch_sweep2(h->D, ip, st)) return ST_ERR_UNSUPPORTED;
+        CKL();
+        return ST_OK;
+      }
       case ST_KERNEL_UPDATE:
         // U + 0 * e with e zeroed above: the loads and stores of the cycle's
         // update, U's values unchanged
@@ -2395,6 +2445,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_JACOBI_PLAIN: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
     case ST_KERNEL_UPDATE: bytes = D * (8 + es + 8); break;
+    case ST_KERNEL_SWEEP2: bytes = D * 4 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_INNER_RESTRICT: {
       const double Dc = (double)L0.in[1].g.Ns * L0.Nt * h->p.M;

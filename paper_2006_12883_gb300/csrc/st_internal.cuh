@@ -336,6 +336,29 @@ __device__ __forceinline__ float jdiv<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// Damped Jacobi update of the shifted slab systems at one point in FP32,
+// with every rounding spelt out (explicit FMAs and rounded products, so no
+// kernel's contraction choices differ): the real system
+//   z' = z + omega (y - (z - s L)) / (1 - s dg),
+// and a complex pair s = sr + i si,
+//   z' = z + omega conj(d) (y - (z - s L)) / |d|^2,  d = 1 - s dg,
+// with L = (nu Lap + cbar) z at the point and dg = its diagonal coefficient.
+// The sweep kernels that must agree to the bit (direct, TMA-staged, two
+// sweeps in one) all use these.
+__device__ __forceinline__ float jac_real(float y, float z, float L, float sr, float omega, float dg) {
+  const float r = __fsub_rn(y, fmaf(-sr, L, z));
+  return __fadd_rn(z, jdiv(__fmul_rn(omega, r), fmaf(-sr, dg, 1.f)));
+}
+__device__ __forceinline__ void jac_cplx(float yr, float yi, float zr, float zi, float Lr, float Li, float sr,
+                                         float si, float omega, float dg, float& outr, float& outi) {
+  const float rr = __fsub_rn(yr, fmaf(si, Li, fmaf(-sr, Lr, zr)));
+  const float ri = __fsub_rn(yi, fmaf(-si, Lr, fmaf(-sr, Li, zi)));
+  const float dr = fmaf(-sr, dg, 1.f), di = __fmul_rn(-si, dg);
+  const float inv = jdiv(omega, fmaf(dr, dr, __fmul_rn(di, di)));
+  outr = fmaf(fmaf(rr, dr, __fmul_rn(ri, di)), inv, zr);
+  outi = fmaf(fmaf(ri, dr, __fmul_rn(-rr, di)), inv, zi);
+}
+
 struct ResidParams {
   GridP g;
   int Nt, M, chunk, nchunks;

@@ -9,7 +9,7 @@ import stgen
 from oracle import multilevel as ml
 from oracle import space, system
 from tests.gpu_cases import (CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, RAGGED, SMMG1D, SMMG2D, STMG1D, STMG2D,
-                             TILED_M5,
+                             TILED_M5, TILED_SQ3, TILED_SQ5,
                              Case)
 
 pytestmark = pytest.mark.gpu
@@ -269,5 +269,24 @@ def test_staged_whole_cycles_same_bits(case):
         S.vcycle(U)
         S.vcycle(U)
         outs.append(U.cpu())
+        S.close()
+    assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("case", [RAGGED, TILED_M5, TILED_SQ3, TILED_SQ5], ids=lambda c: c.name)
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_two_sweep_kernel_same_bits(case, adjoint):
+    """The last two Jacobi sweeps of a slab solve as one kernel (the middle
+    iterate in shared memory) against the two separate launches: whole FP32
+    V-cycles, forward and transposed, give the same bits (the Jacobi update's
+    roundings are spelt out in one shared helper)."""
+    from paper_2006_12883_gb300 import stlib
+    outs = []
+    for fuse in (1, 0):
+        p, S, U = _setup(case, "fp32", fuse_sweeps=fuse)
+        r = torch.tensor(stgen.random_field(S.level_shape(0), 701), dtype=S.cycle_dtype, device="cuda")
+        e1 = S.level_vcycle(r, transpose=adjoint)
+        e2 = S.level_vcycle(r - 0.5 * e1, transpose=adjoint)
+        outs.append(torch.cat([e1.reshape(-1), e2.reshape(-1)]).cpu())
         S.close()
     assert torch.equal(outs[0], outs[1])
