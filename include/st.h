@@ -166,7 +166,7 @@ typedef struct {
                            per block, a divisor of Nt; 0 (default) = off.
                            st_create ignores it. */
   int fuse_sweeps;      /* 1 (default): the last two Jacobi sweeps of a slab
-                           solve on 2D periodic grids in whole 64 x 16 tiles,
+                           solve on 2D periodic grids in whole 64 x 8 tiles,
                            M = 3 or 5, FP32, run as one kernel with the middle
                            iterate in shared memory (same arithmetic); 0: two
                            launches */

@@ -1,5 +1,5 @@
 // The last two Jacobi sweeps of a depth-capped slab solve in one kernel
-// (2D periodic grids in whole 64 x 16 tiles, M = 3 or 5, FP32): the sweep
+// (2D periodic grids in whole 64 x 8 tiles, M = 3 or 5, FP32): the sweep
 // z -> z' and the sweep z' -> z'' fused with the back-transform and the
 // damped block-Jacobi update of e, e = (e_zero ? 0 : e) + omega_bt B z''.
 // The separate kernels stream z, y and cbar twice and z' out and back in;
@@ -7,7 +7,9 @@
 // halo into shared memory (cp.async copies, all of a thread's copies in
 // flight at once), computes z' on the tile and its one-point ring, keeps it
 // in shared memory, and computes the second sweep on the tile: 16.8 instead
-// of 29.6 bytes per dof at M = 5.  The arithmetic is that of k_inner4's
+// of 29.6 bytes per dof at M = 5.  Tiles of 64 x 8 (49 KB of shared memory at
+// M = 5, four blocks per SM) measured faster than 64 x 16 (86 KB, two blocks):
+// 19.5 against 20.8 ms on 1024^2 x 1024 slabs x 5 nodes.  The arithmetic is that of k_inner4's
 // sweep (k_level4.cu), term for term, so the result equals the two-launch
 // sequence.
 #include <mutex>
@@ -18,13 +20,14 @@ namespace st {
 
 namespace {
 
-constexpr int kW = 64, kH = 16;   // tile: x points, rows
+constexpr int kW = 64;            // tile width (x points)
+constexpr int kTH = 8;            // tile height (rows)
 constexpr int kS = 72;            // shared row stride: columns -4..67, the tile's at 4..67
-constexpr int kZR = kH + 4;       // z rows -2..17
-constexpr int kYR = kH + 2;       // y, cbar, z' rows -1..16
 
-template <int M>
+// shared planes of a tile of kH rows: z rows -2..kH+1, y, cbar and z' rows -1..kH
+template <int M, int kH>
 struct Sweep2Smem {
+  static constexpr int kZR = kH + 4, kYR = kH + 2;
   float z[M][kZR][kS];
   float y[M][kYR][kS];
   float z1[M][kYR][kS];
@@ -104,13 +107,16 @@ __device__ __forceinline__ void group_operands(const float* zc, const float* zu,
   }
 }
 
-constexpr int kThreads = kYR * 16;  // one thread per group of 4 points of the first sweep's region
+// one thread per group of 4 points of the first sweep's region (rows -1..kH)
+template <int kH>
+__host__ __device__ constexpr int sweep2_threads() { return (kH + 2) * 16; }
 
-template <int M>
-__global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
+template <int M, int kH>
+__global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<float> p) {
   grid_dep_wait();
+  constexpr int kZR = kH + 4, kYR = kH + 2, kThreads = sweep2_threads<kH>();
   extern __shared__ __align__(16) unsigned char smraw[];
-  Sweep2Smem<M>& S = *reinterpret_cast<Sweep2Smem<M>*>(smraw);
+  Sweep2Smem<M, kH>& S = *reinterpret_cast<Sweep2Smem<M, kH>*>(smraw);
   const int tid = threadIdx.x;
   const int nx = p.g.n0, ny = p.g.n1;
   const long long Ns = p.g.Ns;
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
   const int tile = (int)(blockIdx.x % (unsigned)per_slab), n = (int)(blockIdx.x / (unsigned)per_slab);
   const int j0 = (tile / ntx) * kH, i0 = (tile % ntx) * kW;
   const long long base = (long long)n * M * Ns;
-  auto row = [&](int r) -> long long {  // periodic row r of the tile (r may be -2..17)
+  auto row = [&](int r) -> long long {  // periodic row r of the tile (r may be -2..kH+1)
     int j = j0 + r;
     j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
     return (long long)j * nx;
@@ -130,20 +136,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
   };
   const bool has_cb = p.cbar != nullptr;
   // every copy of the block in flight at once
-  for (int q = tid; q < M * kZR * 16; q += kThreads) {  // z: the tile's columns of rows -2..17
+  for (int q = tid; q < M * kZR * 16; q += kThreads) {  // z: the tile's columns of rows -2..kH+1
     const int pl = q / (kZR * 16), rem = q - pl * (kZR * 16), r = rem >> 4, g = rem & 15;
     cp_async16(&S.z[pl][r][4 + 4 * g], p.z + base + pl * Ns + row(r - 2) + i0 + 4 * g);
   }
-  for (int q = tid; q < M * kZR * 4; q += kThreads) {  // z: columns -2, -1, 64, 65 of rows -2..17
+  for (int q = tid; q < M * kZR * 4; q += kThreads) {  // z: columns -2, -1, 64, 65 of rows -2..kH+1
     const int pl = q / (kZR * 4), rem = q - pl * (kZR * 4), r = rem >> 2, k = rem & 3;
     const int c = k < 2 ? k - 2 : 62 + k;
     cp_async4(&S.z[pl][r][4 + c], p.z + base + pl * Ns + row(r - 2) + col(c));
   }
-  for (int q = tid; q < M * kYR * 16; q += kThreads) {  // y: the tile's columns of rows -1..16
+  for (int q = tid; q < M * kYR * 16; q += kThreads) {  // y: the tile's columns of rows -1..kH
     const int pl = q / (kYR * 16), rem = q - pl * (kYR * 16), r = rem >> 4, g = rem & 15;
     cp_async16(&S.y[pl][r][4 + 4 * g], p.y + base + pl * Ns + row(r - 1) + i0 + 4 * g);
   }
-  for (int q = tid; q < M * kYR * 2; q += kThreads) {  // y: columns -1, 64 of rows -1..16
+  for (int q = tid; q < M * kYR * 2; q += kThreads) {  // y: columns -1, 64 of rows -1..kH
     const int pl = q / (kYR * 2), rem = q - pl * (kYR * 2), r = rem >> 1, c = (rem & 1) ? kW : -1;
     cp_async4(&S.y[pl][r][4 + c], p.y + base + pl * Ns + row(r - 1) + col(c));
   }
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
-  // first sweep on rows -1..16: thread tid takes the group of 4 points at
+  // first sweep on rows -1..kH: thread tid takes the group of 4 points at
   // shared row r (tile row r - 1) and columns c0..c0+3
   {
     const int r = tid >> 4, c0 = 4 + 4 * (tid & 15);
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep2(InnerParams<float> p) {
       if (kd == SH_RE) *reinterpret_cast<float4*>(&S.z1[pi][r][c0]) = make_float4(outi[0], outi[1], outi[2], outi[3]);
     }
   }
-  // first sweep at the ring's columns -1 and 64 of rows -1..16
+  // first sweep at the ring's columns -1 and 64 of rows -1..kH
   if (tid < kYR * 2) {
     const int r = tid >> 1, c = 4 + ((tid & 1) ? kW : -1);
     float cb[1] = {has_cb ? S.cb[r][c] : 0.f};
@@ -249,10 +255,10 @@ int g_sweep2_ready = 0;  // 1 once the shared-memory opt-in is set
 void sweep2_prepare() {
   static std::once_flag once;
   std::call_once(once, [] {
-    bool ok = cudaFuncSetAttribute(k_sweep2<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(Sweep2Smem<3>)) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_sweep2<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(Sweep2Smem<5>)) == cudaSuccess;
+    bool ok = cudaFuncSetAttribute(k_sweep2<3, kTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(Sweep2Smem<3, kTH>)) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_sweep2<5, kTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(Sweep2Smem<5, kTH>)) == cudaSuccess;
     cudaGetLastError();  // without the opt-in the two sweeps stay separate launches
     g_sweep2_ready = ok ? 1 : 0;
   });
@@ -261,13 +267,14 @@ void sweep2_prepare() {
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st) {
   if (g_sweep2_ready != 1) return false;
   if (!(D == 2 && (p.P == 3 || p.P == 5) && p.g.bc == BC_PER && p.g.n0 >= kW && p.g.n0 % kW == 0 &&
-        p.g.n1 >= kH && p.g.n1 % kH == 0 && p.fuse_bt && p.e && aligned16(p.z) && aligned16(p.y) &&
+        p.g.n1 >= kTH && p.g.n1 % kTH == 0 && p.fuse_bt && p.e && aligned16(p.z) && aligned16(p.y) &&
         aligned16(p.e) && aligned16(p.cbar)))
     return false;
-  const long long nb = (long long)(p.g.n0 / kW) * (p.g.n1 / kH) * p.Nt;
+  const long long nb = (long long)(p.g.n0 / kW) * (p.g.n1 / kTH) * p.Nt;
   if (nb >= 0x7fffffffLL) return false;
-  if (p.P == 3) st_launch(k_sweep2<3>, (unsigned)nb, kThreads, sizeof(Sweep2Smem<3>), st, p);
-  else st_launch(k_sweep2<5>, (unsigned)nb, kThreads, sizeof(Sweep2Smem<5>), st, p);
+  constexpr int nt = sweep2_threads<kTH>();
+  if (p.P == 3) st_launch(k_sweep2<3, kTH>, (unsigned)nb, nt, sizeof(Sweep2Smem<3, kTH>), st, p);
+  else st_launch(k_sweep2<5, kTH>, (unsigned)nb, nt, sizeof(Sweep2Smem<5, kTH>), st, p);
   return true;
 }
 

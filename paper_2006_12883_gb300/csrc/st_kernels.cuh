@@ -126,7 +126,7 @@ template <typename T> void launch_inner_jacobi(int D, int zero, const InnerParam
 void slab_smooth_prepare();
 // k_sweep2.cu: the last two Jacobi sweeps of a depth-capped slab solve (the
 // second fused with the back-transform and update of e, p.fuse_bt) as one
-// kernel on 2D periodic grids in whole 64 x 16 tiles, M = 3 or 5; false where
+// kernel on 2D periodic grids in whole 64 x 8 tiles, M = 3 or 5; false where
 // it does not apply.  p is the first sweep's parameter block (z in).
 void sweep2_prepare();
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st);
