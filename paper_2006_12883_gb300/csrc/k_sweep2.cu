@@ -196,15 +196,30 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
       if (kd == SH_RE) *reinterpret_cast<float4*>(&S.z1[pi][r][c0]) = make_float4(outi[0], outi[1], outi[2], outi[3]);
     }
   }
-  // first sweep at the ring's columns -1 and 64 of rows -1..kH
-  if (tid < kYR * 2) {
-    const int r = tid >> 1, c = 4 + ((tid & 1) ? kW : -1);
-    float cb[1] = {has_cb ? S.cb[r][c] : 0.f};
+  // first sweep at the ring's columns -1 and 64 of rows -1..kH: one item per
+  // (point, real plane or complex pair), spread over the block
+  {
+    auto lead = [&](int q) {  // plane q is a real plane or the first of a complex pair
+      const int kd = p.sh.kind[q];
+      return kd == SH_REAL || (kd == SH_RE && q + 1 < M);
+    };
+    int np = 0;
 #pragma unroll
-    for (int pl = 0; pl < M; ++pl) {
+    for (int q = 0; q < M; ++q) np += lead(q) ? 1 : 0;
+    for (int item = tid; item < kYR * 2 * np; item += kThreads) {
+      const int pt = item % (kYR * 2), k = item / (kYR * 2);
+      const int r = pt >> 1, c = 4 + ((pt & 1) ? kW : -1);
+      int pl = 0, cnt = 0;  // the k-th leading plane
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        if (lead(q)) {
+          if (cnt == k) pl = q;
+          ++cnt;
+        }
+      }
       const int kd = p.sh.kind[pl];
-      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
       const int pi = pl + 1 < M ? pl + 1 : pl;
+      float cb[1] = {has_cb ? S.cb[r][c] : 0.f};
       float zr[1] = {S.z[pl][r + 1][c]}, yr[1] = {S.y[pl][r][c]};
       float sxr[1] = {S.z[pl][r + 1][c - 1] + S.z[pl][r + 1][c + 1]}, syr[1] = {S.z[pl][r][c] + S.z[pl][r + 2][c]};
       float zi[1] = {S.z[pi][r + 1][c]}, yi[1] = {S.y[pi][r][c]};
