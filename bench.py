@@ -169,10 +169,10 @@ class ClockSampler:
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # k_inner4<2, 5, 2> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.65 MB read + 477.37 MB written per launch
-    "k_inner4<2, 5, 2>": {"file": "k_level4.cu",
-                          "sha256": "e305c72967d1abed7edb159f2ea60dbf51c6d110cc9cbf12186f7e815bf2924b",
-                          "dram_bytes_per_dof": 2088020224 / 125829120},
+    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.66 MB read + 476.56 MB written per launch
+    "k_sweep2<5, 8>": {"file": "k_sweep2.cu",
+                       "sha256": "d174c4582bab082492269c82e8f9026abd5e829ed2add06516e6f8f24b711c8d",
+                       "dram_bytes_per_dof": (1610664192 + 476563712) / 125829120},
 }
 
 
@@ -557,15 +557,18 @@ def run_ours(args):
 
     hbm, src = measured_peaks()
     # dominant kernel (largest share of the step in the ncu launch list): the
-    # last Jacobi sweep of a slab solve, fused with the back-transform and
-    # the damped block-Jacobi update of e, timed here at level 0 where it
-    # moves the most bytes; HBM bound.  TMA-staged on 2D grids at M = 3.
-    k = kernels["slab_jacobi"]
+    # last two Jacobi sweeps of a slab solve in one kernel, the second fused
+    # with the back-transform and the damped block-Jacobi update of e (2D
+    # periodic grids in whole 64 x 8 tiles), else the fused last sweep alone;
+    # timed here at level 0 where it moves the most bytes; HBM bound
     d = len(w["grid"])
-    kname = "k_jacobi_tma<3>" if (d == 2 and w["M"] == 3 and w["bc"] == "periodic") else \
-        f"k_inner4<{d}, {w['M']}, 2>"
-    roofline = {"bound": "hbm", "kernel": kname + ": level-0 Jacobi sweep of the shifted slab systems fused with "
-                                                  "the back-transform and update of e (z, y, e, cbar in, e out)",
+    two = kernels.get("two_sweeps", {}).get("GBps") is not None
+    k = kernels["two_sweeps"] if two else kernels["slab_jacobi"]
+    kname = f"k_sweep2<{w['M']}, 8>" if two else f"k_inner4<{d}, {w['M']}, 2>"
+    what = ("two Jacobi sweeps of the shifted slab systems in one kernel, the second fused with the back-transform "
+            "and update of e" if two else
+            "Jacobi sweep of the shifted slab systems fused with the back-transform and update of e")
+    roofline = {"bound": "hbm", "kernel": kname + ": level-0 " + what + " (z, y, e, cbar in, e out)",
                 "achieved": k.get("GBps"), "peak": hbm, "unit": "GB/s",
                 "frac": (k["GBps"] / hbm) if k.get("GBps") else None,
                 "traffic": ncu_traffic(kname, D),
