@@ -21,6 +21,11 @@ namespace st {
 namespace {
 
 constexpr int kW = 64;            // tile width (x points)
+// Plane pattern of the Q eigenbasis at odd M (the setup orders the real
+// eigenvalue first, then the conjugate pairs): plane 0 real, planes 1-2 and
+// 3-4 complex pairs.  The launcher checks it.
+__host__ __device__ constexpr bool lead_plane(int q) { return q == 0 || (q & 1); }
+__host__ __device__ constexpr int plane_kind(int q) { return q == 0 ? SH_REAL : ((q & 1) ? SH_RE : SH_IM); }
 constexpr int kTH = 8;            // tile height (rows)
 constexpr int kS = 72;            // shared row stride: columns -4..67, the tile's at 4..67
 
@@ -36,11 +41,6 @@ struct Sweep2Smem {
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
                "l"(__cvta_generic_to_global(src))
                : "memory");
 }
@@ -130,39 +130,27 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
     j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
     return (long long)j * nx;
   };
-  auto col = [&](int c) -> int {  // periodic column c of the tile (c may be -2..65)
-    int i = i0 + c;
-    return i < 0 ? i + nx : (i >= nx ? i - nx : i);
-  };
   const bool has_cb = p.cbar != nullptr;
-  // every copy of the block in flight at once
-  for (int q = tid; q < M * kZR * 16; q += kThreads) {  // z: the tile's columns of rows -2..kH+1
-    const int pl = q / (kZR * 16), rem = q - pl * (kZR * 16), r = rem >> 4, g = rem & 15;
-    cp_async16(&S.z[pl][r][4 + 4 * g], p.z + base + pl * Ns + row(r - 2) + i0 + 4 * g);
+  // every copy of the block in flight at once; a thread takes fixed (row,
+  // column group) slots and walks the planes.  The halo columns come in the
+  // aligned 16-byte groups that hold them (columns -4..-1 and 64..67).
+  const int cl = i0 == 0 ? nx - 4 : i0 - 4, cr = i0 + kW == nx ? 0 : i0 + kW;
+  for (int sl = tid; sl < kZR * 18; sl += kThreads) {  // z: rows -2..kH+1, groups -1..16
+    const int r = sl / 18, g = sl - r * 18;
+    const int gc = g == 0 ? cl : (g == 17 ? cr : i0 + 4 * (g - 1));
+    const float* src = p.z + base + row(r - 2) + gc;
+    float* dst = &S.z[0][r][4 * g];
+#pragma unroll
+    for (int pl = 0; pl < M; ++pl) cp_async16(dst + pl * (kZR * kS), src + pl * Ns);
   }
-  for (int q = tid; q < M * kZR * 4; q += kThreads) {  // z: columns -2, -1, 64, 65 of rows -2..kH+1
-    const int pl = q / (kZR * 4), rem = q - pl * (kZR * 4), r = rem >> 2, k = rem & 3;
-    const int c = k < 2 ? k - 2 : 62 + k;
-    cp_async4(&S.z[pl][r][4 + c], p.z + base + pl * Ns + row(r - 2) + col(c));
-  }
-  for (int q = tid; q < M * kYR * 16; q += kThreads) {  // y: the tile's columns of rows -1..kH
-    const int pl = q / (kYR * 16), rem = q - pl * (kYR * 16), r = rem >> 4, g = rem & 15;
-    cp_async16(&S.y[pl][r][4 + 4 * g], p.y + base + pl * Ns + row(r - 1) + i0 + 4 * g);
-  }
-  for (int q = tid; q < M * kYR * 2; q += kThreads) {  // y: columns -1, 64 of rows -1..kH
-    const int pl = q / (kYR * 2), rem = q - pl * (kYR * 2), r = rem >> 1, c = (rem & 1) ? kW : -1;
-    cp_async4(&S.y[pl][r][4 + c], p.y + base + pl * Ns + row(r - 1) + col(c));
-  }
-  if (has_cb) {
-    const long long cbase = (long long)n * Ns;
-    for (int q = tid; q < kYR * 16; q += kThreads) {
-      const int r = q >> 4, g = q & 15;
-      cp_async16(&S.cb[r][4 + 4 * g], p.cbar + cbase + row(r - 1) + i0 + 4 * g);
-    }
-    for (int q = tid; q < kYR * 2; q += kThreads) {
-      const int r = q >> 1, c = (q & 1) ? kW : -1;
-      cp_async4(&S.cb[r][4 + c], p.cbar + cbase + row(r - 1) + col(c));
-    }
+  for (int sl = tid; sl < kYR * 18; sl += kThreads) {  // y: rows -1..kH, groups -1..16
+    const int r = sl / 18, g = sl - r * 18;
+    const int gc = g == 0 ? cl : (g == 17 ? cr : i0 + 4 * (g - 1));
+    const float* src = p.y + base + row(r - 1) + gc;
+    float* dst = &S.y[0][r][4 * g];
+#pragma unroll
+    for (int pl = 0; pl < M; ++pl) cp_async16(dst + pl * (kYR * kS), src + pl * Ns);
+    if (has_cb) cp_async16(&S.cb[r][4 * g], p.cbar + (long long)n * Ns + row(r - 1) + gc);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   // the e of the tile's thread (4 points of tile row ty, every plane), for the epilogue
@@ -185,8 +173,8 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
     if (has_cb) ld4s(&S.cb[r][c0], cb);
 #pragma unroll
     for (int pl = 0; pl < M; ++pl) {
-      const int kd = p.sh.kind[pl];
-      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
+      if (!lead_plane(pl)) continue;
+      const int kd = plane_kind(pl);
       const int pi = pl + 1 < M ? pl + 1 : pl;
       float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4], outr[4], outi[4];
       group_operands(S.z[pl][r + 1], S.z[pl][r], S.z[pl][r + 2], S.y[pl][r], c0, zr, yr, sxr, syr);
@@ -199,25 +187,12 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
   // first sweep at the ring's columns -1 and 64 of rows -1..kH: one item per
   // (point, real plane or complex pair), spread over the block
   {
-    auto lead = [&](int q) {  // plane q is a real plane or the first of a complex pair
-      const int kd = p.sh.kind[q];
-      return kd == SH_REAL || (kd == SH_RE && q + 1 < M);
-    };
-    int np = 0;
-#pragma unroll
-    for (int q = 0; q < M; ++q) np += lead(q) ? 1 : 0;
+    constexpr int np = (M + 1) / 2;  // the real plane and the pairs
     for (int item = tid; item < kYR * 2 * np; item += kThreads) {
       const int pt = item % (kYR * 2), k = item / (kYR * 2);
       const int r = pt >> 1, c = 4 + ((pt & 1) ? kW : -1);
-      int pl = 0, cnt = 0;  // the k-th leading plane
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        if (lead(q)) {
-          if (cnt == k) pl = q;
-          ++cnt;
-        }
-      }
-      const int kd = p.sh.kind[pl];
+      const int pl = k == 0 ? 0 : 2 * k - 1;  // the k-th leading plane
+      const int kd = pl == 0 ? SH_REAL : SH_RE;
       const int pi = pl + 1 < M ? pl + 1 : pl;
       float cb[1] = {has_cb ? S.cb[r][c] : 0.f};
       float zr[1] = {S.z[pl][r + 1][c]}, yr[1] = {S.y[pl][r][c]};
@@ -240,8 +215,8 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
     float out[M][4];
 #pragma unroll
     for (int pl = 0; pl < M; ++pl) {
-      const int kd = p.sh.kind[pl];
-      if (!(kd == SH_REAL || (kd == SH_RE && pl + 1 < M))) continue;
+      if (!lead_plane(pl)) continue;
+      const int kd = plane_kind(pl);
       const int pi = pl + 1 < M ? pl + 1 : pl;
       float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4];
       group_operands(S.z1[pl][r], S.z1[pl][r - 1], S.z1[pl][r + 1], S.y[pl][r], c0, zr, yr, sxr, syr);
@@ -281,6 +256,8 @@ void sweep2_prepare() {
 
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st) {
   if (g_sweep2_ready != 1) return false;
+  for (int q = 0; q < p.P; ++q)
+    if (p.sh.kind[q] != plane_kind(q)) return false;  // the compiled plane pattern
   if (!(D == 2 && (p.P == 3 || p.P == 5) && p.g.bc == BC_PER && p.g.n0 >= kW && p.g.n0 % kW == 0 &&
         p.g.n1 >= kTH && p.g.n1 % kTH == 0 && p.fuse_bt && p.e && aligned16(p.z) && aligned16(p.y) &&
         aligned16(p.e) && aligned16(p.cbar)))
