@@ -170,6 +170,13 @@ typedef struct {
                            M = 3 or 5, FP32, run as one kernel with the middle
                            iterate in shared memory (same arithmetic); 0: two
                            launches */
+  int fuse_start;       /* 1 (default): where the FP64-accurate fine residual
+                           runs tiled (2D periodic, 64 x 16 tiles, M = 3 or 5)
+                           and the cycle is FP32, it also writes the first
+                           step of the cycle's first level-0 smoothing (from
+                           e = 0: y = F r and the zero-start Jacobi iterate),
+                           which the cycle then skips (same arithmetic); 0:
+                           the cycle does that step itself */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must

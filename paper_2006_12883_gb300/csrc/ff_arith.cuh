@@ -81,7 +81,10 @@ struct ResidFF {
 
 // k_fine_tile.cu: the variant for 2D periodic grids in whole 64 x 16 tiles
 // (M = 3 or 5, 16-byte aligned arrays); false / 0 where it does not apply.
-bool launch_residual_tile(int D, const ResidParams& p, const ResidFF& c, cudaStream_t st);
+// With ss (float residual written, cbar written when there is a reaction
+// term) it also writes the smoothing start.
+bool launch_residual_tile(int D, const ResidParams& p, const ResidFF& c, cudaStream_t st, const SmoothStart* ss);
 long long residual_tile_blocks(int D, const ResidParams& p);
+bool residual_tile_start_ok(int D, const ResidParams& p, const SmoothStart* ss);
 
 }  // namespace st

@@ -297,7 +297,11 @@ long long residual_ff_blocks(int D, const ResidParams& p) {
   return ff4_ok(D, p) ? residual_blocks4(p) : residual_blocks(p);
 }
 
-void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
+bool residual_start_ok(int D, const ResidParams& p, const SmoothStart* ss) {
+  return residual_tile_start_ok(D, p, ss);
+}
+
+void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st, const SmoothStart* ss) {
   ResidFF c;
   c.cx = split_const(p.sc.cx);
   c.cy = split_const(p.sc.cy);
@@ -307,7 +311,7 @@ void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st) {
   c.rho32 = (float)p.rho;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) c.w[a][b] = split_const(p.dtq[a][b]);
-  if (launch_residual_tile(D, p, c, st)) return;
+  if (launch_residual_tile(D, p, c, st, ss)) return;
   if (ff4_ok(D, p)) {
     const FastDiv fG((unsigned)(p.g.Ns >> 2));
     const unsigned nb4 = (unsigned)residual_blocks4(p);

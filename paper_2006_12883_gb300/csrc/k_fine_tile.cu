@@ -64,9 +64,11 @@ __device__ __forceinline__ float tprod(float a, float chi, float clo, float& e) 
 }
 
 // ISO: h_x = h_y (cx == cy), so the two exact second differences add exactly
-// (|Sx + Sy| <= 2^24 grid steps) and take one error-free product with nu/h^2
-template <int M, bool ISO>
-__global__ void __launch_bounds__(256, M == 3 ? 3 : 2) k_residual_tile(ResidParams p, ResidFF c) {
+// (|Sx + Sy| <= 2^24 grid steps) and take one error-free product with nu/h^2.
+// START: also write the first step of the cycle's first smoothing from the
+// float residual (y = F r and the zero-start Jacobi iterate z, SmoothStart).
+template <int M, bool ISO, bool START>
+__global__ void __launch_bounds__(256, M == 3 ? 3 : 2) k_residual_tile(ResidParams p, ResidFF c, SmoothStart ss) {
   grid_dep_wait();
   __shared__ __align__(16) RSmem S;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
@@ -262,20 +264,56 @@ __global__ void __launch_bounds__(256, M == 3 ? 3 : 2) k_residual_tile(ResidPara
         for (int q = 0; q < 4; ++q) { ph[q] = chh[q]; pl[q] = cll[q]; }
       }
     }
+    float out[M][4];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      float out[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        out[q] = g[m][q] + ge[m][q];
-        sq = fmaf(out[q], out[q], sq);
+        out[m][q] = g[m][q] + ge[m][q];
+        sq = fmaf(out[m][q], out[m][q], sq);
       }
-      if (R) *reinterpret_cast<float4*>(R + ((long long)n * M + m) * Ns + own) = make_float4(out[0], out[1], out[2], out[3]);
+      if (R)
+        *reinterpret_cast<float4*>(R + ((long long)n * M + m) * Ns + own) =
+            make_float4(out[m][0], out[m][1], out[m][2], out[m][3]);
     }
+    float cbv[4] = {0.f, 0.f, 0.f, 0.f};
     if (cb) {
       const float invM = 1.0f / M;
-      *reinterpret_cast<float4*>(cb + (long long)n * Ns + own) =
-          make_float4(cbs[0] * invM, cbs[1] * invM, cbs[2] * invM, cbs[3] * invM);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cbv[q] = cbs[q] * invM;
+      *reinterpret_cast<float4*>(cb + (long long)n * Ns + own) = make_float4(cbv[0], cbv[1], cbv[2], cbv[3]);
+    }
+    if constexpr (START) {
+      // y = F r per point (the level residual of e = 0 is r), then the
+      // zero-start iterate of each real plane and complex pair
+      const long long base = (long long)n * M * Ns + own;
+      float y[M][4];
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int b = 0; b < M; ++b) acc = fmaf(ss.F[a][b], out[b][q], acc);
+          y[a][q] = acc;
+        }
+        *reinterpret_cast<float4*>(ss.y + base + (long long)a * Ns) = make_float4(y[a][0], y[a][1], y[a][2], y[a][3]);
+      }
+#pragma unroll
+      for (int pl = 0; pl < M; ++pl) {
+        const int kd = ss.sh.kind[pl];
+        if (kd == SH_REAL || kd == SH_RE) {
+          const int pi = pl + 1 < M ? pl + 1 : pl;
+          float zr[4], zi[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            jac_zero(y[pl][q], kd == SH_REAL ? 0.f : y[pi][q], kd != SH_REAL, ss.sh.sr[pl], ss.sh.si[pl],
+                     ss.k2 + cbv[q], ss.omega, zr[q], zi[q]);
+          *reinterpret_cast<float4*>(ss.z + base + (long long)pl * Ns) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+          if (kd == SH_RE && pl + 1 < M)
+            *reinterpret_cast<float4*>(ss.z + base + (long long)pi * Ns) = make_float4(zi[0], zi[1], zi[2], zi[3]);
+        }
+      }
     }
   }
   if (p.partial) {
@@ -290,6 +328,13 @@ bool tile_ok(int D, const ResidParams& p) {
          aligned16(p.R) && aligned16(p.cbar) && aligned16(p.cnode);
 }
 
+// the smoothing start needs the float residual it transforms and, with a
+// reaction term, the cbar this call writes
+bool start_ok(const ResidParams& p, const SmoothStart* ss) {
+  return ss && ss->y && ss->z && p.R && aligned16(ss->y) && aligned16(ss->z) &&
+         (p.reaction == ST_REACTION_NONE || p.cbar);
+}
+
 }  // namespace
 
 long long residual_tile_blocks(int D, const ResidParams& p) {
@@ -297,14 +342,27 @@ long long residual_tile_blocks(int D, const ResidParams& p) {
   return (long long)(p.g.n0 / kRW) * (p.g.n1 / kRH) * p.nchunks;
 }
 
-bool launch_residual_tile(int D, const ResidParams& p, const ResidFF& c, cudaStream_t st) {
+bool residual_tile_start_ok(int D, const ResidParams& p, const SmoothStart* ss) {
+  return tile_ok(D, p) && start_ok(p, ss);
+}
+
+bool launch_residual_tile(int D, const ResidParams& p, const ResidFF& c, cudaStream_t st, const SmoothStart* ss) {
   if (!tile_ok(D, p)) return false;
   const unsigned nb = (unsigned)residual_tile_blocks(D, p);
   const bool iso = p.sc.cx == p.sc.cy;
-  if (p.M == 3 && iso) st_launch(k_residual_tile<3, true>, nb, 256, 0, st, p, c);
-  else if (p.M == 3) st_launch(k_residual_tile<3, false>, nb, 256, 0, st, p, c);
-  else if (iso) st_launch(k_residual_tile<5, true>, nb, 256, 0, st, p, c);
-  else st_launch(k_residual_tile<5, false>, nb, 256, 0, st, p, c);
+  const bool start = start_ok(p, ss);
+  SmoothStart s{};
+  if (start) s = *ss;
+#define RT(MM, II)                                                                  \
+  do {                                                                              \
+    if (start) st_launch(k_residual_tile<MM, II, true>, nb, 256, 0, st, p, c, s);   \
+    else st_launch(k_residual_tile<MM, II, false>, nb, 256, 0, st, p, c, s);        \
+  } while (0)
+  if (p.M == 3 && iso) RT(3, true);
+  else if (p.M == 3) RT(3, false);
+  else if (iso) RT(5, true);
+  else RT(5, false);
+#undef RT
   return true;
 }
 

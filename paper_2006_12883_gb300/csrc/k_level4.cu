@@ -77,15 +77,7 @@ __device__ __forceinline__ void split4(unsigned idx, const GridP& g, const FastD
 
 __device__ __forceinline__ void zero_jacobi(float yr, float yi, bool cplx, float sr, float si, float dprime,
                                             float omega, float& zr, float& zi) {
-  if (!cplx) {
-    zr = jdiv(omega * yr, 1.f - sr * dprime);
-    zi = 0.f;
-  } else {
-    const float dr = 1.f - sr * dprime, di = -si * dprime;
-    const float inv = jdiv(omega, dr * dr + di * di);
-    zr = (yr * dr + yi * di) * inv;
-    zi = (yi * dr - yr * di) * inv;
-  }
+  jac_zero(yr, yi, cplx, sr, si, dprime, omega, zr, zi);
 }
 
 }  // namespace

@@ -448,19 +448,9 @@ __global__ void __launch_bounds__(256, 2) k_linres_tma(const __grid_constant__ L
             const int pi = pl + 1 < M ? pl + 1 : pl;
             float zr[4], zi[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float dprime = p.sc.k2 + cb[q];
-              const float sr = p.sh.sr[pl], si = p.sh.si[pl];
-              if (kd == SH_REAL) {
-                zr[q] = jdiv(p.omega_j * y[pl][q], 1.f - sr * dprime);
-                zi[q] = 0.f;
-              } else {
-                const float dr = 1.f - sr * dprime, di = -si * dprime;
-                const float inv = jdiv(p.omega_j, dr * dr + di * di);
-                zr[q] = (y[pl][q] * dr + y[pi][q] * di) * inv;
-                zi[q] = (y[pi][q] * dr - y[pl][q] * di) * inv;
-              }
-            }
+            for (int q = 0; q < 4; ++q)
+              jac_zero(y[pl][q], kd == SH_REAL ? 0.f : y[pi][q], kd != SH_REAL, p.sh.sr[pl], p.sh.si[pl],
+                       p.sc.k2 + cb[q], p.omega_j, zr[q], zi[q]);
             *reinterpret_cast<float4*>(p.zout + base + (long long)pl * Ns) = make_float4(zr[0], zr[1], zr[2], zr[3]);
             if (kd == SH_RE && pl + 1 < M)
               *reinterpret_cast<float4*>(p.zout + base + (long long)pi * Ns) =

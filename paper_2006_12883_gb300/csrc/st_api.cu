@@ -385,16 +385,20 @@ struct st_handle {
   double* plane = nullptr;  // staging for one plane (gT / target / du0)
   double* plane2 = nullptr;
   std::vector<Alloc> allocs;
-  // 0 fwd cycle, 1 adjoint cycle, 2 linearise, 3 linearise + fwd cycle
-  // graphs: 0 forward cycle, 1 adjoint cycle, 2 linearisation, 3 linearisation + cycle, 4 PFASST iteration
-  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t gnodes[5] = {0, 0, 0, 0, 0};
+  // graphs: 0 forward cycle, 1 adjoint cycle, 2 linearisation, 3 linearisation + cycle, 4 PFASST iteration,
+  // 5 and 6: 0 and 3 after a fine residual that did the first smoothing step
+  static constexpr int kGraphs = 7;
+  cudaGraphExec_t gexec[kGraphs] = {};
+  size_t gnodes[kGraphs] = {};
   // second capture stream and events of the linearise + cycle graph: the
   // cbar chain and the coarse setup run beside the cycle's finest levels
   cudaStream_t cap2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_lvl[ST_MAX_LEVELS + 1] = {};
   bool split_lin = false;  // set while that graph's cycle is enqueued
+  // set while a forward cycle is enqueued whose first level-0 smoothing
+  // starts from the y and z the fine residual wrote (SmoothStart)
+  bool start_ready = false;
   int nt_override = 0;     // > 0: inner solves act on this many slabs from the first
   int* tma_err = nullptr;   // device count of expired TMA waits (this device's copy)
   int tma_seen = 0;         // the count this handle has reported
@@ -789,7 +793,9 @@ int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
     return ST_OK;
   }
   const bool multi = !(Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit);
-  {
+  if (l == 0 && !adj && e_zero && h->start_ready) {
+    // the fine residual wrote this step's y = F r and zero-start z
+  } else {
     // residual + Q-eigenbasis transform (+ zero-start Jacobi of the slab systems)
     LinParams<T> lp = lin_params<T>(h, Lv, adj);
     lp.e = e_zero ? nullptr : (const T*)Lv.e;
@@ -1006,19 +1012,38 @@ int enq_lin_cycle(st_handle* h, cudaStream_t st) {
   return s;
 }
 
-int cycle(st_handle* h, int adj) {
+// the forward cycle (and linearise + cycle) whose first level-0 smoothing
+// step the fine residual did (FP32 cycles only)
+int enq_cycle_started(st_handle* h, cudaStream_t st) {
+  h->start_ready = true;
+  const int s = vcycle_level<float>(h, 0, 0, st);
+  h->start_ready = false;
+  return s;
+}
+int enq_lin_cycle_started(st_handle* h, cudaStream_t st) {
+  h->start_ready = true;
+  const int s = enq_lin_cycle<float>(h, st);
+  h->start_ready = false;
+  return s;
+}
+
+// `started`: the fine residual just did the first smoothing step (fine_residual)
+int cycle(st_handle* h, int adj, bool started = false) {
   if (h->fp64) return run_graph(h, adj, adj ? enq_cycle_adj<double> : enq_cycle_fwd<double>);
+  if (started && !adj) return run_graph(h, 5, enq_cycle_started);
   return run_graph(h, adj, adj ? enq_cycle_adj<float> : enq_cycle_fwd<float>);
 }
 
 // relinearise and run one forward cycle as one graph
-int lin_cycle(st_handle* h) {
+int lin_cycle(st_handle* h, bool started = false) {
   if (!h->o.use_graphs || !h->cap2) {
     TRY(h->fp64 ? run_graph(h, 2, enq_lin<double>) : run_graph(h, 2, enq_lin<float>));
     h->coarse_ready = true;
-    return cycle(h, 0);
+    return cycle(h, 0, started);
   }
-  TRY(h->fp64 ? run_graph(h, 3, enq_lin_cycle<double>) : run_graph(h, 3, enq_lin_cycle<float>));
+  if (h->fp64) TRY(run_graph(h, 3, enq_lin_cycle<double>));
+  else if (started) TRY(run_graph(h, 6, enq_lin_cycle_started));
+  else TRY(run_graph(h, 3, enq_lin_cycle<float>));
   h->coarse_ready = true;
   return ST_OK;
 }
@@ -1030,7 +1055,7 @@ int linearize_levels(st_handle* h) {
 }
 
 void invalidate_graphs(st_handle* h) {
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < st_handle::kGraphs; ++i)
     if (h->gexec[i]) {
       cudaGraphExecDestroy(h->gexec[i]);
       h->gexec[i] = nullptr;
@@ -1068,14 +1093,46 @@ ResidParams fine_params(st_handle* h, const double* U, int adj) {
 }
 
 // r = G(U) into R (type per r_fp64), cbar optional, ||G||^2 into scal[slot].
-int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_cbar, int slot) {
+// The first step of the forward cycle's first level-0 smoothing (from
+// e = 0: y = F r and the zero-start iterate z) as the fine residual's second
+// output, where the cycle is FP32 and level 0 is smoothed by its inner
+// multigrid with at least one pre-smoothing step.
+bool start_possible(const st_handle* h) {
+  if (!h->o.fuse_start || h->fp64 || h->L.size() < 2 || h->o.nu1 < 1) return false;
+  const Level& L0 = h->L[0];
+  return !L0.fused && !(L0.in.size() == 1 && L0.in[0].g.Ns <= kInnerCoarseLimit);
+}
+
+SmoothStart smooth_start(st_handle* h) {
+  Level& L0 = h->L[0];
+  const LinParams<float> lp = lin_params<float>(h, L0, 0);
+  SmoothStart ss;
+  ss.y = (float*)L0.in[0].y;
+  ss.z = (float*)L0.in[0].z;
+  for (int a = 0; a < MAXM; ++a)
+    for (int b = 0; b < MAXM; ++b) ss.F[a][b] = lp.F[a][b];
+  ss.sh = lp.sh;
+  ss.k2 = lp.sc.k2;
+  ss.omega = lp.omega_j;
+  return ss;
+}
+
+// With `started`, the residual also does the cycle's first smoothing step
+// where it can and reports whether it did: the forward cycle that follows is
+// then run as cycle(h, 0, true) / lin_cycle(h, true).
+int fine_residual(st_handle* h, const double* U, void* R, int r_fp64, bool want_cbar, int slot,
+                  bool* started = nullptr) {
   ResidParams rp = fine_params(h, U, 0);
   rp.R = R;
   rp.cbar = (want_cbar && h->p.reaction != ST_REACTION_NONE) ? h->L[0].cbar : nullptr;
   rp.cnode = rp.cbar ? h->cnode : nullptr;
   long long nparts = residual_blocks(rp);
+  if (started) *started = false;
   if (!r_fp64 && !h->fp64) {  // FP32 output: double-float kernel
-    launch_residual_ff(h->D, rp, h->stream);
+    SmoothStart ss{};
+    const bool st = started && start_possible(h) && ((ss = smooth_start(h)), residual_start_ok(h->D, rp, &ss));
+    launch_residual_ff(h->D, rp, h->stream, st ? &ss : nullptr);
+    if (started) *started = st;
     nparts = residual_ff_blocks(h->D, rp);
   } else {
     launch_residual(h->D, r_fp64, h->fp64, rp, h->stream);
@@ -1164,13 +1221,14 @@ void fill_info(st_solve_info* info, int it, int status, double rel, double abs_,
 int outer_step(st_handle* h, double* Ud, bool do_cycle) {
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   const bool relin = rx && (h->o.newton || !h->linearized);
-  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0));
+  bool started = false;
+  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0, do_cycle ? &started : nullptr));
   if (!do_cycle) return ST_OK;
   if (relin || !h->coarse_ready) {
-    TRY(lin_cycle(h));
+    TRY(lin_cycle(h, started));
     h->linearized = true;
   } else {
-    TRY(cycle(h, 0));
+    TRY(cycle(h, 0, started));
   }
   launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
   CKL();
@@ -1188,14 +1246,15 @@ int outer_step_async(st_handle* h, double* Ud, double* norm) {
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   const bool relin = rx && (h->o.newton || !h->linearized);
   int* deferred = reinterpret_cast<int*>(h->hscal + kHostFlagDeferred);
-  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0));
+  bool started = false;
+  TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0, &started));
   CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaEventRecord(h->ev_norm, h->stream));
   if (relin || !h->coarse_ready) {
-    TRY(lin_cycle(h));
+    TRY(lin_cycle(h, started));
     h->linearized = true;
   } else {
-    TRY(cycle(h, 0));
+    TRY(cycle(h, 0, started));
   }
   launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
   CKL();
@@ -1548,6 +1607,7 @@ void st_default_opts(st_solver_opts* o) {
   o->use_tma = 1;
   o->recompute_slabs = 0;
   o->fuse_sweeps = 1;
+  o->fuse_start = 1;
 }
 
 const char* st_status_str(int s) {
@@ -1930,8 +1990,10 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
   int cycles = 0;
   int kry = h->o.krylov;
   for (;;) {
+    bool started = false;
     TRY(fine_residual(h, Ud, h->L[0].r, h->fp64,
-                      h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized), 0));
+                      h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized), 0,
+                      kry == 0 ? &started : nullptr));
     TRY(read_scalars(h, 1));
     nrm = std::sqrt(h->hscal[0]);
     rel = nrm / ref;
@@ -1960,7 +2022,7 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
     const bool relin = h->p.reaction != ST_REACTION_NONE && (h->o.newton || !h->linearized);
     bool did_cycle = false;
     if (kry == 0 && (relin || !h->coarse_ready)) {
-      TRY(lin_cycle(h));
+      TRY(lin_cycle(h, started));
       h->linearized = true;
       did_cycle = true;
       ++cycles;
@@ -1977,7 +2039,7 @@ int st_solve(st_handle* h, double* U, st_solve_info* info) {
         break;
       }
     } else if (!did_cycle) {
-      TRY(cycle(h, 0));
+      TRY(cycle(h, 0, started));
       ++cycles;
     }
     launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
@@ -2342,8 +2404,14 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         rp.R = L0.r;
         rp.cbar = rx ? L0.cbar : nullptr;
         rp.cnode = rx ? h->cnode : nullptr;
-        if (h->fp64) launch_residual(h->D, 1, 1, rp, st);
-        else launch_residual_ff(h->D, rp, st);
+        if (h->fp64) {
+          launch_residual(h->D, 1, 1, rp, st);
+        } else {
+          // as the step runs it: with the first smoothing step where it applies
+          SmoothStart ss{};
+          const bool stt = start_possible(h) && ((ss = smooth_start(h)), residual_start_ok(h->D, rp, &ss));
+          launch_residual_ff(h->D, rp, st, stt ? &ss : nullptr);
+        }
         CKL();
         return ST_OK;
       }
@@ -2439,7 +2507,17 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     }
   };
   switch (which) {
-    case ST_KERNEL_FINE_RESIDUAL: bytes = D * (8 + es) + (rx ? planes * es : 0); break;
+    case ST_KERNEL_FINE_RESIDUAL: {
+      bytes = D * (8 + es) + (rx ? planes * es : 0);
+      if (!h->fp64 && start_possible(h)) {
+        ResidParams rp = fine_params(h, U, 0);
+        rp.R = L0.r;
+        rp.cbar = rx ? L0.cbar : nullptr;
+        const SmoothStart ss = smooth_start(h);
+        if (residual_start_ok(h->D, rp, &ss)) bytes += 2 * D * es;  // y and z
+      }
+      break;
+    }
     case ST_KERNEL_LEVEL_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_JACOBI: bytes = D * 4 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_JACOBI_PLAIN: bytes = D * 3 * es + (rx ? planes * es : 0); break;
@@ -2499,16 +2577,19 @@ int st_stats(st_handle* h, st_stats_info* out) {
   PdlScope pdl_scope(h);
   if (!h || !out) return ST_ERR_INVALID_ARG;
   out->levels = (int)h->L.size();
-  // the relinearise + cycle graph replaces both when it has been built
-  out->cycle_graph_nodes = (int)(h->gexec[3] ? h->gnodes[3] : h->gnodes[0]);
-  out->linearize_graph_nodes = (int)(h->gexec[3] ? 0 : h->gnodes[2]);
+  // the relinearise + cycle graph replaces both when it has been built; the
+  // variants after a fine residual that did the first smoothing step (5, 6)
+  // replace the plain ones (0, 3) when they have been built
+  const int gc = h->gexec[5] ? 5 : 0, glc = h->gexec[6] ? 6 : 3;
+  out->cycle_graph_nodes = (int)(h->gexec[glc] ? h->gnodes[glc] : h->gnodes[gc]);
+  out->linearize_graph_nodes = (int)(h->gexec[glc] ? 0 : h->gnodes[2]);
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   // fine residual + partial sum + update, plus the graph(s) of one st_vcycle
   // (the linearise + cycle graph holds a few event nodes besides its kernels)
-  if (rx && h->o.newton && h->gexec[3])
-    out->launches_per_vcycle = 3 + (int)h->gnodes[3];
+  if (rx && h->o.newton && h->gexec[glc])
+    out->launches_per_vcycle = 3 + (int)h->gnodes[glc];
   else
-    out->launches_per_vcycle = 3 + (int)h->gnodes[0] + ((rx && h->o.newton) ? (int)h->gnodes[2] : 0);
+    out->launches_per_vcycle = 3 + (int)h->gnodes[gc] + ((rx && h->o.newton) ? (int)h->gnodes[2] : 0);
   return ST_OK;
 }
 

@@ -359,6 +359,23 @@ __device__ __forceinline__ void jac_cplx(float yr, float yi, float zr, float zi,
   outi = fmaf(fmaf(ri, dr, __fmul_rn(-rr, di)), inv, zi);
 }
 
+// The zero-start damped Jacobi iterate z = omega D^-1 y of the shifted slab
+// systems at one point (the first sweep from e = 0), roundings spelt out as
+// in jac_real / jac_cplx: every kernel that forms it (the level residuals and
+// the fine residual's smoothing start) gives the same bits.
+__device__ __forceinline__ void jac_zero(float yr, float yi, bool cplx, float sr, float si, float dg, float omega,
+                                         float& zr, float& zi) {
+  if (!cplx) {
+    zr = jdiv(__fmul_rn(omega, yr), fmaf(-sr, dg, 1.f));
+    zi = 0.f;
+  } else {
+    const float dr = fmaf(-sr, dg, 1.f), di = __fmul_rn(-si, dg);
+    const float inv = jdiv(omega, fmaf(dr, dr, __fmul_rn(di, di)));
+    zr = __fmul_rn(fmaf(yr, dr, __fmul_rn(yi, di)), inv);
+    zi = __fmul_rn(fmaf(yi, dr, __fmul_rn(-yr, di)), inv);
+  }
+}
+
 struct ResidParams {
   GridP g;
   int Nt, M, chunk, nchunks;
@@ -388,6 +405,20 @@ template <typename T>
 struct Shifts {
   int kind[MAXM];
   T sr[MAXM], si[MAXM];
+};
+
+// Optional second output of the FP32 fine residual: the first step of the
+// cycle's first level-0 smoothing, which starts from e = 0 (so its level
+// residual is r itself): the Q-eigenbasis transform y = F r per point and
+// the zero-start Jacobi iterate z of the shifted slab systems, with the
+// same arithmetic as the level-residual kernels.
+struct SmoothStart {
+  float* y;             // [Nt][M][Ns]
+  float* z;             // [Nt][M][Ns]
+  float F[MAXM][MAXM];  // forward transform to the Q eigenbasis
+  Shifts<float> sh;
+  float k2;             // diagonal coefficient of the level-0 stencil
+  float omega;          // Jacobi weight
 };
 
 // Level operator A_l e - C e of the cycle (cycle precision T).

@@ -99,8 +99,11 @@ long long residual_blocks(const ResidParams& p);
 long long residual_ff_blocks(int D, const ResidParams& p);
 long long gradient_blocks(const ResidParams& p);
 void launch_residual(int D, int r_fp64, int c_fp64, const ResidParams& p, cudaStream_t st);
-// double-float variant (float residual and cbar outputs)
-void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st);
+// double-float variant (float residual and cbar outputs); with ss it also
+// writes the cycle's smoothing start where the tiled kernel applies
+// (residual_start_ok) and ignores ss elsewhere
+void launch_residual_ff(int D, const ResidParams& p, cudaStream_t st, const SmoothStart* ss = nullptr);
+bool residual_start_ok(int D, const ResidParams& p, const SmoothStart* ss);
 void launch_adj_residual(int D, int r_fp64, const ResidParams& p, cudaStream_t st);
 void launch_gradients(int D, const ResidParams& p, double* partial2, double* du0, cudaStream_t st);
 void launch_sum_partials(const double* part, long long n, double* out, cudaStream_t st);

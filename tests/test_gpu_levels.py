@@ -290,3 +290,35 @@ def test_two_sweep_kernel_same_bits(case, adjoint):
         outs.append(torch.cat([e1.reshape(-1), e2.reshape(-1)]).cpu())
         S.close()
     assert torch.equal(outs[0], outs[1])
+
+
+# a 2D periodic case in whole 64 x 16 tiles whose level 0 has inner levels
+# (the fine residual's smoothing start applies), beside the two square ones
+TILED_START = Case("tiled_start_m5", (128, 64), P_, 1e-2, 6, 5, reaction=space.LOGISTIC, rho=1.0, u0_kind="noise",
+                   seed=23)
+
+
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+def test_fine_residual_smoothing_start_same_bits(case):
+    """The fine residual doing the first step of the cycle's first level-0
+    smoothing (y = F r and the zero-start iterate, from e = 0) against the
+    cycle doing it: two whole outer steps (residual, relinearisation, FP32
+    V-cycle, update of U) give the same bits, and the started cycle has one
+    launch fewer."""
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    U0 = stgen.random_field((p.Nt, p.M, p.Ns), 11, 0.3) + 0.4
+    outs, norms, launches = [], [], []
+    for fuse in (1, 0):
+        S = case.solver(precision=stlib.FP32_REFINE, fuse_start=fuse)
+        U = torch.tensor(U0, device="cuda").reshape(S.field_shape)
+        n1 = S.vcycle(U)
+        n2 = S.vcycle(U)
+        torch.cuda.synchronize()
+        outs.append(U.reshape(-1).cpu())
+        norms.append((n1, n2))
+        launches.append(S.stats()["launches_per_vcycle"])
+        S.close()
+    assert torch.equal(outs[0], outs[1])
+    assert norms[0] == norms[1]
+    assert launches[0] == launches[1] - 1, launches
