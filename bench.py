@@ -83,7 +83,7 @@ HBM_DATASHEET_GBS = 7900.0  # GB300 HBM3e, vendor figure (context beside the mea
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
                  ("prolong_add", 7), ("slab_jacobi_plain", 8), ("update", 9), ("two_sweeps", 10),
-                 ("vcycle_graph", 4))
+                 ("resid_restrict", 11), ("vcycle_graph", 4))
 
 
 def reduce_max(x, dist, device):
@@ -169,10 +169,10 @@ class ClockSampler:
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.66 MB read + 476.56 MB written per launch
+    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.67 MB read + 476.37 MB written per launch
     "k_sweep2<5, 8>": {"file": "k_sweep2.cu",
-                       "sha256": "d174c4582bab082492269c82e8f9026abd5e829ed2add06516e6f8f24b711c8d",
-                       "dram_bytes_per_dof": (1610664192 + 476563712) / 125829120},
+                       "sha256": "9d5e74981ad5155ceb5453161074ef6fc42ad5b5a79988b34bbaed412c473f49",
+                       "dram_bytes_per_dof": (1610669312 + 476370688) / 125829120},
 }
 
 

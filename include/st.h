@@ -177,6 +177,13 @@ typedef struct {
                            e = 0: y = F r and the zero-start Jacobi iterate),
                            which the cycle then skips (same arithmetic); 0:
                            the cycle does that step itself */
+  int fuse_restrict;    /* 1 (default): the forward level residual of the
+                           coarse-grid correction and its full weighting onto
+                           the next grid run as one kernel where both space
+                           axes are halved (2D periodic, whole 64 x 16 fine
+                           tiles, M = 3 or 5, FP32, cbar operator): the fine
+                           residual stays in shared memory (same arithmetic);
+                           0: two launches */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -436,7 +443,8 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e);
  * ------------------------------------------------------------------- */
 
 enum {
-  ST_KERNEL_FINE_RESIDUAL = 0, /* FP64 residual G(U) -> cycle precision + cbar */
+  ST_KERNEL_FINE_RESIDUAL = 0, /* FP64 residual G(U) -> cycle precision + cbar (+ the cycle's
+                                  first smoothing step where fuse_start applies, as st_vcycle) */
   ST_KERNEL_LEVEL_RESIDUAL = 1,/* level-0 residual r - A e + C e with the Q-eigenbasis transform */
   ST_KERNEL_JACOBI = 2,        /* level-0 Jacobi sweep of the shifted slab systems fused with the
                                   back-transform and damped update of e (the cycle's last sweep) */
@@ -450,9 +458,12 @@ enum {
   ST_KERNEL_UPDATE = 9,           /* the defect-correction update U += alpha e in FP64, run with
                                      alpha = 0: the update's traffic (U and e read, U written)
                                      with U's values left unchanged */
-  ST_KERNEL_SWEEP2 = 10           /* the last two level-0 Jacobi sweeps of a slab solve as one
+  ST_KERNEL_SWEEP2 = 10,          /* the last two level-0 Jacobi sweeps of a slab solve as one
                                      kernel, the second fused with the back-transform and update
                                      of e (ST_ERR_UNSUPPORTED where that kernel does not apply) */
+  ST_KERNEL_RESID_RESTRICT = 11   /* the level-0 residual r - A e + C e fused with its full
+                                     weighting onto level 1 (ST_ERR_UNSUPPORTED where that kernel
+                                     does not apply) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream

@@ -25,7 +25,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["k_fine.cu", "k_fine_tile.cu", "k_level.cu", "k_level4.cu", "k_coarse.cu", "k_krylov.cu", "k_tma.cu", "st_api.cu",
               "st_noalloc.cu", "st_checkpoint.cu",
-              "k_sweep2.cu"]
+              "k_sweep2.cu", "k_linres_restrict.cu"]
 CPP_SOURCES = ["st_setup.cpp"]
 HEADERS = ["st_internal.cuh", "st_kernels.cuh", "st_setup.h"]
 

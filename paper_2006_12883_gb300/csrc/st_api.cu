@@ -898,6 +898,21 @@ int coarse_solve(st_handle* h, int adj, const void* r, void* e, cudaStream_t st)
   return ST_OK;
 }
 
+// The level residual and its restriction onto level l + 1 as one kernel
+// (launch_linres_restrict) where it applies; false: the caller runs both.
+template <typename T>
+bool residual_restrict_fused(st_handle* h, int l, int adj, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    Level& Lv = h->L[l];
+    if (adj || !h->o.fuse_restrict || Lv.next != 1) return false;
+    LinParams<float> lp = lin_params<float>(h, Lv, 0);
+    lp.e = (const float*)Lv.e;
+    lp.r = (const float*)Lv.r;
+    return launch_linres_restrict(h->D, lp, h->L[l + 1].g, (float*)h->L[l + 1].r, st);
+  }
+  return false;
+}
+
 template <typename T>
 int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   Level& Lv = h->L[l];
@@ -908,8 +923,10 @@ int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   const long long n = Lv.g.Ns * Lv.Nt * Lv.M;
   if (nu1 == 0) CK(cudaMemsetAsync(Lv.e, 0, n * h->esz, st));
   for (int i = 0; i < nu1; ++i) TRY(smooth<T>(h, l, adj, i == 0, st));
-  TRY(level_residual<T>(h, l, adj, Lv.e, Lv.r, Lv.in[0].y, 0, st));
-  TRY(restrict_level<T>(h, l, adj, Lv.in[0].y, h->L[l + 1].r, st));
+  if (!residual_restrict_fused<T>(h, l, adj, st)) {
+    TRY(level_residual<T>(h, l, adj, Lv.e, Lv.r, Lv.in[0].y, 0, st));
+    TRY(restrict_level<T>(h, l, adj, Lv.in[0].y, h->L[l + 1].r, st));
+  }
   TRY(vcycle_level<T>(h, l + 1, adj, st));
   const Level& Lc = h->L[l + 1];
   TRY(prolong_level<T>(h, l, adj, (!adj && Lc.fused) ? Lc.e2 : Lc.e, Lv.e, st));
@@ -1608,6 +1625,7 @@ void st_default_opts(st_solver_opts* o) {
   o->recompute_slabs = 0;
   o->fuse_sweeps = 1;
   o->fuse_start = 1;
+  o->fuse_restrict = 1;
 }
 
 const char* st_status_str(int s) {
@@ -1721,6 +1739,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
   // levels and buffers
   slab_smooth_prepare();
   sweep2_prepare();
+  linres_restrict_prepare();
   h->L.resize(pl.size());
   for (size_t l = 0; l < pl.size(); ++l) {
     Level& Lv = h->L[l];
@@ -2385,7 +2404,7 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
   PdlScope pdl_scope(h);
-  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_SWEEP2) return ST_ERR_INVALID_ARG;
+  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_RESID_RESTRICT) return ST_ERR_INVALID_ARG;
   if (which >= ST_KERNEL_SHIFTED_RESIDUAL && which <= ST_KERNEL_PROLONG && h->L[0].in.size() < 2)
     return ST_ERR_UNSUPPORTED;
   if ((which == ST_KERNEL_FINE_RESIDUAL || which == ST_KERNEL_UPDATE) && (!U || !is_device_ptr(U)))
@@ -2496,6 +2515,10 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         CKL();
         return ST_OK;
       }
+      case ST_KERNEL_RESID_RESTRICT:
+        if (h->fp64 || h->L.size() < 2 || !residual_restrict_fused<float>(h, 0, 0, st)) return ST_ERR_UNSUPPORTED;
+        CKL();
+        return ST_OK;
       case ST_KERNEL_UPDATE:
         // U + 0 * e with e zeroed above: the loads and stores of the cycle's
         // update, U's values unchanged
@@ -2524,6 +2547,10 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
     case ST_KERNEL_UPDATE: bytes = D * (8 + es + 8); break;
     case ST_KERNEL_SWEEP2: bytes = D * 4 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_RESID_RESTRICT:  // e and r read, the coarse residual written
+      bytes = 2 * D * es + (rx ? planes * es : 0) +
+              (h->L.size() > 1 ? (double)h->L[1].g.Ns * h->L[1].Nt * h->L[1].M * es : 0);
+      break;
     case ST_KERNEL_SHIFTED_RESIDUAL: bytes = D * 3 * es + (rx ? planes * es : 0); break;
     case ST_KERNEL_INNER_RESTRICT: {
       const double Dc = (double)L0.in[1].g.Ns * L0.Nt * h->p.M;

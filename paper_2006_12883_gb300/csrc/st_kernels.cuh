@@ -132,6 +132,12 @@ void slab_smooth_prepare();
 // kernel on 2D periodic grids in whole 64 x 8 tiles, M = 3 or 5; false where
 // it does not apply.  p is the first sweep's parameter block (z in).
 void sweep2_prepare();
+// k_linres_restrict.cu: the forward level residual r - A e + C e (FP32,
+// cbar, no exact Jacobian) fused with the full weighting onto gc (2D
+// periodic, both axes halved, whole 64 x 16 fine tiles, M = 3 or 5) into
+// coarse; false where it does not apply.
+void linres_restrict_prepare();
+bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st);
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st);
 template <typename T> bool slab_smooth_fits(int M, long long Ns);
 template <typename T>

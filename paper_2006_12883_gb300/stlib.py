@@ -44,7 +44,8 @@ class StSolverOpts(ctypes.Structure):
                 ("krylov_fallback", c_int), ("pfasst_levels", c_int), ("pfasst_coarse_M", c_int),
                 ("pfasst_sweeps", c_int), ("use_tma", c_int), ("recompute_slabs", c_int),
                 ("fuse_sweeps", c_int),
-                ("fuse_start", c_int)]
+                ("fuse_start", c_int),
+                ("fuse_restrict", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)

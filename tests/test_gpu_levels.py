@@ -322,3 +322,29 @@ def test_fine_residual_smoothing_start_same_bits(case):
     assert torch.equal(outs[0], outs[1])
     assert norms[0] == norms[1]
     assert launches[0] == launches[1] - 1, launches
+
+
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+def test_residual_restriction_kernel_same_bits(case):
+    """The level residual of the coarse-grid correction fused with its full
+    weighting onto the next grid (the fine residual kept in shared memory)
+    against the two launches: two outer steps and a level V-cycle give the
+    same bits, and the fused cycle has fewer launches."""
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    U0 = stgen.random_field((p.Nt, p.M, p.Ns), 12, 0.3) + 0.4
+    outs, launches = [], []
+    for fuse in (1, 0):
+        S = case.solver(precision=stlib.FP32_REFINE, fuse_restrict=fuse)
+        U = torch.tensor(U0, device="cuda").reshape(S.field_shape)
+        S.vcycle(U)
+        S.vcycle(U)
+        r = torch.tensor(stgen.random_field(S.level_shape(0), 702), dtype=S.cycle_dtype, device="cuda")
+        e = S.level_vcycle(r)
+        torch.cuda.synchronize()
+        outs.append((U.reshape(-1).cpu(), e.reshape(-1).cpu()))
+        launches.append(S.stats()["launches_per_vcycle"])
+        S.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
+    assert launches[0] < launches[1], launches
