@@ -169,10 +169,11 @@ class ClockSampler:
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.67 MB read + 476.37 MB written per launch
+    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.80 MB read + 476.43 MB written per launch
+    # (the probe's two timed launches)
     "k_sweep2<5, 8>": {"file": "k_sweep2.cu",
-                       "sha256": "9d5e74981ad5155ceb5453161074ef6fc42ad5b5a79988b34bbaed412c473f49",
-                       "dram_bytes_per_dof": (1610669312 + 476370688) / 125829120},
+                       "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
+                       "dram_bytes_per_dof": (1610932736 + 476420864 + 1610664448 + 476431104) / 2 / 125829120},
 }
 
 

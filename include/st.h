@@ -184,6 +184,13 @@ typedef struct {
                            tiles, M = 3 or 5, FP32, cbar operator): the fine
                            residual stays in shared memory (same arithmetic);
                            0: two launches */
+  int fuse_update;      /* 1 (default): in st_vcycle, where the smoothing
+                           start applies, the last two-sweep kernel of the
+                           cycle's level-0 post-smoothing also does the update
+                           U += e (same arithmetic; U 16-byte aligned), and the
+                           separate update launch is skipped; 0: the update
+                           is its own launch.  st_solve keeps its own launch
+                           (its line search reuses e). */
 } st_solver_opts;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc must
@@ -489,6 +496,8 @@ typedef struct {
   int cycle_graph_nodes;        /* kernel + memset nodes of one V-cycle */
   int linearize_graph_nodes;    /* nodes of one relinearisation */
   int launches_per_vcycle;      /* all launches of one st_vcycle call */
+  int update_in_cycle;          /* 1: the last st_vcycle's update of U ran inside
+                                   its cycle (fuse_update), 0: as its own launch */
 } st_stats_info;
 
 /* Launch counts of the captured graphs (0 before the first st_vcycle). */

@@ -111,7 +111,20 @@ __device__ __forceinline__ void group_operands(const float* zc, const float* zu,
 template <int kH>
 __host__ __device__ constexpr int sweep2_threads() { return (kH + 2) * 16; }
 
-template <int M, int kH>
+// The update U += e' of the defect correction from the float e' of the
+// tile's points, as k_update4 does it (float to double by bit
+// manipulation, one FP64 add).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+  const unsigned hi = (ex == 0u) ? sign : sign | ((ex == 0xffu ? 0x7ffu : ex + 896u) << 20) | (man >> 3);
+  const unsigned lo = (ex == 0u) ? 0u : (man << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// UPD: the epilogue also adds e' to the FP64 iterate (*p.Uslot) and writes e
+// only if p.write_e: the step's update of U done by the cycle's last kernel.
+template <int M, int kH, bool UPD>
 __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<float> p) {
   grid_dep_wait();
   constexpr int kZR = kH + 4, kYR = kH + 2, kThreads = sweep2_threads<kH>();
@@ -233,10 +246,49 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
         for (int b = 0; b < M; ++b) acc = fmaf(p.B[a][b], out[b][q], acc);
         ev[q] = fmaf(p.omega_bt, acc, ev[q]);
       }
-      *reinterpret_cast<float4*>(p.e + own + a * Ns) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+      if constexpr (UPD) {
+        // e' to shared memory over z (not read since the first sweep)
+        *reinterpret_cast<float4*>(&S.z[0][0][0] + (a * kH + ty) * kW + 4 * tx) =
+            make_float4(ev[0], ev[1], ev[2], ev[3]);
+      } else {
+        *reinterpret_cast<float4*>(p.e + own + a * Ns) = make_float4(ev[0], ev[1], ev[2], ev[3]);
+      }
+    }
+  }
+  if constexpr (UPD) {
+    // U += e' on the tile: every thread, two points per item, the loads of U
+    // of all its items issued first
+    __syncthreads();
+    double* __restrict__ U = *p.Uslot;
+    constexpr int kItems = M * kH * (kW / 2), kPer = (kItems + kThreads - 1) / kThreads;
+    double2 u[kPer];
+    long long off[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int it = tid + j * kThreads;
+      off[j] = 0;
+      if (it < kItems) {
+        const int a = it / (kH * (kW / 2)), rem = it - a * (kH * (kW / 2)), r = rem / (kW / 2), c2 = rem - r * (kW / 2);
+        off[j] = base + (long long)a * Ns + row(r) + i0 + 2 * c2;
+        u[j] = *reinterpret_cast<const double2*>(U + off[j]);
+      }
+    }
+    const float* et = &S.z[0][0][0];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int it = tid + j * kThreads;
+      if (it < kItems) {
+        const float2 ev = *reinterpret_cast<const float2*>(et + 2 * it);
+        u[j].x += f2d(ev.x);
+        u[j].y += f2d(ev.y);
+        *reinterpret_cast<double2*>(U + off[j]) = u[j];
+        if (p.write_e) *reinterpret_cast<float2*>(p.e + off[j]) = ev;
+      }
     }
   }
 }
+
+__global__ void k_set_uslot(double** slot, double* U) { *slot = U; }
 
 int g_sweep2_ready = 0;  // 1 once the shared-memory opt-in is set
 
@@ -245,10 +297,14 @@ int g_sweep2_ready = 0;  // 1 once the shared-memory opt-in is set
 void sweep2_prepare() {
   static std::once_flag once;
   std::call_once(once, [] {
-    bool ok = cudaFuncSetAttribute(k_sweep2<3, kTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(Sweep2Smem<3, kTH>)) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_sweep2<5, kTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(Sweep2Smem<5, kTH>)) == cudaSuccess;
+    bool ok = true;
+    auto opt_in = [&ok](auto kernel, size_t bytes) {
+      ok = ok && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+    };
+    opt_in(k_sweep2<3, kTH, false>, sizeof(Sweep2Smem<3, kTH>));
+    opt_in(k_sweep2<3, kTH, true>, sizeof(Sweep2Smem<3, kTH>));
+    opt_in(k_sweep2<5, kTH, false>, sizeof(Sweep2Smem<5, kTH>));
+    opt_in(k_sweep2<5, kTH, true>, sizeof(Sweep2Smem<5, kTH>));
     cudaGetLastError();  // without the opt-in the two sweeps stay separate launches
     g_sweep2_ready = ok ? 1 : 0;
   });
@@ -265,9 +321,19 @@ bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st) {
   const long long nb = (long long)(p.g.n0 / kW) * (p.g.n1 / kTH) * p.Nt;
   if (nb >= 0x7fffffffLL) return false;
   constexpr int nt = sweep2_threads<kTH>();
-  if (p.P == 3) st_launch(k_sweep2<3, kTH>, (unsigned)nb, nt, sizeof(Sweep2Smem<3, kTH>), st, p);
-  else st_launch(k_sweep2<5, kTH>, (unsigned)nb, nt, sizeof(Sweep2Smem<5, kTH>), st, p);
+  const bool upd = p.Uslot != nullptr;
+  if (p.P == 3) {
+    if (upd) st_launch(k_sweep2<3, kTH, true>, (unsigned)nb, nt, sizeof(Sweep2Smem<3, kTH>), st, p);
+    else st_launch(k_sweep2<3, kTH, false>, (unsigned)nb, nt, sizeof(Sweep2Smem<3, kTH>), st, p);
+  } else {
+    if (upd) st_launch(k_sweep2<5, kTH, true>, (unsigned)nb, nt, sizeof(Sweep2Smem<5, kTH>), st, p);
+    else st_launch(k_sweep2<5, kTH, false>, (unsigned)nb, nt, sizeof(Sweep2Smem<5, kTH>), st, p);
+  }
   return true;
 }
+
+// a plain launch (no programmatic serialisation): the cycle that reads the
+// slot follows it in stream order
+void launch_set_uslot(double** slot, double* U, cudaStream_t st) { k_set_uslot<<<1, 1, 0, st>>>(slot, U); }
 
 }  // namespace st

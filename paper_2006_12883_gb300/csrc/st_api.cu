@@ -387,7 +387,8 @@ struct st_handle {
   std::vector<Alloc> allocs;
   // graphs: 0 forward cycle, 1 adjoint cycle, 2 linearisation, 3 linearisation + cycle, 4 PFASST iteration,
   // 5 and 6: 0 and 3 after a fine residual that did the first smoothing step
-  static constexpr int kGraphs = 7;
+  // 7 and 8: 5 and 6 whose last level-0 smoothing step also updates U
+  static constexpr int kGraphs = 9;
   cudaGraphExec_t gexec[kGraphs] = {};
   size_t gnodes[kGraphs] = {};
   // second capture stream and events of the linearise + cycle graph: the
@@ -399,6 +400,14 @@ struct st_handle {
   // set while a forward cycle is enqueued whose first level-0 smoothing
   // starts from the y and z the fine residual wrote (SmoothStart)
   bool start_ready = false;
+  // the update U += e fused into the cycle's last level-0 smoothing step:
+  // device slot holding U's address, set before each such cycle; set while
+  // such a cycle is enqueued / its last level-0 smoothing step is; set by
+  // the step that did the update; per graph, whether its capture did
+  double** Uslot = nullptr;
+  bool upd_capture = false, upd_target = false, upd_applied = false;
+  bool gupd[kGraphs] = {};
+  bool last_update_in_cycle = false;  // for st_stats
   int nt_override = 0;     // > 0: inner solves act on this many slabs from the first
   int* tma_err = nullptr;   // device count of expired TMA waits (this device's copy)
   int tma_seen = 0;         // the count this handle has reported
@@ -568,6 +577,8 @@ InnerParams<T> inner_params(st_handle* h, Level& Lv, int k, int P, const Shifts<
   ip.e_zero = 0;
   ip.omega_bt = (T)0;
   ip.e = nullptr;
+  ip.Uslot = nullptr;
+  ip.write_e = 1;
   for (int a2 = 0; a2 < MAXM; ++a2)
     for (int b = 0; b < MAXM; ++b) ip.B[a2][b] = (T)0;
   ip.cbar = use_cbar ? (const T*)I.cbar : nullptr;
@@ -590,6 +601,8 @@ struct BtFuse {
   T omega = 0;
   T B[MAXM][MAXM];
   T* e = nullptr;
+  // the two-sweep kernel also adds e' to U (*Uslot) and leaves e unwritten
+  double* const* Uslot = nullptr;
 };
 
 template <typename T>
@@ -598,6 +611,8 @@ void apply_fuse(InnerParams<T>& ip, const BtFuse<T>& f) {
   ip.e_zero = f.e_zero;
   ip.omega_bt = f.omega;
   ip.e = f.e;
+  ip.Uslot = f.Uslot;
+  ip.write_e = f.Uslot ? 0 : 1;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) ip.B[a][b] = f.B[a][b];
 }
@@ -641,6 +656,7 @@ int inner_vcycle(st_handle* h, Level& Lv, int k, int depth, int sweeps, int P, c
         apply_fuse(ip, *fuse);
         if (launch_sweep2(h->D, ip, st)) {
           CKL();
+          if (ip.Uslot) h->upd_applied = true;
           return ST_OK;
         }
         // not applicable here: the two sweeps run as separate launches
@@ -814,6 +830,8 @@ int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
   f.e = (T*)Lv.e;
   for (int a = 0; a < MAXM; ++a)
     for (int b = 0; b < MAXM; ++b) f.B[a][b] = (T)(adj ? Lv.ns->Ba[a][b] : Lv.ns->Bf[a][b]);
+  // the cycle's last level-0 smoothing step may also do the update of U
+  if (l == 0 && !adj && !e_zero && h->upd_target) f.Uslot = h->Uslot;
   TRY(inner_solve<T>(h, Lv, Lv.smooth_depth, Lv.smooth_sweeps, M, level_shifts<T>(*Lv.ns, Lv.dt), use_cbar,
                      h->o.inner_cycles, multi, &f, st));
   return ST_OK;
@@ -930,7 +948,12 @@ int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   TRY(vcycle_level<T>(h, l + 1, adj, st));
   const Level& Lc = h->L[l + 1];
   TRY(prolong_level<T>(h, l, adj, (!adj && Lc.fused) ? Lc.e2 : Lc.e, Lv.e, st));
-  for (int i = 0; i < nu2; ++i) TRY(smooth<T>(h, l, adj, false, st));
+  for (int i = 0; i < nu2; ++i) {
+    h->upd_target = l == 0 && !adj && h->upd_capture && i == nu2 - 1;
+    const int s = smooth<T>(h, l, adj, false, st);
+    h->upd_target = false;
+    TRY(s);
+  }
   return ST_OK;
 }
 
@@ -978,7 +1001,9 @@ int enqueue_linearize(st_handle* h, cudaStream_t st, cudaEvent_t* ev = nullptr) 
 }
 
 int run_graph(st_handle* h, int which, int (*enq)(st_handle*, cudaStream_t)) {
+  h->upd_applied = false;
   if (!h->o.use_graphs) return enq(h, h->stream);
+  if (h->gexec[which]) h->upd_applied = h->gupd[which];
   if (!h->gexec[which]) {
     // make sure the capture stream sees all prior work of the user stream
     CK(cudaStreamSynchronize(h->stream));
@@ -1004,6 +1029,7 @@ int run_graph(st_handle* h, int which, int (*enq)(st_handle*, cudaStream_t)) {
       return ST_ERR_CUDA;
     }
     h->gexec[which] = ex;
+    h->gupd[which] = h->upd_applied;
   }
   CK(cudaGraphLaunch(h->gexec[which], h->stream));
   return ST_OK;
@@ -1044,22 +1070,39 @@ int enq_lin_cycle_started(st_handle* h, cudaStream_t st) {
   return s;
 }
 
-// `started`: the fine residual just did the first smoothing step (fine_residual)
-int cycle(st_handle* h, int adj, bool started = false) {
+// ... whose last level-0 smoothing step also adds e to U (*h->Uslot)
+int enq_cycle_started_upd(st_handle* h, cudaStream_t st) {
+  h->upd_capture = true;
+  const int s = enq_cycle_started(h, st);
+  h->upd_capture = false;
+  return s;
+}
+int enq_lin_cycle_started_upd(st_handle* h, cudaStream_t st) {
+  h->upd_capture = true;
+  const int s = enq_lin_cycle_started(h, st);
+  h->upd_capture = false;
+  return s;
+}
+
+// `started`: the fine residual just did the first smoothing step
+// (fine_residual); `upd`: the cycle may also do the update U += e, with U's
+// address in h->Uslot (launch_set_uslot before it): h->upd_applied then says
+// whether it did (else the caller updates U)
+int cycle(st_handle* h, int adj, bool started = false, bool upd = false) {
   if (h->fp64) return run_graph(h, adj, adj ? enq_cycle_adj<double> : enq_cycle_fwd<double>);
-  if (started && !adj) return run_graph(h, 5, enq_cycle_started);
+  if (started && !adj) return run_graph(h, upd ? 7 : 5, upd ? enq_cycle_started_upd : enq_cycle_started);
   return run_graph(h, adj, adj ? enq_cycle_adj<float> : enq_cycle_fwd<float>);
 }
 
 // relinearise and run one forward cycle as one graph
-int lin_cycle(st_handle* h, bool started = false) {
+int lin_cycle(st_handle* h, bool started = false, bool upd = false) {
   if (!h->o.use_graphs || !h->cap2) {
     TRY(h->fp64 ? run_graph(h, 2, enq_lin<double>) : run_graph(h, 2, enq_lin<float>));
     h->coarse_ready = true;
-    return cycle(h, 0, started);
+    return cycle(h, 0, started, upd);
   }
   if (h->fp64) TRY(run_graph(h, 3, enq_lin_cycle<double>));
-  else if (started) TRY(run_graph(h, 6, enq_lin_cycle_started));
+  else if (started) TRY(run_graph(h, upd ? 8 : 6, upd ? enq_lin_cycle_started_upd : enq_lin_cycle_started));
   else TRY(run_graph(h, 3, enq_lin_cycle<float>));
   h->coarse_ready = true;
   return ST_OK;
@@ -1233,6 +1276,31 @@ void fill_info(st_solve_info* info, int it, int status, double rel, double abs_,
   for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[off + i];
 }
 
+// The (linearise +) cycle and the update U += e of one outer iteration after
+// the fine residual.  Where the fine residual did the first smoothing step
+// and U is 16-byte aligned, the cycle's last level-0 step does the update
+// (fuse_update; e is then not written: nothing reads it before the next
+// cycle overwrites it); otherwise the update is its own launch.
+int cycle_and_update(st_handle* h, double* Ud, bool started, bool relin) {
+  const bool upd = started && h->o.fuse_update && aligned16(Ud);
+  if (upd) {
+    launch_set_uslot(h->Uslot, Ud, h->stream);
+    CKL();
+  }
+  if (relin) {
+    TRY(lin_cycle(h, started, upd));
+    h->linearized = true;
+  } else {
+    TRY(cycle(h, 0, started, upd));
+  }
+  h->last_update_in_cycle = upd && h->upd_applied;
+  if (!h->last_update_in_cycle) {
+    launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
+    CKL();
+  }
+  return ST_OK;
+}
+
 // One outer iteration on device U: residual + cbar, linearise, cycle, update.
 // The squared norm of G(U) is left in scal[0].
 int outer_step(st_handle* h, double* Ud, bool do_cycle) {
@@ -1241,14 +1309,7 @@ int outer_step(st_handle* h, double* Ud, bool do_cycle) {
   bool started = false;
   TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0, do_cycle ? &started : nullptr));
   if (!do_cycle) return ST_OK;
-  if (relin || !h->coarse_ready) {
-    TRY(lin_cycle(h, started));
-    h->linearized = true;
-  } else {
-    TRY(cycle(h, 0, started));
-  }
-  launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
-  CKL();
+  TRY(cycle_and_update(h, Ud, started, relin || !h->coarse_ready));
   return ST_OK;
 }
 
@@ -1267,14 +1328,7 @@ int outer_step_async(st_handle* h, double* Ud, double* norm) {
   TRY(fine_residual(h, Ud, h->L[0].r, h->fp64, relin, 0, &started));
   CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaEventRecord(h->ev_norm, h->stream));
-  if (relin || !h->coarse_ready) {
-    TRY(lin_cycle(h, started));
-    h->linearized = true;
-  } else {
-    TRY(cycle(h, 0, started));
-  }
-  launch_update(h->fp64, Ud, h->L[0].e, h->D_total, h->stream);
-  CKL();
+  TRY(cycle_and_update(h, Ud, started, relin || !h->coarse_ready));
   CK(cudaEventSynchronize(h->ev_norm));
   *norm = std::sqrt(h->hscal[0]);
   // the count copied behind the previous call's cycle has landed (it precedes
@@ -1626,6 +1680,7 @@ void st_default_opts(st_solver_opts* o) {
   o->fuse_sweeps = 1;
   o->fuse_start = 1;
   o->fuse_restrict = 1;
+  o->fuse_update = 1;
 }
 
 const char* st_status_str(int s) {
@@ -1864,6 +1919,7 @@ int st_create(const st_problem* pin, const st_solver_opts* oin, const st_runtime
     s |= alloc_typed(h, &h->partial, h->npartial * sizeof(double));
     s |= alloc_typed(h, &h->partial2, h->npartial * sizeof(double));
     s |= alloc_typed(h, &h->scal, 8 * sizeof(double));
+    s |= alloc_typed(h, &h->Uslot, sizeof(double*));
     s |= alloc_typed(h, &h->u0, Ns * sizeof(double));
     s |= alloc_typed(h, &h->plane, Ns * sizeof(double));
     s |= alloc_typed(h, &h->plane2, Ns * sizeof(double));
@@ -2605,9 +2661,10 @@ int st_stats(st_handle* h, st_stats_info* out) {
   if (!h || !out) return ST_ERR_INVALID_ARG;
   out->levels = (int)h->L.size();
   // the relinearise + cycle graph replaces both when it has been built; the
-  // variants after a fine residual that did the first smoothing step (5, 6)
-  // replace the plain ones (0, 3) when they have been built
-  const int gc = h->gexec[5] ? 5 : 0, glc = h->gexec[6] ? 6 : 3;
+  // variants after a fine residual that did the first smoothing step (5, 6;
+  // 7, 8 with the update) replace the plain ones (0, 3) when built
+  const int gc = h->gexec[7] ? 7 : (h->gexec[5] ? 5 : 0), glc = h->gexec[8] ? 8 : (h->gexec[6] ? 6 : 3);
+  out->update_in_cycle = h->last_update_in_cycle ? 1 : 0;
   out->cycle_graph_nodes = (int)(h->gexec[glc] ? h->gnodes[glc] : h->gnodes[gc]);
   out->linearize_graph_nodes = (int)(h->gexec[glc] ? 0 : h->gnodes[2]);
   const bool rx = h->p.reaction != ST_REACTION_NONE;

@@ -465,6 +465,11 @@ struct InnerParams {
   T B[MAXM][MAXM];
   T omega_bt;
   T* e;
+  // two-sweep kernel only: with Uslot (device memory holding the FP64
+  // iterate's address) the fused epilogue also adds e' to U; write_e = 0
+  // then leaves e itself unwritten
+  double* const* Uslot;
+  int write_e;
 };
 
 }  // namespace st

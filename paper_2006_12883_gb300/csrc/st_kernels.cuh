@@ -139,6 +139,8 @@ void sweep2_prepare();
 void linres_restrict_prepare();
 bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st);
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st);
+// *slot = U on the stream (the address the two-sweep kernel's fused update reads)
+void launch_set_uslot(double** slot, double* U, cudaStream_t st);
 template <typename T> bool slab_smooth_fits(int M, long long Ns);
 template <typename T>
 void launch_slab_smooth(int D, const LinParams<T>& lp, const InnerParams<T>& ip, int sweeps, T* eout,

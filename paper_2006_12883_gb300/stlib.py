@@ -45,7 +45,8 @@ class StSolverOpts(ctypes.Structure):
                 ("pfasst_sweeps", c_int), ("use_tma", c_int), ("recompute_slabs", c_int),
                 ("fuse_sweeps", c_int),
                 ("fuse_start", c_int),
-                ("fuse_restrict", c_int)]
+                ("fuse_restrict", c_int),
+                ("fuse_update", c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -79,7 +80,7 @@ class StLevelInfo(ctypes.Structure):
 
 class StStatsInfo(ctypes.Structure):
     _fields_ = [("levels", c_int), ("cycle_graph_nodes", c_int), ("linearize_graph_nodes", c_int),
-                ("launches_per_vcycle", c_int)]
+                ("launches_per_vcycle", c_int), ("update_in_cycle", c_int)]
 
 
 class StPlanInfo(ctypes.Structure):
@@ -396,7 +397,8 @@ class Solver:
         st = StStatsInfo()
         check(lib().st_stats(self.h, ctypes.byref(st)), "st_stats")
         return dict(levels=st.levels, cycle_graph_nodes=st.cycle_graph_nodes,
-                    linearize_graph_nodes=st.linearize_graph_nodes, launches_per_vcycle=st.launches_per_vcycle)
+                    linearize_graph_nodes=st.linearize_graph_nodes, launches_per_vcycle=st.launches_per_vcycle,
+                    update_in_cycle=st.update_in_cycle)
 
     def wait_selftest(self):
         """Status of st_wait_selftest (ST_ERR_TIMEOUT when a bounded device wait

@@ -348,3 +348,25 @@ def test_residual_restriction_kernel_same_bits(case):
     assert torch.equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][1], outs[1][1])
     assert launches[0] < launches[1], launches
+
+
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+def test_update_in_cycle_same_bits(case):
+    """The defect-correction update U += e done by the cycle's last level-0
+    two-sweep kernel (its epilogue adds e' to U) against the update's own
+    launch: three st_vcycle steps give the same bits and norms."""
+    from paper_2006_12883_gb300 import stlib
+    p = case.problem()
+    U0 = stgen.random_field((p.Nt, p.M, p.Ns), 13, 0.3) + 0.4
+    outs, norms, where = [], [], []
+    for fuse in (1, 0):
+        S = case.solver(precision=stlib.FP32_REFINE, fuse_update=fuse)
+        U = torch.tensor(U0, device="cuda").reshape(S.field_shape)
+        norms.append([S.vcycle(U) for _ in range(3)])
+        torch.cuda.synchronize()
+        outs.append(U.reshape(-1).cpu())
+        where.append(S.stats()["update_in_cycle"])
+        S.close()
+    assert torch.equal(outs[0], outs[1])
+    assert norms[0] == norms[1]
+    assert where == [1, 0], where
