@@ -83,7 +83,7 @@ HBM_DATASHEET_GBS = 7900.0  # GB300 HBM3e, vendor figure (context beside the mea
 KERNEL_PROBES = (("fine_residual_fp64", 0), ("level_residual_transform", 1), ("slab_jacobi", 2),
                  ("backtransform_update", 3), ("shifted_residual", 5), ("inner_restrict", 6),
                  ("prolong_add", 7), ("slab_jacobi_plain", 8), ("update", 9), ("two_sweeps", 10),
-                 ("resid_restrict", 11), ("vcycle_graph", 4))
+                 ("resid_restrict", 11), ("two_sweeps_update", 12), ("vcycle_graph", 4))
 
 
 def reduce_max(x, dist, device):
@@ -564,12 +564,16 @@ def run_ours(args):
     # timed here at level 0 where it moves the most bytes; HBM bound
     d = len(w["grid"])
     two = kernels.get("two_sweeps", {}).get("GBps") is not None
-    k = kernels["two_sweeps"] if two else kernels["slab_jacobi"]
-    kname = f"k_sweep2<{w['M']}, 8>" if two else f"k_inner4<{d}, {w['M']}, 2>"
+    # the step's last launch: with the update of U when the step ran it there
+    upd = two and stats.get("update_in_cycle") == 1 and kernels.get("two_sweeps_update", {}).get("GBps") is not None
+    k = kernels["two_sweeps_update"] if upd else (kernels["two_sweeps"] if two else kernels["slab_jacobi"])
+    kname = (f"k_sweep2<{w['M']}, 8, true>" if upd else f"k_sweep2<{w['M']}, 8>") if two else \
+        f"k_inner4<{d}, {w['M']}, 2>"
     what = ("two Jacobi sweeps of the shifted slab systems in one kernel, the second fused with the back-transform "
             "and update of e" if two else
             "Jacobi sweep of the shifted slab systems fused with the back-transform and update of e")
-    roofline = {"bound": "hbm", "kernel": kname + ": level-0 " + what + " (z, y, e, cbar in, e out)",
+    io = ("z, y, e, cbar and U in, U out (U += e')" if upd else "z, y, e, cbar in, e out")
+    roofline = {"bound": "hbm", "kernel": kname + ": level-0 " + what + (" and of U" if upd else "") + f" ({io})",
                 "achieved": k.get("GBps"), "peak": hbm, "unit": "GB/s",
                 "frac": (k["GBps"] / hbm) if k.get("GBps") else None,
                 "traffic": ncu_traffic(kname, D),

@@ -468,17 +468,22 @@ enum {
   ST_KERNEL_SWEEP2 = 10,          /* the last two level-0 Jacobi sweeps of a slab solve as one
                                      kernel, the second fused with the back-transform and update
                                      of e (ST_ERR_UNSUPPORTED where that kernel does not apply) */
-  ST_KERNEL_RESID_RESTRICT = 11   /* the level-0 residual r - A e + C e fused with its full
+  ST_KERNEL_RESID_RESTRICT = 11,  /* the level-0 residual r - A e + C e fused with its full
                                      weighting onto level 1 (ST_ERR_UNSUPPORTED where that kernel
                                      does not apply) */
+  ST_KERNEL_SWEEP2_UPDATE = 12    /* ST_KERNEL_SWEEP2 as st_vcycle's last launch (fuse_update):
+                                     its epilogue also adds e' to U and does not write e.  U
+                                     (device) is modified: U += e' per launch (ST_ERR_UNSUPPORTED
+                                     where that kernel does not apply) */
 };
 
 /* Launch kernel `which` `iters` times back to back on the handle's stream
  * between two CUDA events (after one untimed launch) and return the mean
  * duration per launch in milliseconds, plus the algorithmic bytes one launch
  * must move (each input read once, each output written once).  U (device,
- * Nt*M*Ns doubles) is the input of ST_KERNEL_FINE_RESIDUAL and the buffer
- * ST_KERNEL_UPDATE rewrites in place (with its own values); the other kernels
+ * Nt*M*Ns doubles) is the input of ST_KERNEL_FINE_RESIDUAL, the buffer
+ * ST_KERNEL_UPDATE rewrites in place (with its own values) and the iterate
+ * ST_KERNEL_SWEEP2_UPDATE adds its correction to; the other kernels
  * run on the handle's level-0 work buffers (contents unspecified). */
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch);

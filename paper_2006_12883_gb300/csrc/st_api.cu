@@ -2460,11 +2460,13 @@ int st_level_vcycle(st_handle* h, int transpose, const void* r, void* e) {
 int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* ms_per_launch,
                    double* bytes_per_launch) {
   PdlScope pdl_scope(h);
-  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_RESID_RESTRICT) return ST_ERR_INVALID_ARG;
+  if (!h || iters < 1 || which < 0 || which > ST_KERNEL_SWEEP2_UPDATE) return ST_ERR_INVALID_ARG;
   if (which >= ST_KERNEL_SHIFTED_RESIDUAL && which <= ST_KERNEL_PROLONG && h->L[0].in.size() < 2)
     return ST_ERR_UNSUPPORTED;
-  if ((which == ST_KERNEL_FINE_RESIDUAL || which == ST_KERNEL_UPDATE) && (!U || !is_device_ptr(U)))
+  if ((which == ST_KERNEL_FINE_RESIDUAL || which == ST_KERNEL_UPDATE || which == ST_KERNEL_SWEEP2_UPDATE) &&
+      (!U || !is_device_ptr(U)))
     return ST_ERR_INVALID_ARG;
+  if (which == ST_KERNEL_SWEEP2_UPDATE && !aligned16(U)) return ST_ERR_UNSUPPORTED;
   Level& L0 = h->L[0];
   const bool rx = h->p.reaction != ST_REACTION_NONE;
   const double D = (double)h->D_total;
@@ -2556,7 +2558,8 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         };
         return h->fp64 ? go(double(0)) : go(float(0));
       }
-      case ST_KERNEL_SWEEP2: {
+      case ST_KERNEL_SWEEP2:
+      case ST_KERNEL_SWEEP2_UPDATE: {
         if (h->fp64) return ST_ERR_UNSUPPORTED;
         InnerParams<float> ip = inner_params<float>(h, L0, 0, h->p.M, level_shifts<float>(*L0.ns, L0.dt), rx);
         BtFuse<float> f;
@@ -2566,6 +2569,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
         f.e = (float*)L0.e;
         for (int a2 = 0; a2 < MAXM; ++a2)
           for (int b = 0; b < MAXM; ++b) f.B[a2][b] = (float)h->fine->Bf[a2][b];
+        if (which == ST_KERNEL_SWEEP2_UPDATE) f.Uslot = h->Uslot;  // set to U before the timing
         apply_fuse(ip, f);
         if (!launch_sweep2(h->D, ip, st)) return ST_ERR_UNSUPPORTED;
         CKL();
@@ -2603,6 +2607,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     case ST_KERNEL_BACKTRANSFORM: bytes = D * 3 * es; break;
     case ST_KERNEL_UPDATE: bytes = D * (8 + es + 8); break;
     case ST_KERNEL_SWEEP2: bytes = D * 4 * es + (rx ? planes * es : 0); break;
+    case ST_KERNEL_SWEEP2_UPDATE: bytes = D * (3 * es + 16) + (rx ? planes * es : 0); break;  // e not written
     case ST_KERNEL_RESID_RESTRICT:  // e and r read, the coarse residual written
       bytes = 2 * D * es + (rx ? planes * es : 0) +
               (h->L.size() > 1 ? (double)h->L[1].g.Ns * h->L[1].Nt * h->L[1].M * es : 0);
@@ -2622,6 +2627,10 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
   }
   // the update runs on a zeroed e, so U + 0 * e == U whatever e held before
   if (which == ST_KERNEL_UPDATE) CK(cudaMemsetAsync(L0.e, 0, (size_t)h->D_total * h->esz, h->stream));
+  if (which == ST_KERNEL_SWEEP2_UPDATE) {
+    launch_set_uslot(h->Uslot, const_cast<double*>(U), h->stream);
+    CKL();
+  }
   TRY(one(h->stream));  // warm (and capture, for the cycle)
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
