@@ -169,11 +169,15 @@ class ClockSampler:
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # k_sweep2<5, 8> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.80 MB read + 476.43 MB written per launch
-    # (the probe's two timed launches)
-    "k_sweep2<5, 8>": {"file": "k_sweep2.cu",
-                       "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
-                       "dram_bytes_per_dof": (1610932736 + 476420864 + 1610664448 + 476431104) / 2 / 125829120},
+    # k_sweep2<5, 8, 0> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.78 MB read + 476.48 MB written per
+    # launch (the probe's two timed launches)
+    "k_sweep2<5, 8, 0>": {"file": "k_sweep2.cu",
+                          "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
+                          "dram_bytes_per_dof": (1610844416 + 476482048 + 1610709504 + 476481024) / 2 / 125829120},
+    # k_sweep2<5, 8, 1> (with the update of U) on the same case: 2617.33 MB read + 970.44 MB written per launch
+    "k_sweep2<5, 8, 1>": {"file": "k_sweep2.cu",
+                          "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
+                          "dram_bytes_per_dof": (2617369600 + 970466304 + 2617298176 + 970422784) / 2 / 125829120},
 }
 
 
@@ -567,8 +571,7 @@ def run_ours(args):
     # the step's last launch: with the update of U when the step ran it there
     upd = two and stats.get("update_in_cycle") == 1 and kernels.get("two_sweeps_update", {}).get("GBps") is not None
     k = kernels["two_sweeps_update"] if upd else (kernels["two_sweeps"] if two else kernels["slab_jacobi"])
-    kname = (f"k_sweep2<{w['M']}, 8, true>" if upd else f"k_sweep2<{w['M']}, 8>") if two else \
-        f"k_inner4<{d}, {w['M']}, 2>"
+    kname = f"k_sweep2<{w['M']}, 8, {1 if upd else 0}>" if two else f"k_inner4<{d}, {w['M']}, 2>"
     what = ("two Jacobi sweeps of the shifted slab systems in one kernel, the second fused with the back-transform "
             "and update of e" if two else
             "Jacobi sweep of the shifted slab systems fused with the back-transform and update of e")

@@ -60,7 +60,7 @@ __device__ __forceinline__ void ldq(const float* s, float (&v)[NQ]) {
 template <int M, int NQ>
 __device__ __forceinline__ void residual_points(const LinParams<float>& p, LRSmem<M>& S, int re, int rr, int c0,
                                                 bool has_cb) {
-  float cb[NQ], acc[M][NQ], t[NQ];
+  float cb[NQ], acc[M][NQ], ec[M][NQ], t[NQ];
   if (has_cb) ldq<NQ>(&S.cb[rr][c0], cb);
   else
 #pragma unroll
@@ -68,14 +68,14 @@ __device__ __forceinline__ void residual_points(const LinParams<float>& p, LRSme
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     ldq<NQ>(&S.r[a][rr][c0], acc[a]);
-    ldq<NQ>(&S.e[a][re][c0], t);
+    ldq<NQ>(&S.e[a][re][c0], ec[a]);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[a][q] = acc[a][q] - t[q];
+    for (int q = 0; q < NQ; ++q) acc[a][q] = acc[a][q] - ec[a][q];
   }
 #pragma unroll
   for (int b = 0; b < M; ++b) {
-    float c[NQ], up[NQ], dn[NQ], Fe[NQ];
-    ldq<NQ>(&S.e[b][re][c0], c);
+    float up[NQ], dn[NQ], Fe[NQ];
+    const float (&c)[NQ] = ec[b];
     ldq<NQ>(&S.e[b][re - 1][c0], up);
     ldq<NQ>(&S.e[b][re + 1][c0], dn);
     float v[NQ + 2];

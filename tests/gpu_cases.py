@@ -85,10 +85,16 @@ STMG1D = Case("stmg1d_heat", (65,), N_, 0.01, 16, 3, u0_kind="cosine", extra=dic
 TILED_SQ3 = Case("tiled_square_m3", (64, 64), P_, 1e-2, 5, 3, reaction=L_, rho=1.0, u0_kind="noise", seed=21)
 TILED_SQ5 = Case("tiled_square_m5", (64, 64), P_, 2e-2, 4, 5, reaction=C_, rho=1.5, u0_kind="noise", seed=22)
 
+# 2D periodic grids whose level 0 runs the fused level-0 kernels (the fine residual with the first smoothing step,
+# the two-sweep kernel with the update of U, the level residual with its restriction): with the logistic
+# reaction at M = 5, and without a reaction term (no cbar) at M = 3
+TILED_LOG5 = Case("tiled_logistic2d_m5", (64, 128), P_, 1e-2, 6, 5, reaction=L_, rho=1.0, u0_kind="noise", seed=25)
+TILED_HEAT3 = Case("tiled_heat2d_m3", (64, 128), P_, 2e-2, 6, 3, u0_kind="noise", seed=24)
+
 RESIDUAL_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, RAGGED, M1, PER2D_M5, PER3D_M5, TILED_M5,
                   TILED_SQ3, TILED_SQ5]
 SOLVE_CASES = [HEAT1D, HEAT_NEU, MONO, LOG2D, CUB3D, DIR2D_M5, M1, PER2D_M5, PER3D_M5, SMMG2D, SMMG1D, STMG2D,
-               STMG1D]
+               STMG1D, TILED_LOG5, TILED_HEAT3]
 
 
 def residual_scale(p: system.Problem, U: np.ndarray) -> float:

@@ -9,7 +9,7 @@ import stgen
 from oracle import multilevel as ml
 from oracle import space, system
 from tests.gpu_cases import (CUB3D, DIR2D_M5, HEAT1D, LOG2D, PER2D_M5, PER3D_M5, RAGGED, SMMG1D, SMMG2D, STMG1D, STMG2D,
-                             TILED_M5, TILED_SQ3, TILED_SQ5,
+                             TILED_HEAT3, TILED_M5, TILED_SQ3, TILED_SQ5,
                              Case)
 
 pytestmark = pytest.mark.gpu
@@ -298,7 +298,7 @@ TILED_START = Case("tiled_start_m5", (128, 64), P_, 1e-2, 6, 5, reaction=space.L
                    seed=23)
 
 
-@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START, TILED_HEAT3], ids=lambda c: c.name)
 def test_fine_residual_smoothing_start_same_bits(case):
     """The fine residual doing the first step of the cycle's first level-0
     smoothing (y = F r and the zero-start iterate, from e = 0) against the
@@ -324,7 +324,7 @@ def test_fine_residual_smoothing_start_same_bits(case):
     assert launches[0] == launches[1] - 1, launches
 
 
-@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START, TILED_HEAT3], ids=lambda c: c.name)
 def test_residual_restriction_kernel_same_bits(case):
     """The level residual of the coarse-grid correction fused with its full
     weighting onto the next grid (the fine residual kept in shared memory)
@@ -350,7 +350,7 @@ def test_residual_restriction_kernel_same_bits(case):
     assert launches[0] < launches[1], launches
 
 
-@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START], ids=lambda c: c.name)
+@pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START, TILED_HEAT3], ids=lambda c: c.name)
 def test_update_in_cycle_same_bits(case):
     """The defect-correction update U += e done by the cycle's last level-0
     two-sweep kernel (its epilogue adds e' to U) against the update's own

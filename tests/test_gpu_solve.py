@@ -9,7 +9,7 @@ import pytest
 import stgen
 from oracle import sdc as osdc
 from oracle import space, system
-from tests.gpu_cases import HEAT1D, LOG2D, MONO, SOLVE_CASES, TILED_M5, Case
+from tests.gpu_cases import HEAT1D, LOG2D, MONO, SOLVE_CASES, TILED_HEAT3, TILED_LOG5, TILED_M5, Case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -33,6 +33,11 @@ def _oracle_solution(case):
 def test_solve_matches_oracle(case, prec):
     from paper_2006_12883_gb300 import stlib
     tol = 1e-12
+    if prec == "fp32" and case in (TILED_LOG5, TILED_HEAT3):
+        # the double-float residual carries a few 1e-14 of its largest term,
+        # here dt nu / h^2 = 27 times |u|: the FP32 path's relative residual
+        # stops near 3e-12 on these grids (the all-FP64 path goes on)
+        tol = 1e-10
     S = case.solver(precision=stlib.FP64 if prec == "fp64" else stlib.FP32_REFINE, tol=tol, max_iters=200)
     U = S.zeros()
     info = S.solve(U)
@@ -45,6 +50,25 @@ def test_solve_matches_oracle(case, prec):
     assert err <= (1e-10 if prec == "fp64" else 1e-8), err
     h = info["history"]
     assert all(b < a for a, b in zip(h[1:], h[2:])), h  # monotone after the first cycle
+    S.close()
+
+
+@pytest.mark.parametrize("case", [TILED_LOG5, TILED_HEAT3], ids=lambda c: c.name)
+def test_vcycle_iteration_matches_oracle(case):
+    """st_vcycle repeated from zero (on these grids every step runs the fine
+    residual with the first smoothing step, the two-sweep kernel that also
+    updates U and the level residual with its restriction) converges to the
+    oracle's collocation solution."""
+    from paper_2006_12883_gb300 import stlib
+    S = case.solver(precision=stlib.FP32_REFINE)
+    U = S.zeros()
+    norms = [S.vcycle(U) for _ in range(25)]
+    assert S.stats()["update_in_cycle"] == 1
+    assert norms[-1] <= 1e-10 * norms[0], norms
+    ref = _oracle_solution(case)
+    err = _rel(U.cpu().numpy().reshape(ref.shape), ref)
+    print(f"\n[oracle] {case.name} st_vcycle x 25: rel 2-norm error {err:.3e}")
+    assert err <= 1e-8, err
     S.close()
 
 
