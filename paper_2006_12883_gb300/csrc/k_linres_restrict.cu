@@ -9,7 +9,11 @@
 // in place of r, and writes the 32 x 8 coarse tile: about 10.6 bytes per fine
 // dof.  The arithmetic is term for term that of k_lin_residual4 and
 // k_restrict4 (k_level4.cu), so the coarse values equal the two-launch
-// sequence's to the bit.
+// sequence's to the bit.  With START the kernel also does the first step of
+// the coarse level's first smoothing, which starts from e = 0 (so its level
+// residual is the restricted residual itself): y = F r and the zero-start
+// Jacobi iterate z on the coarse tile, as the coarse level's residual kernel
+// would.
 #include <mutex>
 
 #include "st_kernels.cuh"
@@ -108,9 +112,11 @@ __device__ __forceinline__ void residual_points(const LinParams<float>& p, LRSme
   }
 }
 
-template <int M>
+template <int M, bool START>
 __global__ void __launch_bounds__(kThreads, M == 3 ? 4 : 3) k_linres_restrict(LinParams<float> p, GridP gc,
-                                                                              float* __restrict__ coarse) {
+                                                                              float* __restrict__ coarse,
+                                                                              SmoothStart ss,
+                                                                              const float* __restrict__ cbarc) {
   grid_dep_wait();
   constexpr int kER = LRSmem<M>::kER, kRR = LRSmem<M>::kRR;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -187,6 +193,53 @@ __global__ void __launch_bounds__(kThreads, M == 3 ? 4 : 3) k_linres_restrict(Li
     }
     *reinterpret_cast<float4*>(coarse + ((long long)n * M + a) * Nc + (long long)(J0 + J) * gc.n0 + I0 + 4 * G) =
         make_float4(acc[0], acc[1], acc[2], acc[3]);
+    if constexpr (START)  // the coarse tile, all planes, for the smoothing start (over cbar and the coupling plane)
+      *reinterpret_cast<float4*>(&S.cb[0][0] + (a * (kFH / 2) + J) * (kFW / 2) + 4 * G) =
+          make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+  if constexpr (START) {
+    __syncthreads();
+    // y = F r per coarse point, then the zero-start iterate of each real
+    // plane and complex pair (k_lin_residual4's arithmetic without e); four
+    // coarse points per item
+    const float* rc = &S.cb[0][0];
+    for (int it = tid; it < (kFH / 2) * (kFW / 8); it += kThreads) {
+      const int J = it >> 3, G = it & 7;
+      const long long pt = (long long)(J0 + J) * gc.n0 + I0 + 4 * G, base_c = (long long)n * M * Nc + pt;
+      float r[M][4], y[M][4], cb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < M; ++b) ld4s(rc + (b * (kFH / 2) + J) * (kFW / 2) + 4 * G, r[b]);
+      if (cbarc) {
+        const float4 c = *reinterpret_cast<const float4*>(cbarc + (long long)n * Nc + pt);
+        cb[0] = c.x; cb[1] = c.y; cb[2] = c.z; cb[3] = c.w;
+      }
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float t = 0.f;
+#pragma unroll
+          for (int b = 0; b < M; ++b) t = fmaf(ss.F[a][b], r[b][q], t);
+          y[a][q] = t;
+        }
+        *reinterpret_cast<float4*>(ss.y + base_c + (long long)a * Nc) = make_float4(y[a][0], y[a][1], y[a][2], y[a][3]);
+      }
+#pragma unroll
+      for (int pl = 0; pl < M; ++pl) {
+        const int kd = ss.sh.kind[pl];
+        if (kd == SH_REAL || kd == SH_RE) {
+          const int pi = pl + 1 < M ? pl + 1 : pl;
+          float zr[4], zi[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            jac_zero(y[pl][q], kd == SH_REAL ? 0.f : y[pi][q], kd != SH_REAL, ss.sh.sr[pl], ss.sh.si[pl],
+                     ss.k2 + cb[q], ss.omega, zr[q], zi[q]);
+          *reinterpret_cast<float4*>(ss.z + base_c + (long long)pl * Nc) = make_float4(zr[0], zr[1], zr[2], zr[3]);
+          if (kd == SH_RE && pl + 1 < M)
+            *reinterpret_cast<float4*>(ss.z + base_c + (long long)pi * Nc) = make_float4(zi[0], zi[1], zi[2], zi[3]);
+        }
+      }
+    }
   }
 }
 
@@ -197,16 +250,22 @@ int g_lr_ready = 0;  // 1 once the shared-memory opt-in is set
 void linres_restrict_prepare() {
   static std::once_flag once;
   std::call_once(once, [] {
-    bool ok = cudaFuncSetAttribute(k_linres_restrict<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)sizeof(LRSmem<3>)) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_linres_restrict<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(LRSmem<5>)) == cudaSuccess;
+    bool ok = true;
+    auto opt_in = [&ok](auto kernel, size_t bytes) {
+      ok = ok && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+    };
+    opt_in(k_linres_restrict<3, false>, sizeof(LRSmem<3>));
+    opt_in(k_linres_restrict<3, true>, sizeof(LRSmem<3>));
+    opt_in(k_linres_restrict<5, false>, sizeof(LRSmem<5>));
+    opt_in(k_linres_restrict<5, true>, sizeof(LRSmem<5>));
     cudaGetLastError();  // without the opt-in the two steps stay separate launches
     g_lr_ready = ok ? 1 : 0;
   });
 }
 
-bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st) {
+bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st,
+                            const SmoothStart* ss, const float* cbarc, bool* started) {
+  if (started) *started = false;
   if (g_lr_ready != 1) return false;
   if (!(D == 2 && (p.M == 3 || p.M == 5) && !p.transpose && !p.transform && p.e && p.r && !p.cnode &&
         p.g.bc == BC_PER && p.g.n0 >= kFW && p.g.n0 % kFW == 0 && p.g.n1 >= kFH && p.g.n1 % kFH == 0 &&
@@ -215,8 +274,22 @@ bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, f
     return false;
   const long long nb = (long long)(p.g.n0 / kFW) * (p.g.n1 / kFH) * p.Nt;
   if (nb >= 0x7fffffffLL) return false;
-  if (p.M == 3) st_launch(k_linres_restrict<3>, (unsigned)nb, kThreads, sizeof(LRSmem<3>), st, p, gc, coarse);
-  else st_launch(k_linres_restrict<5>, (unsigned)nb, kThreads, sizeof(LRSmem<5>), st, p, gc, coarse);
+  const bool start = ss && ss->y && ss->z && aligned16(ss->y) && aligned16(ss->z) && aligned16(cbarc);
+  SmoothStart s{};
+  if (start) s = *ss;
+#define LR(MM)                                                                                            \
+  do {                                                                                                    \
+    if (start)                                                                                            \
+      st_launch(k_linres_restrict<MM, true>, (unsigned)nb, kThreads, sizeof(LRSmem<MM>), st, p, gc, coarse, s, \
+                cbarc);                                                                                   \
+    else                                                                                                  \
+      st_launch(k_linres_restrict<MM, false>, (unsigned)nb, kThreads, sizeof(LRSmem<MM>), st, p, gc, coarse, s, \
+                cbarc);                                                                                   \
+  } while (0)
+  if (p.M == 3) LR(3);
+  else LR(5);
+#undef LR
+  if (started) *started = start;
   return true;
 }
 

@@ -400,6 +400,9 @@ struct st_handle {
   // set while a forward cycle is enqueued whose first level-0 smoothing
   // starts from the y and z the fine residual wrote (SmoothStart)
   bool start_ready = false;
+  // bit l (l >= 1): the kernel that restricted onto level l also did the
+  // first step of its first smoothing (set and used while a cycle is enqueued)
+  unsigned start_mask = 0;
   // the update U += e fused into the cycle's last level-0 smoothing step:
   // device slot holding U's address, set before each such cycle; set while
   // such a cycle is enqueued / its last level-0 smoothing step is; set by
@@ -809,8 +812,11 @@ int smooth(st_handle* h, int l, int adj, bool e_zero, cudaStream_t st) {
     return ST_OK;
   }
   const bool multi = !(Lv.in.size() == 1 && Lv.in[0].g.Ns <= kInnerCoarseLimit);
-  if (l == 0 && !adj && e_zero && h->start_ready) {
-    // the fine residual wrote this step's y = F r and zero-start z
+  const bool started = !adj && e_zero && (l == 0 ? h->start_ready : ((h->start_mask >> l) & 1u) != 0);
+  if (l > 0) h->start_mask &= ~(1u << l);
+  if (started) {
+    // the fine residual (level 0) or the residual-restriction kernel (the
+    // levels below) wrote this step's y = F r and zero-start z
   } else {
     // residual + Q-eigenbasis transform (+ zero-start Jacobi of the slab systems)
     LinParams<T> lp = lin_params<T>(h, Lv, adj);
@@ -916,8 +922,12 @@ int coarse_solve(st_handle* h, int adj, const void* r, void* e, cudaStream_t st)
   return ST_OK;
 }
 
+SmoothStart smooth_start(st_handle* h, int l);
+
 // The level residual and its restriction onto level l + 1 as one kernel
 // (launch_linres_restrict) where it applies; false: the caller runs both.
+// Where level l + 1 smooths with its inner multigrid from e = 0 (fuse_start)
+// the kernel also does that smoothing's first step (start_mask).
 template <typename T>
 bool residual_restrict_fused(st_handle* h, int l, int adj, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
@@ -926,7 +936,24 @@ bool residual_restrict_fused(st_handle* h, int l, int adj, cudaStream_t st) {
     LinParams<float> lp = lin_params<float>(h, Lv, 0);
     lp.e = (const float*)Lv.e;
     lp.r = (const float*)Lv.r;
-    return launch_linres_restrict(h->D, lp, h->L[l + 1].g, (float*)h->L[l + 1].r, st);
+    Level& Lc = h->L[l + 1];
+    const bool want = h->o.fuse_start && h->o.nu1 >= 1 && l + 2 < (int)h->L.size() && !Lc.fused &&
+                      !(Lc.in.size() == 1 && Lc.in[0].g.Ns <= kInnerCoarseLimit);
+    SmoothStart ss{};
+    if (want) {
+      ss = smooth_start(h, l + 1);
+      // the coarse level's cbar is written by the linearisation branch
+      if (h->split_lin && cudaStreamWaitEvent(st, h->ev_lvl[l + 1], 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+    }
+    const float* cbc = h->p.reaction != ST_REACTION_NONE ? (const float*)Lc.cbar : nullptr;
+    bool started = false;
+    if (!launch_linres_restrict(h->D, lp, Lc.g, (float*)Lc.r, st, want ? &ss : nullptr, cbc, &started))
+      return false;
+    if (started) h->start_mask |= 1u << (l + 1);
+    return true;
   }
   return false;
 }
@@ -935,6 +962,7 @@ template <typename T>
 int vcycle_level(st_handle* h, int l, int adj, cudaStream_t st) {
   Level& Lv = h->L[l];
   const int last = (int)h->L.size() - 1;
+  if (l == 0) h->start_mask = 0;
   if (h->split_lin) CK(cudaStreamWaitEvent(st, h->ev_lvl[l == last ? last + 1 : l], 0));
   if (l == last) return coarse_solve<T>(h, adj, Lv.r, Lv.e, st);
   const int nu1 = h->o.nu1, nu2 = h->o.nu2;
@@ -1163,8 +1191,8 @@ bool start_possible(const st_handle* h) {
   return !L0.fused && !(L0.in.size() == 1 && L0.in[0].g.Ns <= kInnerCoarseLimit);
 }
 
-SmoothStart smooth_start(st_handle* h) {
-  Level& L0 = h->L[0];
+SmoothStart smooth_start(st_handle* h, int l = 0) {
+  Level& L0 = h->L[l];
   const LinParams<float> lp = lin_params<float>(h, L0, 0);
   SmoothStart ss;
   ss.y = (float*)L0.in[0].y;
@@ -2632,6 +2660,11 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
     CKL();
   }
   TRY(one(h->stream));  // warm (and capture, for the cycle)
+  if (which == ST_KERNEL_RESID_RESTRICT && (h->start_mask & 2u)) {
+    // as in the cycle, the kernel also wrote level 1's smoothing start (y, z)
+    bytes += 2.0 * (double)h->L[1].g.Ns * h->L[1].Nt * h->L[1].M * es;
+  }
+  h->start_mask = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -135,9 +135,12 @@ void sweep2_prepare();
 // k_linres_restrict.cu: the forward level residual r - A e + C e (FP32,
 // cbar, no exact Jacobian) fused with the full weighting onto gc (2D
 // periodic, both axes halved, whole 64 x 16 fine tiles, M = 3 or 5) into
-// coarse; false where it does not apply.
+// coarse; false where it does not apply.  With ss (and the coarse level's
+// cbar, or null without a reaction term) it also writes the first step of
+// the coarse level's first smoothing into ss->y, ss->z (*started: whether it did).
 void linres_restrict_prepare();
-bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st);
+bool launch_linres_restrict(int D, const LinParams<float>& p, const GridP& gc, float* coarse, cudaStream_t st,
+                            const SmoothStart* ss = nullptr, const float* cbarc = nullptr, bool* started = nullptr);
 bool launch_sweep2(int D, const InnerParams<float>& p, cudaStream_t st);
 // *slot = U on the stream (the address the two-sweep kernel's fused update reads)
 void launch_set_uslot(double** slot, double* U, cudaStream_t st);

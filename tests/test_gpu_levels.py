@@ -321,7 +321,9 @@ def test_fine_residual_smoothing_start_same_bits(case):
         S.close()
     assert torch.equal(outs[0], outs[1])
     assert norms[0] == norms[1]
-    assert launches[0] == launches[1] - 1, launches
+    # one launch fewer at level 0, and one per level below whose smoothing
+    # start the residual-restriction kernel wrote
+    assert launches[0] <= launches[1] - 1, launches
 
 
 @pytest.mark.parametrize("case", [TILED_SQ3, TILED_SQ5, TILED_START, TILED_HEAT3], ids=lambda c: c.name)
