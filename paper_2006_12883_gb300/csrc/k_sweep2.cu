@@ -30,12 +30,13 @@ constexpr int kTH = 8;            // tile height (rows)
 constexpr int kS = 72;            // shared row stride: columns -4..67, the tile's at 4..67
 
 // shared planes of a tile of kH rows: z rows -2..kH+1, y, cbar and z' rows -1..kH
+// (the first sweep's result z' replaces z in place, rows -1..kH, once every
+// thread has read z)
 template <int M, int kH>
 struct Sweep2Smem {
   static constexpr int kZR = kH + 4, kYR = kH + 2;
   float z[M][kZR][kS];
   float y[M][kYR][kS];
-  float z1[M][kYR][kS];
   float cb[kYR][kS];
 };
 
@@ -125,7 +126,7 @@ __device__ __forceinline__ double f2d(float f) {
 // UPD: the epilogue also adds e' to the FP64 iterate (*p.Uslot) and writes e
 // only if p.write_e: the step's update of U done by the cycle's last kernel.
 template <int M, int kH, bool UPD>
-__global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<float> p) {
+__global__ void __launch_bounds__(sweep2_threads<kH>(), 5) k_sweep2(InnerParams<float> p) {
   grid_dep_wait();
   constexpr int kZR = kH + 4, kYR = kH + 2, kThreads = sweep2_threads<kH>();
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -180,8 +181,11 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
 
   // first sweep on rows -1..kH: thread tid takes the group of 4 points at
   // shared row r (tile row r - 1) and columns c0..c0+3
+  // (held in registers until every thread has read z)
+  const int r1 = tid >> 4, c1 = 4 + 4 * (tid & 15);
+  float z1g[M][4];
   {
-    const int r = tid >> 4, c0 = 4 + 4 * (tid & 15);
+    const int r = r1, c0 = c1;
     float cb[4] = {0.f, 0.f, 0.f, 0.f};
     if (has_cb) ld4s(&S.cb[r][c0], cb);
 #pragma unroll
@@ -189,18 +193,20 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
       if (!lead_plane(pl)) continue;
       const int kd = plane_kind(pl);
       const int pi = pl + 1 < M ? pl + 1 : pl;
-      float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4], outr[4], outi[4];
+      float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4];
       group_operands(S.z[pl][r + 1], S.z[pl][r], S.z[pl][r + 2], S.y[pl][r], c0, zr, yr, sxr, syr);
       if (kd == SH_RE) group_operands(S.z[pi][r + 1], S.z[pi][r], S.z[pi][r + 2], S.y[pi][r], c0, zi, yi, sxi, syi);
-      jacobi_pair<4>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, outr, outi);
-      *reinterpret_cast<float4*>(&S.z1[pl][r][c0]) = make_float4(outr[0], outr[1], outr[2], outr[3]);
-      if (kd == SH_RE) *reinterpret_cast<float4*>(&S.z1[pi][r][c0]) = make_float4(outi[0], outi[1], outi[2], outi[3]);
+      jacobi_pair<4>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, z1g[pl], z1g[pi]);
     }
   }
   // first sweep at the ring's columns -1 and 64 of rows -1..kH: one item per
   // (point, real plane or complex pair), spread over the block
+  constexpr int np = (M + 1) / 2;  // the real plane and the pairs
+  static_assert(kYR * 2 * np <= kThreads, "one ring item per thread at most");
+  const bool ring = tid < kYR * 2 * np;
+  float ring_r = 0.f, ring_i = 0.f;
+  int ring_pl = 0, ring_pi = 0, ring_row = 0, ring_col = 0;
   {
-    constexpr int np = (M + 1) / 2;  // the real plane and the pairs
     for (int item = tid; item < kYR * 2 * np; item += kThreads) {
       const int pt = item % (kYR * 2), k = item / (kYR * 2);
       const int r = pt >> 1, c = 4 + ((pt & 1) ? kW : -1);
@@ -214,13 +220,27 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
       float sxi[1] = {S.z[pi][r + 1][c - 1] + S.z[pi][r + 1][c + 1]}, syi[1] = {S.z[pi][r][c] + S.z[pi][r + 2][c]};
       float outr[1], outi[1];
       jacobi_pair<1>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, outr, outi);
-      S.z1[pl][r][c] = outr[0];
-      if (kd == SH_RE) S.z1[pi][r][c] = outi[0];
+      ring_r = outr[0];
+      ring_i = outi[0];
+      ring_pl = pl;
+      ring_pi = kd == SH_RE ? pi : -1;
+      ring_row = r;
+      ring_col = c;
     }
+  }
+  __syncthreads();
+  // z' over z: z' row r (tile row r - 1) at z row r + 1, same columns
+#pragma unroll
+  for (int pl = 0; pl < M; ++pl)
+    *reinterpret_cast<float4*>(&S.z[pl][r1 + 1][c1]) = make_float4(z1g[pl][0], z1g[pl][1], z1g[pl][2], z1g[pl][3]);
+  if (ring) {
+    S.z[ring_pl][ring_row + 1][ring_col] = ring_r;
+    if (ring_pi >= 0) S.z[ring_pi][ring_row + 1][ring_col] = ring_i;
   }
   __syncthreads();
 
   // second sweep on the tile, fused with the back-transform and the update of e
+  float evs[UPD ? M : 1][4];
   if (in_tile) {
     const int r = ty + 1, c0 = 4 + 4 * tx;
     float cb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -232,8 +252,8 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
       const int kd = plane_kind(pl);
       const int pi = pl + 1 < M ? pl + 1 : pl;
       float zr[4], yr[4], sxr[4], syr[4], zi[4], yi[4], sxi[4], syi[4];
-      group_operands(S.z1[pl][r], S.z1[pl][r - 1], S.z1[pl][r + 1], S.y[pl][r], c0, zr, yr, sxr, syr);
-      if (kd == SH_RE) group_operands(S.z1[pi][r], S.z1[pi][r - 1], S.z1[pi][r + 1], S.y[pi][r], c0, zi, yi, sxi, syi);
+      group_operands(S.z[pl][r + 1], S.z[pl][r], S.z[pl][r + 2], S.y[pl][r], c0, zr, yr, sxr, syr);
+      if (kd == SH_RE) group_operands(S.z[pi][r + 1], S.z[pi][r], S.z[pi][r + 2], S.y[pi][r], c0, zi, yi, sxi, syi);
       jacobi_pair<4>(p, kd, p.sh.sr[pl], p.sh.si[pl], zr, yr, sxr, syr, zi, yi, sxi, syi, cb, out[pl], out[pi]);
     }
 #pragma unroll
@@ -247,17 +267,24 @@ __global__ void __launch_bounds__(sweep2_threads<kH>(), 4) k_sweep2(InnerParams<
         ev[q] = fmaf(p.omega_bt, acc, ev[q]);
       }
       if constexpr (UPD) {
-        // e' to shared memory over z (not read since the first sweep)
-        *reinterpret_cast<float4*>(&S.z[0][0][0] + (a * kH + ty) * kW + 4 * tx) =
-            make_float4(ev[0], ev[1], ev[2], ev[3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) evs[a][q] = ev[q];
       } else {
         *reinterpret_cast<float4*>(p.e + own + a * Ns) = make_float4(ev[0], ev[1], ev[2], ev[3]);
       }
     }
   }
   if constexpr (UPD) {
+    // e' to shared memory over z (once every thread has read z'), then
     // U += e' on the tile: every thread, two points per item, the loads of U
     // of all its items issued first
+    __syncthreads();
+    if (in_tile) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+        *reinterpret_cast<float4*>(&S.z[0][0][0] + (a * kH + ty) * kW + 4 * tx) =
+            make_float4(evs[a][0], evs[a][1], evs[a][2], evs[a][3]);
+    }
     __syncthreads();
     double* __restrict__ U = *p.Uslot;
     constexpr int kItems = M * kH * (kW / 2), kPer = (kItems + kThreads - 1) / kThreads;
