@@ -126,7 +126,7 @@ __device__ __forceinline__ double f2d(float f) {
 // UPD: the epilogue also adds e' to the FP64 iterate (*p.Uslot) and writes e
 // only if p.write_e: the step's update of U done by the cycle's last kernel.
 template <int M, int kH, bool UPD>
-__global__ void __launch_bounds__(sweep2_threads<kH>(), 5) k_sweep2(InnerParams<float> p) {
+__global__ void __launch_bounds__(sweep2_threads<kH>(), M == 3 ? 7 : 5) k_sweep2(InnerParams<float> p) {
   grid_dep_wait();
   constexpr int kZR = kH + 4, kYR = kH + 2, kThreads = sweep2_threads<kH>();
   extern __shared__ __align__(16) unsigned char smraw[];
