@@ -169,15 +169,15 @@ class ClockSampler:
 # launch by the dofs it processes.  Valid only for the kernel source it was
 # taken on (sha256 of the file that holds the kernel).
 NCU_TRAFFIC = {
-    # k_sweep2<5, 8, 0> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.78 MB read + 476.48 MB written per
+    # k_sweep2<5, 8, 0> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.78 MB read + 476.65 MB written per
     # launch (the probe's two timed launches)
     "k_sweep2<5, 8, 0>": {"file": "k_sweep2.cu",
-                          "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
-                          "dram_bytes_per_dof": (1610844416 + 476482048 + 1610709504 + 476481024) / 2 / 125829120},
-    # k_sweep2<5, 8, 1> (with the update of U) on the same case: 2617.33 MB read + 970.44 MB written per launch
+                          "sha256": "47e1f17e813b7cfc9319cc7bdf7f585f459d63e12a778189bb4f44cfd4c08bb6",
+                          "dram_bytes_per_dof": (1610694400 + 476702464 + 1610873088 + 476605696) / 2 / 125829120},
+    # k_sweep2<5, 8, 1> (with the update of U) on the same case: 2617.33 MB read + 968.78 MB written per launch
     "k_sweep2<5, 8, 1>": {"file": "k_sweep2.cu",
-                          "sha256": "b93290c3dc1de4c01e85cb7015b71ef276b3a1189fab6038a2e2db4332eb25c4",
-                          "dram_bytes_per_dof": (2617369600 + 970466304 + 2617298176 + 970422784) / 2 / 125829120},
+                          "sha256": "47e1f17e813b7cfc9319cc7bdf7f585f459d63e12a778189bb4f44cfd4c08bb6",
+                          "dram_bytes_per_dof": (2617355264 + 968940032 + 2617312768 + 968617728) / 2 / 125829120},
 }
 
 
