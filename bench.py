@@ -172,11 +172,11 @@ NCU_TRAFFIC = {
     # k_sweep2<5, 8, 0> on 512^2 x 96 slabs x M = 5 (125.8M dofs): 1610.78 MB read + 476.65 MB written per
     # launch (the probe's two timed launches)
     "k_sweep2<5, 8, 0>": {"file": "k_sweep2.cu",
-                          "sha256": "47e1f17e813b7cfc9319cc7bdf7f585f459d63e12a778189bb4f44cfd4c08bb6",
+                          "sha256": "a9cc179b363433806c939574ba174a042f5c6a81725743f8fb2f46b647887b4c",
                           "dram_bytes_per_dof": (1610694400 + 476702464 + 1610873088 + 476605696) / 2 / 125829120},
     # k_sweep2<5, 8, 1> (with the update of U) on the same case: 2617.33 MB read + 968.78 MB written per launch
     "k_sweep2<5, 8, 1>": {"file": "k_sweep2.cu",
-                          "sha256": "47e1f17e813b7cfc9319cc7bdf7f585f459d63e12a778189bb4f44cfd4c08bb6",
+                          "sha256": "a9cc179b363433806c939574ba174a042f5c6a81725743f8fb2f46b647887b4c",
                           "dram_bytes_per_dof": (2617355264 + 968940032 + 2617312768 + 968617728) / 2 / 125829120},
 }
 

@@ -6,8 +6,9 @@
 // M = 5); here a block stages e with a two-point ring, r, cbar and the slab
 // coupling plane with a one-point ring in shared memory (cp.async), computes
 // res on its 64 x 16 fine tile and the one-point ring the weighting needs,
-// in place of r, and writes the 32 x 8 coarse tile: about 10.6 bytes per fine
-// dof.  The arithmetic is term for term that of k_lin_residual4 and
+// in place of r (one 4-point group or ring point per thread), and writes the
+// 32 x 8 coarse tile: 9.8 bytes per fine dof (the coupling plane and the
+// halos come from L2).  The arithmetic is term for term that of k_lin_residual4 and
 // k_restrict4 (k_level4.cu), so the coarse values equal the two-launch
 // sequence's to the bit.  With START the kernel also does the first step of
 // the coarse level's first smoothing, which starts from e = 0 (so its level

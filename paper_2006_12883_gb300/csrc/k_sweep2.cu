@@ -5,13 +5,14 @@
 // The separate kernels stream z, y and cbar twice and z' out and back in;
 // here a block brings z with a two-point halo, y and cbar with a one-point
 // halo into shared memory (cp.async copies, all of a thread's copies in
-// flight at once), computes z' on the tile and its one-point ring, keeps it
-// in shared memory, and computes the second sweep on the tile: 16.8 instead
-// of 29.6 bytes per dof at M = 5.  Tiles of 64 x 8 (49 KB of shared memory at
-// M = 5, four blocks per SM) measured faster than 64 x 16 (86 KB, two blocks):
-// 19.5 against 20.8 ms on 1024^2 x 1024 slabs x 5 nodes.  The arithmetic is that of k_inner4's
-// sweep (k_level4.cu), term for term, so the result equals the two-launch
-// sequence.
+// flight at once), computes z' on the tile and its one-point ring into
+// registers, writes it over z once every thread has read z, and computes the
+// second sweep on the tile: 16.8 instead of 29.6 bytes per dof at M = 5.
+// Tiles of 64 x 8 with z' over z take 35 KB of shared memory at M = 5 (five
+// blocks per SM) and 22 KB at M = 3 (seven); a separate z' buffer (four
+// blocks) and 64 x 16 tiles (two blocks) measured slower.  The arithmetic is
+// that of k_inner4's sweep (k_level4.cu), term for term, so the result
+// equals the two-launch sequence.
 #include <mutex>
 
 #include "st_kernels.cuh"
@@ -29,9 +30,9 @@ __host__ __device__ constexpr int plane_kind(int q) { return q == 0 ? SH_REAL : 
 constexpr int kTH = 8;            // tile height (rows)
 constexpr int kS = 72;            // shared row stride: columns -4..67, the tile's at 4..67
 
-// shared planes of a tile of kH rows: z rows -2..kH+1, y, cbar and z' rows -1..kH
-// (the first sweep's result z' replaces z in place, rows -1..kH, once every
-// thread has read z)
+// shared planes of a tile of kH rows: z rows -2..kH+1, y and cbar rows
+// -1..kH (the first sweep's result z' replaces z in place, rows -1..kH, once
+// every thread has read z)
 template <int M, int kH>
 struct Sweep2Smem {
   static constexpr int kZR = kH + 4, kYR = kH + 2;
