@@ -36,6 +36,33 @@ def test_exports_every_declared_symbol(stlib):
     assert set(names) <= set(stlib._SIGS), set(names) - set(stlib._SIGS)
 
 
+def test_solver_opts_layout_and_defaults(stlib):
+    """The binding's st_solver_opts matches the C struct: the library's
+    defaults land in the fields the header documents, through the last one
+    (a field missing or out of order in the binding would shift them)."""
+    C_FIELDS = [n.strip() for decl in re.findall(r"\b(?:int|double)\s+([^;]+);", _struct_text("st_solver_opts"))
+                for n in decl.split(",")]
+    assert [f for f, _ in stlib.StSolverOpts._fields_] == C_FIELDS
+    o = stlib.st_default_opts()
+    assert (o.nu1, o.nu2, o.smooth_sweeps, o.inner_cycles, o.use_graphs, o.use_tma) == (1, 1, 3, 1, 1, 1)
+    assert o.recompute_slabs == 0
+    assert (o.fuse_sweeps, o.fuse_start, o.fuse_restrict, o.fuse_update) == (1, 1, 1, 1)
+    assert o.tol > 0 and o.krylov_rtol > 0
+    S_FIELDS = [n.strip() for decl in re.findall(r"\b(?:int|double)\s+([^;]+);", _struct_text("st_stats_info"))
+                for n in decl.split(",")]
+    assert [f for f, _ in stlib.StStatsInfo._fields_] == S_FIELDS
+
+
+def _struct_text(name):
+    with open(os.path.join(ROOT, "include", "st.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    end = re.search(r"\}\s*" + name + r"\s*;", text)
+    assert end, name
+    start = text.rfind("typedef struct", 0, end.start())
+    return text[text.index("{", start) + 1:end.start()]
+
+
 @pytest.mark.parametrize("M", [1, 2, 3, 4, 5])
 def test_host_collocation_setup_matches_oracle(stlib, M):
     tau, Q, lam, V, Vi = stlib.st_collocation(M)
