@@ -2679,6 +2679,7 @@ int st_time_kernel(st_handle* h, int which, const double* U, int iters, double* 
   }
   CK(cudaEventRecord(e1, h->stream));
   CK(cudaEventSynchronize(e1));
+  h->start_mask = 0;  // set by the residual-restriction probe, consumed by no cycle
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
